@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark: negacyclic RNS NTT, N = 2^16, L = 45 limbs, forward + inverse.
+
+One step = the forward then the inverse transform of one RNS polynomial of 45
+limbs (the 45 largest primes < 2^60 with q = 1 mod 2^17), uint64 residues,
+seeded uniform inputs.  Metric: limb-NTT/s (each limb forward or inverse
+counts as one), with the fraction of the HBM roofline for one read plus one
+write of the data per transform.
+
+Arms:
+  default            the CUDA library through its C ABI (device buffers);
+  --impl reference   the CPU oracle, timed on the host cores.
+Multi-GPU (torchrun): every rank transforms its own polynomials on its own GPU
+(replicas, no collective); value = all ranks' limb-NTTs / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ntt_inputs as I  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+PROFILE_MD = os.path.join(ROOT, "profiles", "ntt_c2_n65536_l45.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--twiddle", default="auto", choices=["auto", "table", "ot1", "ot2"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2012_01968_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per transform launch from the committed ncu summary, if it is
+    for the current kernel sources (else None)."""
+    try:
+        txt = open(PROFILE_MD).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg
+# ----------------------------------------------------------------------------
+def oracle_time(primes, N, seconds_target: float):
+    """Oracle forward + inverse over all limbs of one C2 polynomial, repeated
+    until ~seconds_target elapse; returns (limb-NTT/s, cores, sample text)."""
+    import oracle
+    orc = oracle.get()
+    cores = os.cpu_count() or 1
+    data = I.batch_uniform(2, 1, primes, N)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        f = orc.ntt_batch(data, primes, +1, cores)
+        b = orc.ntt_batch(f, primes, -1, cores)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target:
+            break
+    if not np.array_equal(b, data):
+        raise RuntimeError("oracle round trip failed")
+    v = reps * 2 * len(primes) / el
+    return v, cores, f"{reps} x (forward + inverse of all {len(primes)} limbs), N={N}, {el:.1f} s"
+
+
+def run_reference(args, metric, unit, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    orc = oracle.get()
+    cores = os.cpu_count() or 1
+    N, primes = w.N, w.primes
+    data = I.batch_uniform(w.seed, 1, primes, N)[0]
+    # one step = forward + inverse of one limb (limb = step mod L); steps run
+    # `cores` at a time, one per host thread
+    def run_group(first, count):
+        done = 0
+        while done < count:
+            k = min(cores, count - done)
+            idx = [(first + done + i) % len(primes) for i in range(k)]
+            # all limbs of a group share N; the oracle threads over (batch x L)
+            blk = np.stack([data[i] for i in idx])[None]          # [1, k, N]
+            pr = [primes[i] for i in idx]
+            f = orc.ntt_batch(blk, pr, +1, k)
+            orc.ntt_batch(f, pr, -1, k)
+            done += k
+        return done
+    run_group(0, args.warmup)
+    t0 = time.perf_counter()
+    run_group(args.warmup, args.steps)
+    el = time.perf_counter() - t0
+    value = 2.0 * args.steps / el
+    line = {
+        "impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": config_dict(w, args, ws),
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                         "sample": f"each step = forward + inverse of one N={N} limb (limb = step mod 45), "
+                                   f"{cores} steps in flight on {cores} host threads"},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(w, args, ws):
+    return {"workload": "c2_n65536_l45_fwd_inv", "N": w.N, "L": len(w.primes), "polys_per_step": 1,
+            "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
+            "twiddle": args.twiddle, "parallelism": f"replicas{ws}",
+            "l2": "inputs rotate over buffers totalling > 2x L2 (129 MB)"}
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+def main():
+    args = parse()
+    metric = "limb-NTT/s, N=2^16 L=45 forward+inverse (bit-exact)"
+    unit = "limb-NTT/s"
+    w = I.workload_c2()
+    if args.impl == "reference":
+        run_reference(args, metric, unit, w)
+        return
+
+    import torch
+    import paper_2012_01968_gb300 as G
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+    G.lib()
+
+    N, primes, L = w.N, w.primes, len(w.primes)
+    mode = {"auto": (G.NTT_TWIDDLE_AUTO, 0), "table": (G.NTT_TWIDDLE_TABLE, 0),
+            "ot1": (G.NTT_TWIDDLE_OT, 1), "ot2": (G.NTT_TWIDDLE_OT, 2)}[args.twiddle]
+    plan = G.Plan(N, primes, *mode)
+    info = plan.info()
+    poly_bytes = N * L * 8
+    nbuf = max(2, -(-2 * L2_BYTES // poly_bytes) + 1)
+    host = I.batch_uniform(w.seed, 1, primes, N)
+    src = torch.from_numpy(host.view(np.int64).copy()).cuda()
+    bufs = [src.clone() for _ in range(nbuf)]
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    lib = G.lib()
+    ph = plan.handle
+
+    def step(i):
+        b = bufs[i % nbuf].data_ptr()
+        if lib.ntt_forward(ph, b, 1, sh) or lib.ntt_inverse(ph, b, 1, sh):
+            raise RuntimeError("launch failed: " + G.ntt_last_cuda_error())
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+    torch.cuda.synchronize()
+    # correctness of the timed path: forward + inverse restores the input
+    for b in bufs:
+        if not torch.equal(b, src):
+            raise RuntimeError("round trip mismatch before timing")
+
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    clk = ClockSampler(dev_index)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.15)
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for i in range(K):
+            b = bufs[i % nbuf].data_ptr()
+            if lib.ntt_forward(ph, b, 1, sh):
+                raise RuntimeError(G.ntt_last_cuda_error())
+            ev[2 * i + 1].record(stream)
+            if lib.ntt_inverse(ph, b, 1, sh):
+                raise RuntimeError(G.ntt_last_cuda_error())
+            ev[2 * i + 2].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist is not None:
+        dist.barrier()
+    total_ms = ev[0].elapsed_time(ev[2 * K])
+    fwd_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)]
+    inv_ms = [ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(K)]
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    for b in bufs:
+        if not torch.equal(b, src):
+            raise RuntimeError("round trip mismatch after timing")
+    limb_ntts = 2 * L * K * ws
+    value = limb_ntts / (total_ms / 1e3)
+
+    peak, peak_src = measured_peak_hbm()
+    fwd_avg = float(np.mean(fwd_ms))
+    inv_avg = float(np.mean(inv_ms))
+    dom_name, dom_ms = ("ntt_forward", fwd_avg) if fwd_avg >= inv_avg else ("ntt_inverse", inv_avg)
+    alg_bytes = 2 * poly_bytes                       # one read + one write per transform
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    step_bytes = 2 * alg_bytes
+    frac_step = (step_bytes * K / (total_ms / 1e3) / 1e9) / peak
+
+    # end to end through the host-buffer C ABI call (pinned host memory)
+    e2e = None
+    if True:
+        hin = torch.from_numpy(host.view(np.int64).copy()).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        ops = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+        for _ in range(3):
+            G.ntt_execute_host(ph, hin, hout, 1, ops, stream)
+        E = args.e2e_steps
+        t0 = time.perf_counter()
+        for _ in range(E):
+            G.ntt_execute_host(ph, hin, hout, 1, ops, stream)
+        el = time.perf_counter() - t0
+        if not torch.equal(hout, hin):
+            raise RuntimeError("e2e round trip mismatch")
+        e2e = {"value": 2 * L * E / el, "unit": unit, "h2d_bytes_per_step": poly_bytes,
+               "d2h_bytes_per_step": poly_bytes, "steps": E}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_time(primes, N, 10.0)
+        cpu = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": config_dict(w, args, ws),
+        "hbm_roofline_frac_step": frac_step,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profile_traffic(),
+                     "kernel": f"{dom_name} ({info.passes} pass launches)",
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
+        "per_transform_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3,
+                             "sum_of_calls_vs_wall": (sum(fwd_ms) + sum(inv_ms)) / total_ms},
+        "plan": {"twiddle_mode": int(info.twiddle_mode), "ot_stages": int(info.ot_stages),
+                 "passes": int(info.passes), "pass1_log2": int(info.pass1_log2)},
+        "e2e": e2e,
+        "gpu_launches": K * 2 * int(info.passes),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

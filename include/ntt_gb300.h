@@ -1,0 +1,169 @@
+/*
+ * ntt_gb300.h -- C ABI of the GB300 (sm_103a) negacyclic RNS NTT library.
+ *
+ * The library computes the forward and inverse negacyclic Number Theoretic
+ * Transform of RNS polynomials (Kim, Jung, Park, Ahn, "Accelerating Number
+ * Theoretic Transformations for Bootstrappable Homomorphic Encryption on
+ * GPUs"):
+ *
+ *   forward (Sec. III-A merged form; output order of Algorithm 1):
+ *     out[i] = sum_{n<N} a[n] * psi^{n (2 brv(i) + 1)}  mod q
+ *   inverse (Sec. III-A, Psi^{-1} merged into the iNTT):
+ *     a[n]   = N^{-1} * sum_{i<N} out[i] * psi^{-n (2 brv(i) + 1)}  mod q
+ *
+ * where brv is the log2(N)-bit reversal (forward outputs are in bit-reversed
+ * order, as Algorithm 1 produces them; the inverse takes that order back to
+ * natural order), q is an RNS prime with q = 1 mod 2N (Sec. III-B), and psi =
+ * g^{(q-1)/2N} with g the smallest generator of Z_q^*.
+ *
+ * Data layout: a batch of polynomials is one device array of uint64_t words,
+ * laid out [batch][L][N] (limb-contiguous: limb l of polynomial b starts at
+ * word (b * L + l) * N).  Coefficients are residues in [0, q_l); results are
+ * residues in [0, q_l).  Inputs outside [0, q_l) give unspecified results.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Device calls are asynchronous and stream-ordered; argument
+ * errors are returned synchronously before anything is enqueued.  A plan is
+ * immutable after creation and may be used from several host threads and
+ * streams at once.  All calls must run with the plan's device current.
+ *
+ * Errors: every call returns an ntt_status; NTT_OK is 0.  On error nothing is
+ * enqueued and output arguments are left untouched.
+ */
+#ifndef NTT_GB300_H
+#define NTT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ntt_status {
+    NTT_OK = 0,
+    NTT_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad option */
+    NTT_ERR_BAD_PRIME = 2,    /* composite, q != 1 mod 2N, or q outside (2^32, 2^60) */
+    NTT_ERR_MISALIGNED = 3,   /* a device pointer is not 16-byte aligned */
+    NTT_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    NTT_ERR_OOM = 5,          /* device or host allocation failed */
+    NTT_ERR_BUSY = 6,         /* admission refused (serving) */
+    NTT_ERR_TIMEOUT = 7,      /* a bounded wait expired */
+    NTT_ERR_DEVICE = 8        /* a kernel reported an error status */
+} ntt_status;
+
+/* Opaque plan: N, the primes, psi per prime and the device tables. */
+typedef struct ntt_plan ntt_plan;
+
+/* Twiddle supply (Sec. VII): precomputed table Psi with Shoup companions, or
+ * on-the-fly twiddling (OT), which rebuilds the twiddles of the last stages
+ * from two small per-prime factor tables with one extra Shoup product each. */
+enum {
+    NTT_TWIDDLE_AUTO = 0,
+    NTT_TWIDDLE_TABLE = 1,
+    NTT_TWIDDLE_OT = 2
+};
+
+typedef struct ntt_plan_opts {
+    uint32_t twiddle_mode;    /* NTT_TWIDDLE_*; AUTO picks per N */
+    uint32_t ot_stages;       /* OT: final stages built on the fly, 1 or 2 (0 = 1) */
+    uint32_t reserved[6];     /* must be zero */
+} ntt_plan_opts;
+
+/*
+ * Create a plan for N-point transforms over the L primes primes[0..L-1].
+ *   N      : power of two, 2 <= N <= 131072 (2^17).
+ *   primes : host array of L primes, each with q = 1 mod 2N and
+ *            2^32 < q < 2^60 (copied; the caller keeps ownership).
+ *   L      : 1 <= L <= 4096.
+ *   opts   : NULL for defaults.
+ * The plan (host object and device tables, 16 * N * L bytes in table mode)
+ * belongs to the library until ntt_plan_destroy.  It is created on the
+ * current CUDA device.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME,
+ * NTT_ERR_OOM, NTT_ERR_CUDA; *out is left untouched on error.
+ * (Paper: the precomputed tables of Sec. IV "Precomputed table size with
+ * batching" and Sec. VII.)
+ */
+ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t* primes, uint32_t L,
+                           const ntt_plan_opts* opts);
+
+/* Free a plan.  NULL is allowed.  Work that uses the plan must have finished. */
+void ntt_plan_destroy(ntt_plan* plan);
+
+/*
+ * In-place forward transform of `batch` polynomials at device address `data`
+ * (layout [batch][L][N], 16-byte aligned, caller-owned).  Input in natural
+ * coefficient order, output in bit-reversed order (Algorithm 1).  All
+ * batch * L limbs run in one launch per pass (batching, Sec. V / VI-A).
+ * Errors: NTT_ERR_INVALID_ARG (NULL, batch == 0), NTT_ERR_MISALIGNED,
+ * NTT_ERR_CUDA (launch failure).
+ */
+ntt_status ntt_forward(const ntt_plan* plan, uint64_t* data, uint32_t batch, void* stream);
+
+/* In-place inverse transform (bit-reversed order in, natural order out,
+ * N^{-1} applied).  Same arguments and errors as ntt_forward. */
+ntt_status ntt_inverse(const ntt_plan* plan, uint64_t* data, uint32_t batch, void* stream);
+
+/*
+ * Level-aware variants: transform only the first `levels` primes of the plan
+ * (1 <= levels <= L); data is laid out [batch][levels][N].  A polynomial at a
+ * lower HE level carries fewer RNS limbs (Sec. III-B).
+ */
+ntt_status ntt_forward_levels(const ntt_plan* plan, uint64_t* data, uint32_t batch,
+                              uint32_t levels, void* stream);
+ntt_status ntt_inverse_levels(const ntt_plan* plan, uint64_t* data, uint32_t batch,
+                              uint32_t levels, void* stream);
+
+/*
+ * c = a (*) b, the element-wise product mod q_l of two polynomials in the
+ * transform domain (the middle step of the convolution theorem, Sec. III-A).
+ * a, b, c: device arrays [batch][L][N], 16-byte aligned; c may alias a or b.
+ */
+ntt_status ntt_mul_pointwise(const ntt_plan* plan, const uint64_t* a, const uint64_t* b,
+                             uint64_t* c, uint32_t batch, void* stream);
+
+/* Operation flags for ntt_execute_host. */
+enum {
+    NTT_OP_FORWARD = 1,
+    NTT_OP_INVERSE = 2          /* with NTT_OP_FORWARD: forward, then inverse */
+};
+
+/*
+ * Host-memory convenience call: copy `batch` polynomials from host_in to the
+ * device, apply the operations in `ops` (forward, inverse, or forward then
+ * inverse), copy the result to host_out, and wait for completion.  Uses a
+ * device staging buffer owned by the plan (grown on first use and kept until
+ * ntt_plan_destroy); host_in and host_out may be the same array and should be
+ * page-locked for full copy bandwidth.  Calls on one plan are serialised.
+ */
+ntt_status ntt_execute_host(const ntt_plan* plan, const uint64_t* host_in, uint64_t* host_out,
+                            uint32_t batch, uint32_t ops, void* stream);
+
+/* Plan facts, for callers and tests. */
+typedef struct ntt_plan_info {
+    uint32_t N, L;
+    uint32_t log2_N;
+    uint32_t passes;          /* kernel passes per transform (1 or 2) */
+    uint32_t pass1_log2;      /* stages in the first pass */
+    uint32_t twiddle_mode;    /* NTT_TWIDDLE_TABLE or NTT_TWIDDLE_OT */
+    uint32_t ot_stages;       /* OT: final stages built on the fly */
+    uint32_t device;          /* CUDA device ordinal */
+    uint64_t device_bytes;    /* device memory held by the plan (tables) */
+} ntt_plan_info;
+
+ntt_status ntt_plan_query(const ntt_plan* plan, ntt_plan_info* info);
+
+/* psi for prime l (0 <= l < L) of the plan, into *psi. */
+ntt_status ntt_plan_psi(const ntt_plan* plan, uint32_t l, uint64_t* psi);
+
+/* Static text for a status code (never NULL). */
+const char* ntt_status_string(ntt_status status);
+
+/* Text of the last CUDA error seen by this thread inside the library. */
+const char* ntt_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTT_GB300_H */

@@ -1,0 +1,276 @@
+"""Python binding of the GB300 negacyclic RNS NTT library (libntt_gb300.so).
+
+The functions mirror the C ABI in include/ntt_gb300.h one to one and only
+marshal arguments: every transform step runs in the library's CUDA kernels.
+Device buffers may be given as torch CUDA tensors (uint64 or int64, contiguous)
+or as raw integer addresses; streams as torch.cuda.Stream, a raw handle, or
+None (torch's current stream when a tensor is passed, else the default
+stream).  There is no CPU fallback: if the library is missing, importing the
+functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libntt_gb300.so")
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "ntt_gb300.h")
+
+NTT_OK = 0
+NTT_ERR_INVALID_ARG = 1
+NTT_ERR_BAD_PRIME = 2
+NTT_ERR_MISALIGNED = 3
+NTT_ERR_CUDA = 4
+NTT_ERR_OOM = 5
+NTT_ERR_BUSY = 6
+NTT_ERR_TIMEOUT = 7
+NTT_ERR_DEVICE = 8
+
+NTT_TWIDDLE_AUTO = 0
+NTT_TWIDDLE_TABLE = 1
+NTT_TWIDDLE_OT = 2
+
+NTT_OP_FORWARD = 1
+NTT_OP_INVERSE = 2
+
+_u32, _u64, _vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("reserved", _u32 * 6)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("N", _u32), ("L", _u32), ("log2_N", _u32), ("passes", _u32),
+                ("pass1_log2", _u32), ("twiddle_mode", _u32), ("ot_stages", _u32),
+                ("device", _u32), ("device_bytes", _u64)]
+
+
+class NttError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib().ntt_status_string(status).decode()
+        if status == NTT_ERR_CUDA:
+            msg += " (" + _lib().ntt_last_cuda_error().decode() + ")"
+        super().__init__(f"{where}: {msg}")
+
+
+_lock = threading.Lock()
+_L = None
+
+
+def build(verbose: bool = False) -> str:
+    from . import builder
+    return builder.build(verbose=verbose)
+
+
+def _lib():
+    global _L
+    if _L is not None:
+        return _L
+    with _lock:
+        if _L is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run paper_2012_01968_gb300.build() or python -m paper_2012_01968_gb300.builder)")
+            L = ctypes.CDLL(LIB_PATH)
+            S = ctypes.c_int
+            L.ntt_plan_create.restype = S
+            L.ntt_plan_create.argtypes = [ctypes.POINTER(_vp), _u32, _u64p, _u32, ctypes.POINTER(PlanOpts)]
+            L.ntt_plan_destroy.restype = None
+            L.ntt_plan_destroy.argtypes = [_vp]
+            for f in ("ntt_forward", "ntt_inverse"):
+                getattr(L, f).restype = S
+                getattr(L, f).argtypes = [_vp, _vp, _u32, _vp]
+            for f in ("ntt_forward_levels", "ntt_inverse_levels"):
+                getattr(L, f).restype = S
+                getattr(L, f).argtypes = [_vp, _vp, _u32, _u32, _vp]
+            L.ntt_mul_pointwise.restype = S
+            L.ntt_mul_pointwise.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
+            L.ntt_execute_host.restype = S
+            L.ntt_execute_host.argtypes = [_vp, _vp, _vp, _u32, _u32, _vp]
+            L.ntt_plan_query.restype = S
+            L.ntt_plan_query.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
+            L.ntt_plan_psi.restype = S
+            L.ntt_plan_psi.argtypes = [_vp, _u32, _u64p]
+            L.ntt_status_string.restype = ctypes.c_char_p
+            L.ntt_status_string.argtypes = [S]
+            L.ntt_last_cuda_error.restype = ctypes.c_char_p
+            L.ntt_last_cuda_error.argtypes = []
+            _L = L
+    return _L
+
+
+def lib():
+    """The loaded ctypes library (raises if it was not built)."""
+    return _lib()
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+def _addr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a device address of {type(x)!r}")
+
+
+def _stream(stream, like=None) -> int:
+    if stream is None:
+        if like is not None and hasattr(like, "data_ptr"):
+            import torch
+            return int(torch.cuda.current_stream(like.device).cuda_stream)
+        return 0
+    if isinstance(stream, int):
+        return stream
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    raise TypeError(f"bad stream {type(stream)!r}")
+
+
+def _check(st: int, where: str):
+    if st != NTT_OK:
+        raise NttError(st, where)
+
+
+# --------------------------------------------------------------------------
+# C ABI, same names
+# --------------------------------------------------------------------------
+def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0) -> int:
+    """Create a plan; returns the opaque handle (an int).  Raises NttError."""
+    primes = [int(p) for p in primes]
+    arr = (_u64 * len(primes))(*primes)
+    opts = PlanOpts(twiddle_mode, ot_stages)
+    out = _vp()
+    _check(_lib().ntt_plan_create(ctypes.byref(out), N, arr, len(primes), ctypes.byref(opts)),
+           "ntt_plan_create")
+    return int(out.value)
+
+
+def ntt_plan_create_status(N: int, primes, twiddle_mode: int = 0, ot_stages: int = 0, reserved=None):
+    """Like ntt_plan_create but returns (status, handle) without raising."""
+    primes = [int(p) for p in primes]
+    arr = (_u64 * max(1, len(primes)))(*primes)
+    opts = PlanOpts(twiddle_mode, ot_stages)
+    if reserved:
+        for i, v in enumerate(reserved):
+            opts.reserved[i] = v
+    out = _vp()
+    st = _lib().ntt_plan_create(ctypes.byref(out), N, arr if primes else None, len(primes),
+                                ctypes.byref(opts))
+    return st, (int(out.value) if out.value else 0)
+
+
+def ntt_plan_destroy(plan: int) -> None:
+    _lib().ntt_plan_destroy(plan)
+
+
+def ntt_forward(plan: int, data, batch: int, stream=None) -> None:
+    _check(_lib().ntt_forward(plan, _addr(data), batch, _stream(stream, data)), "ntt_forward")
+
+
+def ntt_inverse(plan: int, data, batch: int, stream=None) -> None:
+    _check(_lib().ntt_inverse(plan, _addr(data), batch, _stream(stream, data)), "ntt_inverse")
+
+
+def ntt_forward_levels(plan: int, data, batch: int, levels: int, stream=None) -> None:
+    _check(_lib().ntt_forward_levels(plan, _addr(data), batch, levels, _stream(stream, data)),
+           "ntt_forward_levels")
+
+
+def ntt_inverse_levels(plan: int, data, batch: int, levels: int, stream=None) -> None:
+    _check(_lib().ntt_inverse_levels(plan, _addr(data), batch, levels, _stream(stream, data)),
+           "ntt_inverse_levels")
+
+
+def ntt_mul_pointwise(plan: int, a, b, c, batch: int, stream=None) -> None:
+    _check(_lib().ntt_mul_pointwise(plan, _addr(a), _addr(b), _addr(c), batch, _stream(stream, a)),
+           "ntt_mul_pointwise")
+
+
+def ntt_execute_host(plan: int, host_in, host_out, batch: int, ops: int, stream=None) -> None:
+    """host_in / host_out: numpy uint64 arrays or CPU torch tensors (pinned for speed)."""
+    def hp(x):
+        if hasattr(x, "ctypes"):
+            return x.ctypes.data
+        if hasattr(x, "data_ptr"):
+            return int(x.data_ptr())
+        return int(x)
+    _check(_lib().ntt_execute_host(plan, hp(host_in), hp(host_out), batch, ops, _stream(stream)),
+           "ntt_execute_host")
+
+
+def ntt_plan_query(plan: int) -> PlanInfo:
+    info = PlanInfo()
+    _check(_lib().ntt_plan_query(plan, ctypes.byref(info)), "ntt_plan_query")
+    return info
+
+
+def ntt_plan_psi(plan: int, l: int) -> int:
+    v = _u64()
+    _check(_lib().ntt_plan_psi(plan, l, ctypes.byref(v)), "ntt_plan_psi")
+    return int(v.value)
+
+
+def ntt_status_string(status: int) -> str:
+    return _lib().ntt_status_string(status).decode()
+
+
+def ntt_last_cuda_error() -> str:
+    return _lib().ntt_last_cuda_error().decode()
+
+
+class Plan:
+    """RAII wrapper over a plan handle."""
+
+    def __init__(self, N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0):
+        self.N = N
+        self.primes = [int(p) for p in primes]
+        self.L = len(self.primes)
+        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages)
+
+    def forward(self, data, batch: int = 1, stream=None):
+        ntt_forward(self.handle, data, batch, stream)
+
+    def inverse(self, data, batch: int = 1, stream=None):
+        ntt_inverse(self.handle, data, batch, stream)
+
+    def info(self) -> PlanInfo:
+        return ntt_plan_query(self.handle)
+
+    def close(self):
+        if self.handle:
+            ntt_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/ntt_gb300.h."""
+    import re
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^(?:ntt_status|void|const char\*)\s+(ntt_\w+)\s*\(", txt, re.M)))

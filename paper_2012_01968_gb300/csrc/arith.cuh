@@ -1,0 +1,178 @@
+// Modular arithmetic for the NTT kernels (device side).
+//
+// Word size 64 bit, primes 2^32 < q < 2^60 (the paper uses 2^59 < p < 2^60,
+// Sec. IV "32b vs. 64b word size").  Because q < 2^60, any value below 16q
+// fits in a word, so the butterflies keep values lazily in [0, X*q) for a
+// compile-time bound X <= 16 and reduce only when the bound would overflow.
+//
+// shoup_lazy is Shoup's modular multiplication (Algorithm 3) with the
+// quotient estimated from three 32x32-bit partial products instead of the
+// exact high word of the 128-bit product:
+//   qhat = yh*wh' + hi32(yh*wl') + hi32(yl*wh')   (w' = floor(w 2^64 / q))
+//   r    = lo64(y*w - qhat*q)
+// For every y < 2^64 and w < q the exact quotient floor(y w / q) exceeds qhat
+// by at most 3, so r lies in [0, 4q).  (Dropped: lo32 parts of both middle
+// products and the low product, each < 1 in units of 2^64, and < 1 from the
+// floor in w'.)
+#pragma once
+#include <stdint.h>
+
+namespace ntt {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+struct __align__(16) Tw {      // a twiddle and its Shoup companion
+    u64 w, wp;
+};
+
+__device__ __forceinline__ u32 lo32(u64 x) { return (u32)x; }
+__device__ __forceinline__ u32 hi32(u64 x) { return (u32)(x >> 32); }
+
+__device__ __forceinline__ u64 mul_wide(u32 a, u32 b) { return (u64)a * (u64)b; }
+
+// y * w mod q, result in [0, 4q), any 64-bit y.
+__device__ __forceinline__ u64 shoup_lazy(u64 y, u64 w, u64 wp, u64 q)
+{
+    const u32 yl = lo32(y), yh = hi32(y);
+    const u64 qhat = mul_wide(yh, hi32(wp)) + __umulhi(yh, lo32(wp)) + __umulhi(yl, hi32(wp));
+    return y * w - qhat * q;      // exact value < 4q, so the wrapped difference is it
+}
+
+// x mod q into [0, 3q) for any 64-bit x; mbar = floor(2^64 / q) < 2^32.
+__device__ __forceinline__ u64 reduce3(u64 x, u64 q, u32 mbar)
+{
+    // qh = floor(xh mbar / 2^32) is at most 2 below floor(x / q): [0, 3q)
+    const u32 qh = __umulhi(hi32(x), mbar);
+    return x - (u64)qh * q;
+}
+
+// x in [0, 2c) -> [0, c)
+__device__ __forceinline__ u64 csub(u64 x, u64 c) { return x >= c ? x - c : x; }
+
+// Bring x in [0, X q) to [0, q), X a compile-time bound <= 16.
+template <int X>
+__device__ __forceinline__ u64 canon(u64 x, u64 q, u32 mbar)
+{
+    static_assert(X >= 1 && X <= 16, "range");
+    if (X > 4) {
+        x = reduce3(x, q, mbar);            // [0, 3q)
+        x = csub(x, 2 * q);                 // [0, 2q)
+        return csub(x, q);
+    }
+    if (X > 2) x = csub(x, 2 * q);
+    if (X > 1) x = csub(x, q);
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Range bookkeeping for the forward (Cooley-Tukey) butterfly
+//   x' = x + t,  y' = x + 4q - t,   t = shoup_lazy(y, w) in [0, 4q)
+// Inputs of a stage lie in [0, X q); outputs in [0, (X + 4) q).  When X + 4
+// would exceed 16, the x operand is first reduced with reduce3 (to [0, 3q)),
+// so the outputs lie in [0, 7q).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr bool ct_reduces(int X) { return X + 4 > 16; }
+__host__ __device__ constexpr int ct_next(int X) { return ct_reduces(X) ? 7 : X + 4; }
+__host__ __device__ constexpr int ct_range_after(int X, int stages)
+{
+    return stages == 0 ? X : ct_range_after(ct_next(X), stages - 1);
+}
+
+template <int X>
+__device__ __forceinline__ void ct_bfly(u64& x, u64& y, const u64 w, const u64 wp,
+                                        const u64 q, const u64 q4, const u32 mbar)
+{
+    u64 a = x;
+    if (ct_reduces(X)) a = reduce3(a, q, mbar);
+    const u64 t = shoup_lazy(y, w, wp, q);
+    x = a + t;
+    y = a + q4 - t;
+}
+
+// same, with the twiddle applied as two factors (on-the-fly twiddling):
+// t = (y * w1) * w2, each a Shoup product
+template <int X>
+__device__ __forceinline__ void ct_bfly_ot(u64& x, u64& y, const Tw f1, const Tw f2,
+                                           const u64 q, const u64 q4, const u32 mbar)
+{
+    u64 a = x;
+    if (ct_reduces(X)) a = reduce3(a, q, mbar);
+    const u64 t = shoup_lazy(shoup_lazy(y, f1.w, f1.wp, q), f2.w, f2.wp, q);
+    x = a + t;
+    y = a + q4 - t;
+}
+
+// ---------------------------------------------------------------------------
+// Range bookkeeping for the inverse (Gentleman-Sande) butterfly
+//   x' = x + y,  y' = shoup_lazy(d, w)  with d = x - y + X q  (or y - x + X q
+//   when the twiddle is stored negated).
+// Inputs in [0, X q) need X <= 8 (x + y < 16 q).  y' is in [0, 4q); x' in
+// [0, 2X q) and is reduced with reduce3 when 2X > 8 so the next stage again
+// sees X <= 8.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr bool gs_reduces(int X) { return 2 * X > 8; }
+__host__ __device__ constexpr int gs_next(int X)
+{
+    return gs_reduces(X) ? 4 : (2 * X > 4 ? 2 * X : 4);
+}
+__host__ __device__ constexpr int gs_range_after(int X, int stages)
+{
+    return stages == 0 ? X : gs_range_after(gs_next(X), stages - 1);
+}
+
+// NEG: twiddle stored as -w (the forward table read backwards), so the
+// difference is taken as y - x.
+template <int X, bool NEG>
+__device__ __forceinline__ void gs_bfly(u64& x, u64& y, const u64 w, const u64 wp,
+                                        const u64 q, const u32 mbar)
+{
+    static_assert(X <= 8, "GS inputs must stay below 8q");
+    const u64 Xq = (u64)X * q;
+    const u64 d = NEG ? (y + Xq - x) : (x + Xq - y);
+    u64 s = x + y;
+    if (gs_reduces(X)) s = reduce3(s, q, mbar);
+    x = s;
+    y = shoup_lazy(d, w, wp, q);
+}
+
+template <int X, bool NEG>
+__device__ __forceinline__ void gs_bfly_ot(u64& x, u64& y, const Tw f1, const Tw f2,
+                                           const u64 q, const u32 mbar)
+{
+    static_assert(X <= 8, "GS inputs must stay below 8q");
+    const u64 Xq = (u64)X * q;
+    const u64 d = NEG ? (y + Xq - x) : (x + Xq - y);
+    u64 s = x + y;
+    if (gs_reduces(X)) s = reduce3(s, q, mbar);
+    x = s;
+    y = shoup_lazy(shoup_lazy(d, f1.w, f1.wp, q), f2.w, f2.wp, q);
+}
+
+// Last inverse stage with N^{-1} folded in:
+//   x' = (x + y) N^{-1},  y' = d * (w N^{-1});  both in [0, 4q).
+template <int X, bool NEG>
+__device__ __forceinline__ void gs_bfly_scaled(u64& x, u64& y, const Tw wn, const Tw ninv,
+                                               const u64 q)
+{
+    static_assert(X <= 8, "GS inputs must stay below 8q");
+    const u64 Xq = (u64)X * q;
+    const u64 d = NEG ? (y + Xq - x) : (x + Xq - y);
+    x = shoup_lazy(x + y, ninv.w, ninv.wp, q);
+    y = shoup_lazy(d, wn.w, wn.wp, q);
+}
+
+// Barrett product of two residues a, b < q (data times data, no companion;
+// Barrett, CRYPTO 1986).  k = bit length of q, mu = floor(2^{2k} / q) < 2^{k+1}:
+//   t = floor(ab / 2^{k-1}),  qhat = floor(t mu / 2^{k+1}),  r = ab - qhat q
+// and qhat is at most 2 below floor(ab / q), so r lies in [0, 3q).
+__device__ __forceinline__ u64 mulmod_barrett(u64 a, u64 b, u64 q, u64 mu, u32 k)
+{
+    const u64 lo = a * b, hi = __umul64hi(a, b);
+    const u64 t = (hi << (65 - k)) | (lo >> (k - 1));   // k in [33, 60]
+    const u64 plo = t * mu, phi = __umul64hi(t, mu);
+    const u64 qhat = (phi << (63 - k)) | (plo >> (k + 1));
+    return lo - qhat * q;
+}
+
+}  // namespace ntt

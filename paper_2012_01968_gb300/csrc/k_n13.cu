@@ -1,0 +1,8 @@
+// Two-pass kernels for N = 2^13: 6 column stages, then 7 row stages.
+#include "launch.cuh"
+
+namespace ntt {
+
+cudaError_t launch_n13(const LaunchCtx& c, bool fwd) { return launch_two_pass<6, 7, 5, 4>(c, fwd); }
+
+}  // namespace ntt

@@ -1,0 +1,8 @@
+// Two-pass kernels for N = 2^14: 7 column stages, then 7 row stages.
+#include "launch.cuh"
+
+namespace ntt {
+
+cudaError_t launch_n14(const LaunchCtx& c, bool fwd) { return launch_two_pass<7, 7, 5, 4>(c, fwd); }
+
+}  // namespace ntt

@@ -1,0 +1,233 @@
+// Plan creation: validate the primes, derive psi, build the device tables.
+//
+// Tables per prime q (paper: Sec. III-C Psi list, Algorithm 3 companions,
+// Sec. VII on-the-fly twiddling):
+//   tw[i]  = (Psi[i], floor(Psi[i] 2^64 / q)),  Psi[i] = psi^{brv(i)},  i < tw_len
+//            (tw_len = N in table mode; 2^{n - ot} with OT, since the last ot
+//            stages never read the table).  The inverse reads the same table:
+//            Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j].
+//   OT factors of the second pass (s0 = p1 first stage, p2 stages):
+//            Psi[2^s + (u << sl) + j] = A[2^sl + j] * B[sl][u],  s = s0 + sl,
+//            A[2^sl + j] = psi^{2^{n-sl} brv_sl(j)},
+//            B[sl][u]    = psi^{2^{n-1-s} (2 brv_s0(u) + 1)},
+//            and the same with psi^{-1} for the inverse.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "numtheory.h"
+#include "plan.h"
+
+using ntt::Tw;
+using ntt::PrimeDev;
+namespace nt = ntt::nt;
+
+extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
+
+namespace {
+
+struct HostTables {
+    std::vector<Tw> tw, ota_f, otb_f, ota_i, otb_i;
+    std::vector<PrimeDev> pd;
+};
+
+Tw make_tw(uint64_t w, uint64_t q) { return Tw{w, nt::shoup_companion(w, q)}; }
+
+void build_prime(const ntt_plan& p, uint32_t l, HostTables& h)
+{
+    const uint64_t q = p.primes[l], psi = p.psis[l];
+    const uint32_t N = p.N, n = p.n;
+    std::vector<uint64_t> pw(N);          // psi^e, e < N
+    pw[0] = 1;
+    for (uint32_t e = 1; e < N; ++e) pw[e] = nt::mulmod(pw[e - 1], psi, q);
+    auto fwd = [&](uint64_t e) { return pw[e]; };                          // e < N
+    auto inv = [&](uint64_t e) { return e == 0 ? 1 : q - pw[N - e]; };    // psi^{-e}, e < N
+
+    Tw* tw = h.tw.data() + (size_t)l * p.tw_len;
+    for (uint32_t i = 0; i < p.tw_len; ++i) tw[i] = make_tw(fwd(nt::brv(i, n)), q);
+
+    PrimeDev& d = h.pd[l];
+    d.q = q;
+    d.k = (uint32_t)nt::bitlen(q);
+    d.mu = (uint64_t)(((nt::u128)1 << (2 * d.k)) / q);
+    d.mbar = (uint32_t)((~(uint64_t)0) / q);       // floor((2^64 - 1)/q) = floor(2^64/q) for odd q
+    const uint64_t ninv = nt::powmod(N % q, q - 2, q);
+    d.ninv = make_tw(ninv, q);
+    const uint64_t psi_half = N >= 2 ? fwd(nt::brv(1, n)) : 1;   // Psi[1] = psi^{N/2}
+    d.w1ninv = make_tw(nt::mulmod(psi_half, ninv, q), q);
+
+    if (p.twiddle_mode == NTT_TWIDDLE_OT) {
+        const uint32_t s0 = p.p1, p2 = n - p.p1, R = 1u << p2;
+        Tw* af = h.ota_f.data() + (size_t)l * R;
+        Tw* ai = h.ota_i.data() + (size_t)l * R;
+        af[0] = ai[0] = make_tw(1, q);
+        for (uint32_t sl = 0; sl < p2; ++sl)
+            for (uint32_t j = 0; j < (1u << sl); ++j) {
+                const uint64_t e = ((uint64_t)nt::brv(j, sl)) << (n - sl);
+                af[(1u << sl) + j] = make_tw(fwd(e), q);
+                ai[(1u << sl) + j] = make_tw(inv(e), q);
+            }
+        const size_t bl = (size_t)p2 << s0;
+        Tw* bf = h.otb_f.data() + (size_t)l * bl;
+        Tw* bi = h.otb_i.data() + (size_t)l * bl;
+        for (uint32_t sl = 0; sl < p2; ++sl)
+            for (uint32_t u = 0; u < (1u << s0); ++u) {
+                const uint32_t s = s0 + sl;
+                const uint64_t e = ((uint64_t)(2 * nt::brv(u, s0) + 1)) << (n - 1 - s);
+                bf[((size_t)sl << s0) + u] = make_tw(fwd(e), q);
+                bi[((size_t)sl << s0) + u] = make_tw(inv(e), q);
+            }
+    }
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src, uint64_t& bytes)
+{
+    if (src.empty()) return cudaSuccess;
+    const size_t sz = src.size() * sizeof(T);
+    cudaError_t e = cudaMalloc(dst, sz);
+    if (e != cudaSuccess) return e;
+    bytes += sz;
+    return cudaMemcpy(*dst, src.data(), sz, cudaMemcpyHostToDevice);
+}
+
+void free_plan(ntt_plan* p)
+{
+    if (!p) return;
+    cudaFree(p->d_primes);
+    cudaFree(p->d_tw);
+    cudaFree(p->d_ota_f);
+    cudaFree(p->d_otb_f);
+    cudaFree(p->d_ota_i);
+    cudaFree(p->d_otb_i);
+    cudaFree(p->d_stage);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t* primes, uint32_t L,
+                                      const ntt_plan_opts* opts)
+{
+    if (!out || !primes || L == 0 || L > 4096) return NTT_ERR_INVALID_ARG;
+    if (N < 2 || N > (1u << 17) || (N & (N - 1))) return NTT_ERR_INVALID_ARG;
+    ntt_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    for (uint32_t r : o.reserved)
+        if (r) return NTT_ERR_INVALID_ARG;
+    if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
+    const uint32_t n = (uint32_t)__builtin_ctz(N);
+    const uint32_t p1 = (uint32_t)ntt::split_p1((int)n);
+    const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
+    uint32_t mode = o.twiddle_mode == NTT_TWIDDLE_AUTO ? NTT_TWIDDLE_TABLE : o.twiddle_mode;
+    uint32_t ots = 0;
+    if (mode == NTT_TWIDDLE_OT) {
+        ots = o.ot_stages ? o.ot_stages : 1;
+        if (ots > 2) return NTT_ERR_INVALID_ARG;
+        if (!two_pass) mode = NTT_TWIDDLE_TABLE, ots = 0;   // tables of <= 2^12 entries
+    } else if (o.ot_stages) {
+        return NTT_ERR_INVALID_ARG;
+    }
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint64_t q = primes[l];
+        if (q <= (1ull << 32) || q >= (1ull << 60)) return NTT_ERR_BAD_PRIME;
+        if ((q - 1) % (2ull * N) != 0) return NTT_ERR_BAD_PRIME;
+        if (!nt::is_prime(q)) return NTT_ERR_BAD_PRIME;
+    }
+
+    ntt_plan* p = new (std::nothrow) ntt_plan();
+    if (!p) return NTT_ERR_OOM;
+    p->N = N;
+    p->n = n;
+    p->L = L;
+    p->p1 = p1;
+    p->passes = two_pass ? 2 : 1;
+    p->twiddle_mode = mode;
+    p->ot_stages = ots;
+    cudaError_t ce = cudaGetDevice(&p->device);
+    if (ce != cudaSuccess) {
+        ntt_internal_set_cuda_error(ce);
+        delete p;
+        return NTT_ERR_CUDA;
+    }
+    p->primes.assign(primes, primes + L);
+    p->psis.resize(L);
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint64_t q = primes[l];
+        const uint64_t g = nt::smallest_generator(q);
+        p->psis[l] = nt::powmod(g, (q - 1) / (2ull * N), q);
+    }
+    p->tw_len = N >> ots;
+
+    HostTables h;
+    try {
+        h.tw.resize((size_t)L * p->tw_len);
+        h.pd.resize(L);
+        if (mode == NTT_TWIDDLE_OT) {
+            const size_t R = (size_t)1 << (n - p1), bl = (size_t)(n - p1) << p1;
+            h.ota_f.resize(L * R);
+            h.ota_i.resize(L * R);
+            h.otb_f.resize(L * bl);
+            h.otb_i.resize(L * bl);
+        }
+    } catch (...) {
+        delete p;
+        return NTT_ERR_OOM;
+    }
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const unsigned nth = std::min<unsigned>(hw, L);
+    if (nth <= 1 || (size_t)N * L < (1u << 16)) {
+        for (uint32_t l = 0; l < L; ++l) build_prime(*p, l, h);
+    } else {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nth; ++t)
+            th.emplace_back([&, t] {
+                for (uint32_t l = t; l < L; l += nth) build_prime(*p, l, h);
+            });
+        for (auto& t : th) t.join();
+    }
+
+    ce = upload(&p->d_primes, h.pd, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&p->d_tw, h.tw, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&p->d_ota_f, h.ota_f, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&p->d_otb_f, h.otb_f, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&p->d_ota_i, h.ota_i, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&p->d_otb_i, h.otb_i, p->device_bytes);
+    if (ce != cudaSuccess) {
+        ntt_internal_set_cuda_error(ce);
+        free_plan(p);
+        cudaGetLastError();
+        return ce == cudaErrorMemoryAllocation ? NTT_ERR_OOM : NTT_ERR_CUDA;
+    }
+    *out = p;
+    return NTT_OK;
+}
+
+extern "C" void ntt_plan_destroy(ntt_plan* plan) { free_plan(plan); }
+
+extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
+{
+    if (!p || !info) return NTT_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->N = p->N;
+    info->L = p->L;
+    info->log2_N = p->n;
+    info->passes = p->passes;
+    info->pass1_log2 = p->p1;
+    info->twiddle_mode = p->twiddle_mode;
+    info->ot_stages = p->ot_stages;
+    info->device = (uint32_t)p->device;
+    info->device_bytes = p->device_bytes;
+    return NTT_OK;
+}
+
+extern "C" ntt_status ntt_plan_psi(const ntt_plan* p, uint32_t l, uint64_t* psi)
+{
+    if (!p || !psi || l >= p->L) return NTT_ERR_INVALID_ARG;
+    *psi = p->psis[l];
+    return NTT_OK;
+}

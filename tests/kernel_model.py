@@ -1,0 +1,312 @@
+"""CPU model of the pass kernels' index math and lazy arithmetic (test only).
+
+Mirrors paper_2012_01968_gb300/csrc/ntt_pass.cuh and arith.cuh: the tile
+geometry, item decomposition, round schedule, twiddle indices (table and
+on-the-fly), the lazy Shoup product with its 3-partial-product quotient, the
+reduce3 step and the range bookkeeping, with every value checked against the
+bound the kernel assumes (below 2^64 and below X q).  Used to check the
+kernel design against the oracle on the CPU before it runs on a GPU.
+"""
+from __future__ import annotations
+
+M32 = (1 << 32) - 1
+M64 = (1 << 64) - 1
+
+
+def brv(i, bits):
+    r = 0
+    for _ in range(bits):
+        r = (r << 1) | (i & 1)
+        i >>= 1
+    return r
+
+
+def shoup_lazy(y, w, wp, q):
+    assert 0 <= y <= M64 and 0 <= w < q
+    yl, yh = y & M32, y >> 32
+    qhat = yh * (wp >> 32) + ((yh * (wp & M32)) >> 32) + ((yl * (wp >> 32)) >> 32)
+    r = (y * w - qhat * q) & M64
+    assert r < 4 * q and r % q == (y * w) % q
+    return r
+
+
+def reduce3(x, q, mbar):
+    assert 0 <= x <= M64
+    qh = ((x >> 32) * mbar) >> 32
+    r = x - qh * q
+    assert 0 <= r < 3 * q
+    return r
+
+
+def canon(x, X, q, mbar):
+    assert x < X * q
+    if X > 4:
+        x = reduce3(x, q, mbar)
+        x = x - 2 * q if x >= 2 * q else x
+        return x - q if x >= q else x
+    if X > 2:
+        x = x - 2 * q if x >= 2 * q else x
+    if X > 1:
+        x = x - q if x >= q else x
+    return x
+
+
+def ct_reduces(X):
+    return X + 4 > 16
+
+
+def ct_next(X):
+    return 7 if ct_reduces(X) else X + 4
+
+
+def gs_reduces(X):
+    return 2 * X > 8
+
+
+def gs_next(X):
+    return 4 if gs_reduces(X) else (2 * X if 2 * X > 4 else 4)
+
+
+def ct_after(X, k):
+    for _ in range(k):
+        X = ct_next(X)
+    return X
+
+
+def gs_after(X, k):
+    for _ in range(k):
+        X = gs_next(X)
+    return X
+
+
+def rounds(P, KMAX):
+    nr = (P + KMAX - 1) // KMAX
+    sizes = [P // nr + (1 if r < P % nr else 0) for r in range(nr)]
+    starts = [sum(sizes[:r]) for r in range(nr)]
+    return sizes, starts
+
+
+def swz(w):
+    return w ^ (((w >> 4) & 7) << 1)
+
+
+class PrimeTables:
+    """Tables for one prime, built as the plan builds them."""
+
+    def __init__(self, q, psi, n, p1, ots):
+        N = 1 << n
+        self.q, self.n, self.N = q, n, N
+        pw = [1] * N
+        for e in range(1, N):
+            pw[e] = pw[e - 1] * psi % q
+        fwd = lambda e: pw[e]
+        inv = lambda e: 1 if e == 0 else q - pw[N - e]
+        comp = lambda w: (w << 64) // q
+        self.tw_len = N >> ots
+        self.tw = [(fwd(brv(i, n)), comp(fwd(brv(i, n)))) for i in range(self.tw_len)]
+        self.mbar = M64 // q
+        ninv = pow(N, q - 2, q)
+        self.ninv = (ninv, comp(ninv))
+        w1 = fwd(brv(1, n)) if N >= 2 else 1
+        self.w1ninv = (w1 * ninv % q, comp(w1 * ninv % q))
+        p2 = n - p1
+        R = 1 << p2
+        self.ota_f = [(1, comp(1))] * R
+        self.ota_i = [(1, comp(1))] * R
+        for sl in range(p2):
+            for j in range(1 << sl):
+                e = brv(j, sl) << (n - sl)
+                self.ota_f[(1 << sl) + j] = (fwd(e), comp(fwd(e)))
+                self.ota_i[(1 << sl) + j] = (inv(e), comp(inv(e)))
+        s0 = p1
+        self.otb_f = [None] * (p2 << s0)
+        self.otb_i = [None] * (p2 << s0)
+        for sl in range(p2):
+            for u in range(1 << s0):
+                s = s0 + sl
+                e = (2 * brv(u, s0) + 1) << (n - 1 - s)
+                self.otb_f[(sl << s0) + u] = (fwd(e), comp(fwd(e)))
+                self.otb_i[(sl << s0) + u] = (inv(e), comp(inv(e)))
+
+
+def run_pass(data, T: PrimeTables, *, P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, s0):
+    """Apply one pass to one limb (list of ints) in place, tile by tile."""
+    n, q = T.n, T.q
+    N = 1 << n
+    R, C = 1 << P, 1 << LOGC
+    b = n - s0 - P
+    nb = n - s0
+    TILE = R * C
+    sizes, starts = rounds(P, KMAX)
+    NR = len(sizes)
+    tiles = N >> (P + LOGC)
+    seen = [0] * N
+    q4 = 4 * q
+    for tile in range(tiles):
+        if ROWS:
+            u_base, l0 = tile * C, 0
+        else:
+            per_u = (1 << b) >> LOGC
+            u_base, l0 = tile // per_u, (tile % per_u) * C
+        sm = [None] * TILE
+        # load
+        for i in range(TILE // 2):
+            if ROWS:
+                g = (u_base << P) + 2 * i
+                w = 2 * i
+            else:
+                VPR = C // 2
+                v, cv = i // VPR, i % VPR
+                g = (u_base << nb) + l0 + (v << b) + 2 * cv
+                w = v * C + 2 * cv
+            assert 0 <= g and g + 1 < N
+            sw = swz(w)
+            assert sw % 2 == 0 and sw + 1 < TILE
+            sm[sw], sm[sw + 1] = data[g], data[g + 1]
+            seen[g] += 1
+            seen[g + 1] += 1
+        order = range(NR) if FWD else range(NR - 1, -1, -1)
+        for r in order:
+            KR, K0 = sizes[r], starts[r]
+            E = 1 << KR
+            NLO = P - K0 - KR
+            if FWD:
+                XR = ct_after(XIN, K0)
+            else:
+                XR = gs_after(XIN, P - K0 - KR)
+            items = C << (P - KR)
+            canon_here = FINAL and ((FWD and r == NR - 1) or ((not FWD) and r == 0))
+            for it in range(items):
+                if ROWS:
+                    lo = it & ((1 << NLO) - 1)
+                    hi = (it >> NLO) & ((1 << K0) - 1)
+                    cc = it >> (NLO + K0)
+                    u = u_base + cc
+                else:
+                    cc = it & (C - 1)
+                    lo = (it >> LOGC) & ((1 << NLO) - 1)
+                    hi = it >> (LOGC + NLO)
+                    u = u_base
+                vbase = (hi << (P - K0)) | lo
+                idx = []
+                for i in range(E):
+                    v = vbase | (i << NLO)
+                    w = cc * R + v if ROWS else v * C + cc
+                    idx.append(swz(w))
+                x = [sm[j] for j in idx]
+                X = XR
+                ks = range(KR) if FWD else range(KR - 1, -1, -1)
+                if not FWD:
+                    # the inverse applies gs_next per executed stage, in order
+                    Xs = {}
+                    Xc = XR
+                    for k in ks:
+                        Xs[k] = Xc
+                        Xc = gs_next(Xc)
+                for k in ks:
+                    half = E >> (k + 1)
+                    sl = K0 + k
+                    ot = sl >= P - OTS
+                    if FWD:
+                        assert X + 4 <= 16 or ct_reduces(X)
+                    else:
+                        X = Xs[k]
+                        assert X <= 8
+                    if (not FWD) and HAS_S0 and K0 == 0 and k == 0:
+                        for i in range(half):
+                            a, bb = x[i], x[i + half]
+                            Xq = X * q
+                            d = bb + Xq - a
+                            assert a < Xq and bb < Xq
+                            x[i] = shoup_lazy(a + bb, T.ninv[0], T.ninv[1], q)
+                            x[i + half] = shoup_lazy(d, T.w1ninv[0], T.w1ninv[1], q)
+                        continue
+                    for pre in range(1 << k):
+                        jlo = (hi << k) | pre
+                        if ot:
+                            B = (T.otb_f if FWD else T.otb_i)[(sl << s0) + u]
+                            A = (T.ota_f if FWD else T.ota_i)[(1 << sl) + jlo]
+                        else:
+                            if FWD:
+                                ix = (1 << (s0 + sl)) + (u << sl) + jlo if not TW_SMEM else (1 << sl) + jlo
+                            else:
+                                j = (u << sl) + jlo if not TW_SMEM else jlo
+                                ix = ((2 << (s0 + sl)) - 1 - j) if not TW_SMEM else ((2 << sl) - 1 - j)
+                            assert 0 <= ix < (T.tw_len if not TW_SMEM else R)
+                            tw = T.tw[ix]
+                        for i in range(half):
+                            ia, ib = pre * 2 * half + i, pre * 2 * half + i + half
+                            a, bb = x[ia], x[ib]
+                            if FWD:
+                                assert a < X * q and bb < X * q
+                                if ct_reduces(X):
+                                    a = reduce3(a, q, T.mbar)
+                                t = shoup_lazy(shoup_lazy(bb, *B, q), *A, q) if ot else shoup_lazy(bb, tw[0], tw[1], q)
+                                x[ia] = a + t
+                                x[ib] = a + q4 - t
+                                assert x[ia] <= M64 and x[ib] <= M64
+                            else:
+                                Xq = X * q
+                                assert a < Xq and bb < Xq
+                                d = (a + Xq - bb) if ot else (bb + Xq - a)
+                                s = a + bb
+                                if gs_reduces(X):
+                                    s = reduce3(s, q, T.mbar)
+                                x[ia] = s
+                                x[ib] = shoup_lazy(shoup_lazy(d, *B, q), *A, q) if ot else shoup_lazy(d, tw[0], tw[1], q)
+                    if FWD:
+                        X = ct_next(X)
+                if canon_here:
+                    if FWD:
+                        x = [canon(v, ct_after(XIN, P), q, T.mbar) for v in x]
+                    else:
+                        x = [canon(v, 4 if HAS_S0 else gs_after(XIN, P), q, T.mbar) for v in x]
+                for j, v in zip(idx, x):
+                    sm[j] = v
+        # store
+        for i in range(TILE // 2):
+            if ROWS:
+                g, w = (u_base << P) + 2 * i, 2 * i
+            else:
+                VPR = C // 2
+                v, cv = i // VPR, i % VPR
+                g = (u_base << nb) + l0 + (v << b) + 2 * cv
+                w = v * C + 2 * cv
+            sw = swz(w)
+            data[g], data[g + 1] = sm[sw], sm[sw + 1]
+    assert all(s == 1 for s in seen), "every word loaded exactly once"
+
+
+def split(n):
+    if n <= 12:
+        return n, 0
+    p2 = (n + 1) // 2
+    return n - p2, p2
+
+
+def logc_rows(p2):
+    return min(5, 12 - p2)
+
+
+def transform(a, q, psi, n, fwd, ots=0):
+    """Whole transform as the library dispatches it (one limb)."""
+    data = [int(v) for v in a]
+    p1, p2 = split(n)
+    if p2 == 0:
+        T = PrimeTables(q, psi, n, n, 0)
+        run_pass(data, T, P=n, LOGC=0, KMAX=4, ROWS=True, FWD=fwd, XIN=1, FINAL=True, HAS_S0=True,
+                 OTS=0, TW_SMEM=False, s0=0)
+        return data
+    T = PrimeTables(q, psi, n, p1, ots)
+    LR = logc_rows(p2)
+    if fwd:
+        run_pass(data, T, P=p1, LOGC=4, KMAX=4, ROWS=False, FWD=True, XIN=1, FINAL=False, HAS_S0=True,
+                 OTS=0, TW_SMEM=True, s0=0)
+        run_pass(data, T, P=p2, LOGC=LR, KMAX=4, ROWS=True, FWD=True, XIN=ct_after(1, p1), FINAL=True,
+                 HAS_S0=False, OTS=ots, TW_SMEM=False, s0=p1)
+    else:
+        run_pass(data, T, P=p2, LOGC=LR, KMAX=4, ROWS=True, FWD=False, XIN=1, FINAL=False, HAS_S0=False,
+                 OTS=ots, TW_SMEM=False, s0=p1)
+        run_pass(data, T, P=p1, LOGC=4, KMAX=4, ROWS=False, FWD=False, XIN=gs_after(1, p2), FINAL=True,
+                 HAS_S0=True, OTS=0, TW_SMEM=True, s0=0)
+    return data

@@ -1,0 +1,216 @@
+"""CUDA path against the CPU oracle, element by element (bit-exact).
+
+Every call goes through the C ABI (ctypes binding); inputs are the seeded
+synthetic workloads of ntt_inputs.  Integer results: the bar is equality.
+"""
+import numpy as np
+import pytest
+
+import ntt_inputs as I
+from gpu_util import dev, host, oracle_fwd, oracle_inv
+
+torch = pytest.importorskip("torch")
+G = pytest.importorskip("paper_2012_01968_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.build()
+    G.lib()
+
+
+def _roundtrip_case(orc, N, primes, batch, seed, mode=G.NTT_TWIDDLE_TABLE, ots=0):
+    data = I.batch_uniform(seed, batch, primes, N)
+    with G.Plan(N, primes, mode, ots) as p:
+        d = dev(data)
+        p.forward(d, batch)
+        torch.cuda.synchronize()
+        got = host(d)
+        want = oracle_fwd(orc, data, primes)
+        assert np.array_equal(got, want), f"forward mismatch N={N} mode={mode} ots={ots}"
+        p.inverse(d, batch)
+        assert np.array_equal(host(d), data), "inverse(forward(x)) != x"
+        # inverse on input not produced by the forward (arbitrary NTT-domain data)
+        y = I.batch_uniform(seed + 1000, batch, primes, N)
+        dy = dev(y)
+        p.inverse(dy, batch)
+        assert np.array_equal(host(dy), oracle_inv(orc, y, primes)), "inverse mismatch"
+    return got
+
+
+def test_config1_n4096_single_limb(orc):
+    w = I.workload_c1()
+    _roundtrip_case(orc, w.N, w.primes, w.batch, w.seed)
+
+
+@pytest.mark.parametrize("n", list(range(1, 18)))
+def test_every_size_table_mode(orc, n):
+    N = 1 << n
+    primes = I.prime_chain(3, 2 * N)
+    _roundtrip_case(orc, N, primes, 2, 40 + n)
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+@pytest.mark.parametrize("ots", [1, 2])
+def test_ot_equals_table_and_oracle(orc, n, ots):
+    N = 1 << n
+    primes = I.prime_chain(2, 2 * N)
+    a = _roundtrip_case(orc, N, primes, 1, 70 + n, G.NTT_TWIDDLE_OT, ots)
+    b = _roundtrip_case(orc, N, primes, 1, 70 + n, G.NTT_TWIDDLE_TABLE)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode,ots", [(G.NTT_TWIDDLE_TABLE, 0), (G.NTT_TWIDDLE_OT, 1), (G.NTT_TWIDDLE_OT, 2)])
+def test_config2_full_size(orc, mode, ots):
+    w = I.workload_c2()
+    _roundtrip_case(orc, w.N, w.primes, w.batch, w.seed, mode, ots)
+
+
+def test_config3_full_size_and_product(orc):
+    w = I.workload_c3()
+    N, primes = w.N, w.primes
+    data = I.batch_uniform(w.seed, 2, primes, N)              # one ciphertext
+    with G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1) as p:
+        d = dev(data)
+        p.forward(d, 2)
+        torch.cuda.synchronize()
+        fwd = host(d)
+        assert np.array_equal(fwd, oracle_fwd(orc, data, primes))
+        p.inverse(d, 2)
+        assert np.array_equal(host(d), data)
+        # negacyclic product of two more polynomials: NTT, pointwise, iNTT
+        a = I.poly_uniform(w.seed, 2, primes, N)[None]
+        b = I.poly_uniform(w.seed, 3, primes, N)[None]
+        da, db = dev(a), dev(b)
+        p.forward(da, 1)
+        p.forward(db, 1)
+        G.ntt_mul_pointwise(p.handle, da, db, da, 1)
+        p.inverse(da, 1)
+        torch.cuda.synchronize()
+        c = host(da)
+    A = oracle_fwd(orc, a, primes)
+    B = oracle_fwd(orc, b, primes)
+    want = oracle_inv(orc, orc.pointwise_batch(A, B, primes), primes)
+    assert np.array_equal(c, want)
+    # sampled outputs checked one by one: c(x) = a(x) b(x) at roots of X^N + 1
+    rng = np.random.default_rng(3)
+    for l in rng.choice(len(primes), 3, replace=False):
+        q = primes[l]
+        psi = orc.psi(q, N)
+        for k in rng.choice(N, 2, replace=False):
+            x = pow(psi, 2 * int(k) + 1, q)
+            lhs = orc.eval(c[0, l], x, q)
+            rhs = orc.eval(a[0, l], x, q) * orc.eval(b[0, l], x, q) % q
+            assert lhs == rhs
+
+
+def test_edge_values(orc):
+    N = 1 << 14
+    primes = I.prime_chain(3, 2 * N)
+    q = np.array(primes, dtype=np.uint64)[:, None]
+    cases = [np.zeros((3, N), np.uint64), np.broadcast_to(q - np.uint64(1), (3, N)).copy()]
+    one = np.zeros((3, N), np.uint64)
+    one[:, 0] = 1
+    cases.append(one)
+    spike = np.zeros((3, N), np.uint64)
+    spike[:, N - 1] = (q[:, 0] - np.uint64(1))
+    cases.append(spike)
+    with G.Plan(N, primes) as p:
+        for data in cases:
+            d = dev(data[None])
+            p.forward(d, 1)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(d)[0], oracle_fwd(orc, data[None], primes)[0])
+            d2 = dev(data[None])
+            p.inverse(d2, 1)
+            assert np.array_equal(host(d2)[0], oracle_inv(orc, data[None], primes)[0])
+
+
+def test_many_limbs_grid_chunking(orc):
+    """batch * L above the 65535 grid-y limit is split into several launches."""
+    N = 1 << 4
+    primes = I.prime_chain(2, 2 * N)
+    batch = 33000                                   # 66000 limbs
+    data = I.batch_uniform(5, 4, primes, N)
+    data = np.tile(data, (batch // 4 + 1, 1, 1))[:batch]
+    with G.Plan(N, primes) as p:
+        d = dev(data)
+        p.forward(d, batch)
+        torch.cuda.synchronize()
+        got = host(d)
+    want = oracle_fwd(orc, data[:4], primes)
+    assert np.array_equal(got[-4:], oracle_fwd(orc, data[-4:], primes))
+    assert np.array_equal(got[:4], want)
+
+
+def test_levels_api(orc):
+    N = 1 << 15
+    primes = I.prime_chain(6, 2 * N)
+    data = I.batch_uniform(8, 2, primes[:4], N)
+    with G.Plan(N, primes) as p:
+        d = dev(data)
+        G.ntt_forward_levels(p.handle, d, 2, 4)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), oracle_fwd(orc, data, primes[:4]))
+        G.ntt_inverse_levels(p.handle, d, 2, 4)
+        assert np.array_equal(host(d), data)
+        with pytest.raises(G.NttError):
+            G.ntt_forward_levels(p.handle, d, 2, 7)
+
+
+def test_misaligned_pointer_rejected():
+    N = 1 << 12
+    primes = I.prime_chain(1, 2 * N)
+    buf = torch.zeros(N + 2, dtype=torch.int64, device="cuda")
+    with G.Plan(N, primes) as p:
+        st = G.lib().ntt_forward(p.handle, buf.data_ptr() + 8, 1, None)
+        assert st == G.NTT_ERR_MISALIGNED
+        assert G.lib().ntt_forward(p.handle, buf.data_ptr(), 0, None) == G.NTT_ERR_INVALID_ARG
+
+
+def test_nondefault_stream_and_pointwise(orc):
+    N = 1 << 16
+    primes = I.prime_chain(4, 2 * N)
+    a = I.batch_uniform(9, 1, primes, N)
+    b = I.batch_uniform(10, 1, primes, N)
+    s = torch.cuda.Stream()
+    with G.Plan(N, primes) as p:
+        with torch.cuda.stream(s):
+            da, db = dev(a), dev(b)
+            dc = torch.empty_like(da)
+            G.ntt_mul_pointwise(p.handle, da, db, dc, 1, s)
+            p.forward(dc, 1, s)
+        s.synchronize()
+        got = host(dc)
+    want = oracle_fwd(orc, orc.pointwise_batch(a, b, primes), primes)
+    assert np.array_equal(got, want)
+
+
+def test_execute_host_roundtrip(orc):
+    w = I.workload_c2()
+    primes = w.primes[:5]
+    data = I.batch_uniform(w.seed, 1, primes, w.N)
+    with G.Plan(w.N, primes) as p:
+        out = np.empty_like(data)
+        G.ntt_execute_host(p.handle, data, out, 1, G.NTT_OP_FORWARD)
+        assert np.array_equal(out, oracle_fwd(orc, data, primes))
+        back = np.empty_like(data)
+        G.ntt_execute_host(p.handle, out, back, 1, G.NTT_OP_INVERSE)
+        assert np.array_equal(back, data)
+        both = np.empty_like(data)
+        G.ntt_execute_host(p.handle, data, both, 1, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE)
+        assert np.array_equal(both, data)
+
+
+def test_plan_query_and_psi(orc):
+    w = I.workload_c2()
+    with G.Plan(w.N, w.primes[:3], G.NTT_TWIDDLE_OT, 2) as p:
+        info = p.info()
+        assert (info.N, info.L, info.log2_N, info.passes) == (w.N, 3, 16, 2)
+        assert info.twiddle_mode == G.NTT_TWIDDLE_OT and info.ot_stages == 2
+        for l in range(3):
+            assert G.ntt_plan_psi(p.handle, l) == orc.psi(w.primes[l], w.N)

@@ -1,0 +1,116 @@
+"""The CPU model of the pass kernels (index math, lazy ranges) against the oracle.
+
+Checks on the CPU, before any GPU run, that the kernels' tile geometry,
+round schedule, twiddle indexing (table and on-the-fly) and lazy reduction
+steps compute the oracle's transform, with every intermediate value inside the
+bound the kernel assumes.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import ntt_inputs as I
+import kernel_model as KM
+
+
+def _case(n, seed):
+    N = 1 << n
+    q = I.prime_chain(2, 2 * N)[seed % 2]
+    rng = random.Random(seed)
+    a = [rng.randrange(q) for _ in range(N)]
+    return N, q, a
+
+
+@pytest.mark.parametrize("n", list(range(1, 15)))
+def test_model_matches_oracle_table(orc, n):
+    N, q, a = _case(n, n)
+    psi = orc.psi(q, N)
+    want = orc.ntt_radix2(a, q)
+    got = KM.transform(a, q, psi, n, True)
+    assert got == [int(v) for v in want]
+    back = KM.transform(got, q, psi, n, False)
+    assert back == a
+    # inverse on arbitrary (not forward-produced) input, with edge values
+    y = list(a)
+    y[0], y[-1] = q - 1, 0
+    assert KM.transform(y, q, psi, n, False) == [int(v) for v in orc.intt_radix2(y, q)]
+
+
+@pytest.mark.parametrize("n,ots", [(13, 1), (13, 2), (14, 1), (14, 2)])
+def test_model_matches_oracle_ot(orc, n, ots):
+    N, q, a = _case(n, 100 + n)
+    psi = orc.psi(q, N)
+    got = KM.transform(a, q, psi, n, True, ots)
+    assert got == [int(v) for v in orc.ntt_radix2(a, q)]
+    assert KM.transform(got, q, psi, n, False, ots) == a
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,ots", [(15, 0), (16, 1), (17, 2)])
+def test_model_large_geometries(orc, n, ots):
+    N, q, a = _case(n, 200 + n)
+    psi = orc.psi(q, N)
+    got = KM.transform(a, q, psi, n, True, ots)
+    assert got == [int(v) for v in orc.ntt_radix2(a, q)]
+    assert KM.transform(got, q, psi, n, False, ots) == a
+
+
+def test_model_extreme_values(orc):
+    """All-(q-1) input keeps every lazy value in range (worst case for the bounds)."""
+    n = 13
+    N = 1 << n
+    q = I.prime_chain(1, 2 * N)[0]
+    psi = orc.psi(q, N)
+    a = [q - 1] * N
+    assert KM.transform(a, q, psi, n, True) == [int(v) for v in orc.ntt_radix2(a, q)]
+    assert KM.transform(a, q, psi, n, False) == [int(v) for v in orc.intt_radix2(a, q)]
+
+
+def test_swizzle_is_a_bijection_keeping_pairs():
+    for tile in (2, 64, 4096, 8192):
+        img = [KM.swz(w) for w in range(tile)]
+        assert sorted(img) == list(range(tile))
+        assert all(KM.swz(w) + 1 == KM.swz(w + 1) for w in range(0, tile, 2))
+
+
+@pytest.mark.parametrize("P,LOGC,rows", [(8, 4, True), (8, 4, False), (9, 3, True), (7, 5, True),
+                                          (7, 4, False), (6, 4, False), (12, 0, True)])
+def test_round_accesses_bank_conflicts(P, LOGC, rows):
+    """Shared-memory accesses of each round: at most 2-way bank conflicts.
+
+    For 8-byte accesses a half-warp (16 lanes) is served per 128-byte
+    wavefront: conflict-free iff the 16 word addresses are distinct mod 16.
+    Rounds whose items are contiguous (rows, last round) use 16-byte accesses:
+    a quarter-warp per wavefront, distinct 16-byte chunks mod 8.
+    """
+    sizes, starts = KM.rounds(P, 4)
+    R, C = 1 << P, 1 << LOGC
+    worst = 1
+    for KR, K0 in zip(sizes, starts):
+        NLO = P - K0 - KR
+        E = 1 << KR
+        pairs = rows and NLO == 0
+        T = C << (P - sizes[0])
+        for warp0 in range(0, min(T, 256), 32):
+            lanes = range(warp0, min(warp0 + 32, T))
+            for i in range(0, E, 2 if pairs else 1):
+                addrs = []
+                for it in lanes:
+                    if rows:
+                        lo = it & ((1 << NLO) - 1)
+                        hi = (it >> NLO) & ((1 << K0) - 1)
+                        cc = it >> (NLO + K0)
+                    else:
+                        cc = it & (C - 1)
+                        lo = (it >> LOGC) & ((1 << NLO) - 1)
+                        hi = it >> (LOGC + NLO)
+                    v = ((hi << (P - K0)) | lo) | (i << NLO)
+                    w = cc * R + v if rows else v * C + cc
+                    addrs.append(KM.swz(w))
+                group = 8 if pairs else 16
+                for g0 in range(0, len(addrs), group):
+                    grp = addrs[g0:g0 + group]
+                    keys = [(a >> 1) % 8 for a in grp] if pairs else [a % 16 for a in grp]
+                    worst = max(worst, max(keys.count(k) for k in set(keys)))
+    assert worst <= 2, worst
