@@ -23,9 +23,16 @@
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
  * default stream).  Device calls are asynchronous and stream-ordered; argument
- * errors are returned synchronously before anything is enqueued.  A plan is
- * immutable after creation and may be used from several host threads and
- * streams at once.  All calls must run with the plan's device current.
+ * errors are returned synchronously before anything is enqueued.  All calls
+ * must run with the plan's device current.
+ *
+ * Concurrency: a plan owns one device work area (dependency counters of the
+ * one-launch two-pass kernel, for N >= 2^13) and one host staging buffer.
+ * Transform calls on one plan must therefore be ordered: issue them on one
+ * stream, or order the streams with events.  Two plans are independent.  The
+ * work area is sized at plan creation for batch 16; a call with a larger
+ * batch * L grows it (a device synchronisation and an allocation), so make
+ * one call at the largest batch before capturing calls into a CUDA graph.
  *
  * Errors: every call returns an ntt_status; NTT_OK is 0.  On error nothing is
  * enqueued and output arguments are left untouched.
@@ -64,10 +71,20 @@ enum {
     NTT_TWIDDLE_OT = 2
 };
 
+/* Kernel organisation for two-pass sizes (N >= 2^13): one persistent launch
+ * that runs both passes with per-limb dependency counters (FUSED, the
+ * default), or one launch per pass (PER_PASS).  Results are identical. */
+enum {
+    NTT_KERNEL_AUTO = 0,
+    NTT_KERNEL_FUSED = 1,
+    NTT_KERNEL_PER_PASS = 2
+};
+
 typedef struct ntt_plan_opts {
     uint32_t twiddle_mode;    /* NTT_TWIDDLE_*; AUTO picks per N */
     uint32_t ot_stages;       /* OT: final stages built on the fly, 1 or 2 (0 = 1) */
-    uint32_t reserved[6];     /* must be zero */
+    uint32_t kernel;          /* NTT_KERNEL_* */
+    uint32_t reserved[5];     /* must be zero */
 } ntt_plan_opts;
 
 /*
@@ -77,8 +94,8 @@ typedef struct ntt_plan_opts {
  *            2^32 < q < 2^60 (copied; the caller keeps ownership).
  *   L      : 1 <= L <= 4096.
  *   opts   : NULL for defaults.
- * The plan (host object and device tables, 16 * N * L bytes in table mode)
- * belongs to the library until ntt_plan_destroy.  It is created on the
+ * The plan (host object, device tables of 16 * N * L bytes in table mode, and
+ * the work area) belongs to the library until ntt_plan_destroy.  It is created on the
  * current CUDA device.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME,
  * NTT_ERR_OOM, NTT_ERR_CUDA; *out is left untouched on error.
  * (Paper: the precomputed tables of Sec. IV "Precomputed table size with
@@ -94,9 +111,11 @@ void ntt_plan_destroy(ntt_plan* plan);
  * In-place forward transform of `batch` polynomials at device address `data`
  * (layout [batch][L][N], 16-byte aligned, caller-owned).  Input in natural
  * coefficient order, output in bit-reversed order (Algorithm 1).  All
- * batch * L limbs run in one launch per pass (batching, Sec. V / VI-A).
+ * batch * L limbs run in one launch (N <= 2^12, or the fused two-pass kernel)
+ * or one launch per pass (PER_PASS) (batching, Sec. V / VI-A).
  * Errors: NTT_ERR_INVALID_ARG (NULL, batch == 0), NTT_ERR_MISALIGNED,
- * NTT_ERR_CUDA (launch failure).
+ * NTT_ERR_OOM (growing the plan's work area failed), NTT_ERR_CUDA (launch
+ * failure).
  */
 ntt_status ntt_forward(const ntt_plan* plan, uint64_t* data, uint32_t batch, void* stream);
 
@@ -148,10 +167,19 @@ typedef struct ntt_plan_info {
     uint32_t twiddle_mode;    /* NTT_TWIDDLE_TABLE or NTT_TWIDDLE_OT */
     uint32_t ot_stages;       /* OT: final stages built on the fly */
     uint32_t device;          /* CUDA device ordinal */
+    uint32_t kernel;          /* NTT_KERNEL_FUSED or NTT_KERNEL_PER_PASS */
     uint64_t device_bytes;    /* device memory held by the plan (tables) */
 } ntt_plan_info;
 
 ntt_status ntt_plan_query(const ntt_plan* plan, ntt_plan_info* info);
+
+/*
+ * Device status word of the plan: bit 0 set when a bounded wait for a
+ * dependency of the fused kernel ran out, bit 1 when a bounded wait for a
+ * tile copy ran out (results of that call are then invalid).  Synchronises
+ * the device, reads the word into *status and clears it.
+ */
+ntt_status ntt_plan_device_status(const ntt_plan* plan, uint32_t* status);
 
 /* psi for prime l (0 <= l < L) of the plan, into *psi. */
 ntt_status ntt_plan_psi(const ntt_plan* plan, uint32_t l, uint64_t* psi);

@@ -33,6 +33,10 @@ NTT_TWIDDLE_AUTO = 0
 NTT_TWIDDLE_TABLE = 1
 NTT_TWIDDLE_OT = 2
 
+NTT_KERNEL_AUTO = 0
+NTT_KERNEL_FUSED = 1
+NTT_KERNEL_PER_PASS = 2
+
 NTT_OP_FORWARD = 1
 NTT_OP_INVERSE = 2
 
@@ -41,13 +45,13 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("reserved", _u32 * 6)]
+    _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("kernel", _u32), ("reserved", _u32 * 5)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("N", _u32), ("L", _u32), ("log2_N", _u32), ("passes", _u32),
                 ("pass1_log2", _u32), ("twiddle_mode", _u32), ("ot_stages", _u32),
-                ("device", _u32), ("device_bytes", _u64)]
+                ("device", _u32), ("kernel", _u32), ("device_bytes", _u64)]
 
 
 class NttError(RuntimeError):
@@ -95,6 +99,8 @@ def _lib():
             L.ntt_execute_host.argtypes = [_vp, _vp, _vp, _u32, _u32, _vp]
             L.ntt_plan_query.restype = S
             L.ntt_plan_query.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
+            L.ntt_plan_device_status.restype = S
+            L.ntt_plan_device_status.argtypes = [_vp, ctypes.POINTER(_u32)]
             L.ntt_plan_psi.restype = S
             L.ntt_plan_psi.argtypes = [_vp, _u32, _u64p]
             L.ntt_status_string.restype = ctypes.c_char_p
@@ -148,22 +154,24 @@ def _check(st: int, where: str):
 # --------------------------------------------------------------------------
 # C ABI, same names
 # --------------------------------------------------------------------------
-def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0) -> int:
+def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
+                    kernel: int = NTT_KERNEL_AUTO) -> int:
     """Create a plan; returns the opaque handle (an int).  Raises NttError."""
     primes = [int(p) for p in primes]
     arr = (_u64 * len(primes))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel)
     out = _vp()
     _check(_lib().ntt_plan_create(ctypes.byref(out), N, arr, len(primes), ctypes.byref(opts)),
            "ntt_plan_create")
     return int(out.value)
 
 
-def ntt_plan_create_status(N: int, primes, twiddle_mode: int = 0, ot_stages: int = 0, reserved=None):
+def ntt_plan_create_status(N: int, primes, twiddle_mode: int = 0, ot_stages: int = 0, reserved=None,
+                           kernel: int = 0):
     """Like ntt_plan_create but returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
     arr = (_u64 * max(1, len(primes)))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel)
     if reserved:
         for i, v in enumerate(reserved):
             opts.reserved[i] = v
@@ -218,6 +226,12 @@ def ntt_plan_query(plan: int) -> PlanInfo:
     return info
 
 
+def ntt_plan_device_status(plan: int) -> int:
+    v = _u32()
+    _check(_lib().ntt_plan_device_status(plan, ctypes.byref(v)), "ntt_plan_device_status")
+    return int(v.value)
+
+
 def ntt_plan_psi(plan: int, l: int) -> int:
     v = _u64()
     _check(_lib().ntt_plan_psi(plan, l, ctypes.byref(v)), "ntt_plan_psi")
@@ -235,11 +249,12 @@ def ntt_last_cuda_error() -> str:
 class Plan:
     """RAII wrapper over a plan handle."""
 
-    def __init__(self, N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0):
+    def __init__(self, N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
+                 kernel: int = NTT_KERNEL_AUTO):
         self.N = N
         self.primes = [int(p) for p in primes]
         self.L = len(self.primes)
-        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages)
+        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel)
 
     def forward(self, data, batch: int = 1, stream=None):
         ntt_forward(self.handle, data, batch, stream)
@@ -249,6 +264,9 @@ class Plan:
 
     def info(self) -> PlanInfo:
         return ntt_plan_query(self.handle)
+
+    def device_status(self) -> int:
+        return ntt_plan_device_status(self.handle)
 
     def close(self):
         if self.handle:

@@ -38,8 +38,15 @@ def _headers_mtime() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
+def _obj_dir(extra: list[str]) -> str:
+    if not extra:
+        return OBJ_DIR
+    import hashlib
+    return os.path.join(OBJ_DIR, hashlib.sha1(" ".join(extra).encode()).hexdigest()[:10])
+
+
 def _compile(src: str, extra: list[str], verbose: bool) -> str:
-    obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
+    obj = os.path.join(_obj_dir(extra), os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
@@ -55,14 +62,21 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
 
 
 def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None) -> str:
-    """Compile and link the library; returns the path of the .so."""
+    """Compile and link the library; returns the path of the .so.
+
+    `extra` adds nvcc flags (e.g. -DNTT_KMAX=3); objects of each flag set are
+    kept apart, and the library is relinked whenever the flag set changes.
+    """
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    os.makedirs(_obj_dir(extra or []), exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra or [], verbose), srcs))
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
+    stamp = LIB + ".flags"
+    flags = " ".join(extra or [])
+    same = os.path.exists(stamp) and open(stamp).read() == flags
+    if same and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
@@ -72,6 +86,8 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | Non
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(flags)
     return LIB
 
 

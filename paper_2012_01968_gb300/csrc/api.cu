@@ -11,6 +11,8 @@ namespace {
 thread_local char g_cuda_err[256] = "no error";
 }
 
+cudaError_t ntt_internal_grow_work(ntt_plan* p, uint32_t limbs);
+
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e)
 {
     std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -87,6 +89,10 @@ ntt_status transform(const ntt_plan* p, uint64_t* data, uint32_t batch, uint32_t
     if (!aligned16(data)) return NTT_ERR_MISALIGNED;
     const uint64_t limbs = (uint64_t)batch * levels;
     if (limbs > 0xFFFFFFFFull) return NTT_ERR_INVALID_ARG;
+    if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED && p->work_limbs < limbs) {
+        cudaError_t e = ntt_internal_grow_work(const_cast<ntt_plan*>(p), (uint32_t)limbs);
+        if (e != cudaSuccess) return to_status(e);
+    }
     const ntt::LaunchCtx c = p->ctx(data, (uint32_t)limbs, levels, (cudaStream_t)stream);
     return to_status(ntt::launch_transform(c, fwd));
 }
@@ -157,6 +163,10 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
     }
     e = cudaMemcpyAsync(p->d_stage, host_in, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return to_status(e);
+    if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED && p->work_limbs < batch * p->L) {
+        e = ntt_internal_grow_work(p, batch * p->L);
+        if (e != cudaSuccess) return to_status(e);
+    }
     const ntt::LaunchCtx c = p->ctx(p->d_stage, batch * p->L, p->L, s);
     if (ops & NTT_OP_FORWARD) {
         e = ntt::launch_transform(c, true);

@@ -39,6 +39,40 @@ __device__ __forceinline__ u64 shoup_lazy(u64 y, u64 w, u64 wp, u64 q)
     return y * w - qhat * q;      // exact value < 4q, so the wrapped difference is it
 }
 
+// The same product with the quotient's two middle partial products taken
+// whole (IMAD.WIDE, half rate on sm_103a, where IMAD.HI is quarter rate) and
+// summed with their carry:
+//   qhat = yh*wh' + floor((yh*wl' + yl*wh') / 2^32)
+//   r    = lo64(y*w + qhat*(2^64 - q))
+// Only yl*wl' (< 2^64) is dropped, so floor(y w / q) - qhat <= 2 and r lies in
+// [0, 3q) for every y < 2^64.  nq = 2^64 - q.
+__device__ __forceinline__ u64 shoup3(u64 y, u64 w, u64 wp, u64 nq)
+{
+    const u32 yl = lo32(y), yh = hi32(y), wl = lo32(wp), wh = hi32(wp);
+    u64 t1, t2;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(t1) : "r"(yh), "r"(wl));
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(t2) : "r"(yl), "r"(wh));
+    u32 mid_hi, carry;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %2, %3;\n\t"
+        "addc.cc.u32 %0, %4, %5;\n\t"
+        "addc.u32 %1, 0, 0;\n\t}"
+        : "=r"(mid_hi), "=r"(carry)
+        : "r"(lo32(t1)), "r"(lo32(t2)), "r"(hi32(t1)), "r"(hi32(t2)));
+    u64 qhat;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(qhat) : "r"(yh), "r"(wh), "l"(((u64)carry << 32) | mid_hi));
+    return y * w + qhat * nq;
+}
+
+// x mod q into [0, 3q) for any 64-bit x, the quotient estimate taken from a
+// whole 32x32 product (see shoup3).  zero must be a run-time 0.
+__device__ __forceinline__ u64 reduce3w(u64 x, u64 nq, u32 mbar, u64 zero)
+{
+    u64 p;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(p) : "r"(hi32(x)), "r"(mbar), "l"(zero));
+    return x + (u64)hi32(p) * nq;
+}
+
 // x mod q into [0, 3q) for any 64-bit x; mbar = floor(2^64 / q) < 2^32.
 __device__ __forceinline__ u64 reduce3(u64 x, u64 q, u32 mbar)
 {
@@ -69,11 +103,13 @@ __device__ __forceinline__ u64 canon(u64 x, u64 q, u32 mbar)
 // Range bookkeeping for the forward (Cooley-Tukey) butterfly
 //   x' = x + t,  y' = x + 4q - t,   t = shoup_lazy(y, w) in [0, 4q)
 // Inputs of a stage lie in [0, X q); outputs in [0, (X + 4) q).  When X + 4
-// would exceed 16, the x operand is first reduced with reduce3 (to [0, 3q)),
-// so the outputs lie in [0, 7q).
+// would exceed 16, the x operand is first brought below 8q by one
+// conditional subtraction of 8q (integer ALU work, which leaves the multiply
+// pipe to the Shoup products), so the outputs lie in [0, 12q).  From a
+// canonical input the bounds run 1, 5, 9, 13, 12, 16, 12, 16, ...
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr bool ct_reduces(int X) { return X + 4 > 16; }
-__host__ __device__ constexpr int ct_next(int X) { return ct_reduces(X) ? 7 : X + 4; }
+__host__ __device__ constexpr int ct_next(int X) { return ct_reduces(X) ? 12 : X + 4; }
 __host__ __device__ constexpr int ct_range_after(int X, int stages)
 {
     return stages == 0 ? X : ct_range_after(ct_next(X), stages - 1);
@@ -84,7 +120,7 @@ __device__ __forceinline__ void ct_bfly(u64& x, u64& y, const u64 w, const u64 w
                                         const u64 q, const u64 q4, const u32 mbar)
 {
     u64 a = x;
-    if (ct_reduces(X)) a = reduce3(a, q, mbar);
+    if (ct_reduces(X)) a = csub(a, q4 << 1);
     const u64 t = shoup_lazy(y, w, wp, q);
     x = a + t;
     y = a + q4 - t;
@@ -97,7 +133,7 @@ __device__ __forceinline__ void ct_bfly_ot(u64& x, u64& y, const Tw f1, const Tw
                                            const u64 q, const u64 q4, const u32 mbar)
 {
     u64 a = x;
-    if (ct_reduces(X)) a = reduce3(a, q, mbar);
+    if (ct_reduces(X)) a = csub(a, q4 << 1);
     const u64 t = shoup_lazy(shoup_lazy(y, f1.w, f1.wp, q), f2.w, f2.wp, q);
     x = a + t;
     y = a + q4 - t;
@@ -108,13 +144,14 @@ __device__ __forceinline__ void ct_bfly_ot(u64& x, u64& y, const Tw f1, const Tw
 //   x' = x + y,  y' = shoup_lazy(d, w)  with d = x - y + X q  (or y - x + X q
 //   when the twiddle is stored negated).
 // Inputs in [0, X q) need X <= 8 (x + y < 16 q).  y' is in [0, 4q); x' in
-// [0, 2X q) and is reduced with reduce3 when 2X > 8 so the next stage again
-// sees X <= 8.
+// [0, 2X q) and, when 2X > 8, is brought below 8q by one conditional
+// subtraction of 8q, so the next stage again sees X <= 8.  From a canonical
+// input the bounds run 1, 4, 8, 8, 8, ...
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr bool gs_reduces(int X) { return 2 * X > 8; }
 __host__ __device__ constexpr int gs_next(int X)
 {
-    return gs_reduces(X) ? 4 : (2 * X > 4 ? 2 * X : 4);
+    return gs_reduces(X) ? 8 : (2 * X > 4 ? 2 * X : 4);
 }
 __host__ __device__ constexpr int gs_range_after(int X, int stages)
 {
@@ -131,7 +168,7 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, const u64 w, const u64 w
     const u64 Xq = (u64)X * q;
     const u64 d = NEG ? (y + Xq - x) : (x + Xq - y);
     u64 s = x + y;
-    if (gs_reduces(X)) s = reduce3(s, q, mbar);
+    if (gs_reduces(X)) s = csub(s, q << 3);
     x = s;
     y = shoup_lazy(d, w, wp, q);
 }
@@ -144,7 +181,7 @@ __device__ __forceinline__ void gs_bfly_ot(u64& x, u64& y, const Tw f1, const Tw
     const u64 Xq = (u64)X * q;
     const u64 d = NEG ? (y + Xq - x) : (x + Xq - y);
     u64 s = x + y;
-    if (gs_reduces(X)) s = reduce3(s, q, mbar);
+    if (gs_reduces(X)) s = csub(s, q << 3);
     x = s;
     y = shoup_lazy(shoup_lazy(d, f1.w, f1.wp, q), f2.w, f2.wp, q);
 }

@@ -1,0 +1,64 @@
+// Host helpers for the fused launch: tensor maps and per-launch scratch.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "plan.h"
+
+namespace ntt {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+cudaError_t encode_2d(CUtensorMap* m, void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                      uint32_t box_inner, uint32_t box_outer)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// Column view: [N1 * limbs rows][N2 words], box 16 words x R1 rows.
+// Row view:    [N / 16 * limbs lines][16 words], box 16 words x row_tile/16 lines.
+cudaError_t encode_tile_maps(const LaunchCtx& c, int p1, int row_tile_words, CUtensorMap* mapC, CUtensorMap* mapR)
+{
+    const uint64_t N = 1ull << c.n, N1 = 1ull << p1, N2 = N >> p1;
+    cudaError_t e = encode_2d(mapC, c.data, N2, N1 * c.limbs, N2 * 8, 16, (uint32_t)N1);
+    if (e != cudaSuccess) return e;
+    return encode_2d(mapR, c.data, 16, (N / 16) * c.limbs, 128, 16, (uint32_t)(row_tile_words / 16));
+}
+
+int device_sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace ntt

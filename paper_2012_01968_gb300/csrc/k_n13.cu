@@ -3,6 +3,6 @@
 
 namespace ntt {
 
-cudaError_t launch_n13(const LaunchCtx& c, bool fwd) { return launch_two_pass<6, 7, 5, 4>(c, fwd); }
+cudaError_t launch_n13(const LaunchCtx& c, bool fwd) { return launch_two_pass<6, 7, 5, KMAX_ALL>(c, fwd); }
 
 }  // namespace ntt

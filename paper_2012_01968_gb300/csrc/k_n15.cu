@@ -3,6 +3,6 @@
 
 namespace ntt {
 
-cudaError_t launch_n15(const LaunchCtx& c, bool fwd) { return launch_two_pass<7, 8, 4, 4>(c, fwd); }
+cudaError_t launch_n15(const LaunchCtx& c, bool fwd) { return launch_two_pass<7, 8, 4, KMAX_ALL>(c, fwd); }
 
 }  // namespace ntt

@@ -3,6 +3,6 @@
 
 namespace ntt {
 
-cudaError_t launch_n17(const LaunchCtx& c, bool fwd) { return launch_two_pass<8, 9, 3, 4>(c, fwd); }
+cudaError_t launch_n17(const LaunchCtx& c, bool fwd) { return launch_two_pass<8, 9, 3, KMAX_ALL>(c, fwd); }
 
 }  // namespace ntt

@@ -4,6 +4,7 @@
 
 #include <mutex>
 
+#include "ntt_fused.cuh"
 #include "ntt_pass.cuh"
 #include "plan.h"
 
@@ -52,8 +53,8 @@ template <int N_LOG>
 cudaError_t launch_single_n(const LaunchCtx& c, bool fwd)
 {
     if (fwd)
-        return launch_pass<N_LOG, 0, 4, true, true, 1, true, true, 0, false>(c, 0, nullptr, nullptr);
-    return launch_pass<N_LOG, 0, 4, true, false, 1, true, true, 0, false>(c, 0, nullptr, nullptr);
+        return launch_pass<N_LOG, 0, KMAX_ALL, true, true, 1, true, true, 0, false>(c, 0, nullptr, nullptr);
+    return launch_pass<N_LOG, 0, KMAX_ALL, true, false, 1, true, true, 0, false>(c, 0, nullptr, nullptr);
 }
 
 // Two passes: P1 column-like stages [0, P1), then P2 row-like stages.
@@ -61,7 +62,7 @@ template <int P1, int P2, int LOGC_R, int KMAX_R, int OTS>
 cudaError_t launch_two_pass_ots(const LaunchCtx& c, bool fwd)
 {
     constexpr int LOGC_C = 4;
-    constexpr int KMAX_C = 4;
+    constexpr int KMAX_C = KMAX_R;
     cudaError_t e;
     if (fwd) {
         e = launch_pass<P1, LOGC_C, KMAX_C, false, true, 1, false, true, 0, true>(c, 0, nullptr, nullptr);
@@ -75,13 +76,70 @@ cudaError_t launch_two_pass_ots(const LaunchCtx& c, bool fwd)
     return launch_pass<P1, LOGC_C, KMAX_C, false, false, X1, true, true, 0, true>(c, 0, nullptr, nullptr);
 }
 
+// host helpers for the fused launch (fused_host.cu)
+cudaError_t encode_tile_maps(const LaunchCtx& c, int p1, int row_tile_words, CUtensorMap* mapC, CUtensorMap* mapR);
+int device_sm_count();
+
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS>
+cudaError_t launch_fused_dir(const LaunchCtx& c)
+{
+    using F = FusedCfg<P1, P2, LOGC_R, KMAX>;
+    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int occ = 0;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, F::THREADS, F::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    if (!c.work || c.work_limbs < c.limbs) return cudaErrorInvalidValue;
+    CUtensorMap mapC, mapR;
+    cudaError_t e = encode_tile_maps(c, P1, F::TILE_R, &mapC, &mapR);
+    if (e != cudaSuccess) return e;
+    constexpr u32 UC = F::R2 / 16, UR = F::R1 / F::CR;
+    const u64 units = (u64)c.limbs * (UC + UR);
+    const u64 slots = (u64)device_sm_count() * (u64)occ;
+    const u32 grid = (u32)(units < slots ? units : slots);
+    FusedArgs a;
+    a.primes = c.primes;
+    a.tw = c.tw;
+    a.ota = FWD ? c.ota_f : c.ota_i;
+    a.otb = FWD ? c.otb_f : c.otb_i;
+    a.ctl = c.work;
+    a.status = c.status;
+    a.tw_len = c.tw_len;
+    a.L = c.L;
+    a.limbs = c.limbs;
+    a.max_polls = 1u << 22;
+    kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(mapC, mapR, a);
+    return cudaGetLastError();
+}
+
+template <int P1, int P2, int LOGC_R, int KMAX, int OTS>
+cudaError_t launch_fused(const LaunchCtx& c, bool fwd)
+{
+    return fwd ? launch_fused_dir<P1, P2, LOGC_R, KMAX, true, OTS>(c)
+               : launch_fused_dir<P1, P2, LOGC_R, KMAX, false, OTS>(c);
+}
+
 template <int P1, int P2, int LOGC_R, int KMAX_R>
 cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
 {
+    if (c.separate_passes) {
+        switch (c.ots) {
+        case 0: return launch_two_pass_ots<P1, P2, LOGC_R, KMAX_R, 0>(c, fwd);
+        case 1: return launch_two_pass_ots<P1, P2, LOGC_R, KMAX_R, 1>(c, fwd);
+        case 2: return launch_two_pass_ots<P1, P2, LOGC_R, KMAX_R, 2>(c, fwd);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (c.ots) {
-    case 0: return launch_two_pass_ots<P1, P2, LOGC_R, KMAX_R, 0>(c, fwd);
-    case 1: return launch_two_pass_ots<P1, P2, LOGC_R, KMAX_R, 1>(c, fwd);
-    case 2: return launch_two_pass_ots<P1, P2, LOGC_R, KMAX_R, 2>(c, fwd);
+    case 0: return launch_fused<P1, P2, LOGC_R, KMAX_R, 0>(c, fwd);
+    case 1: return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(c, fwd);
+    case 2: return launch_fused<P1, P2, LOGC_R, KMAX_R, 2>(c, fwd);
     default: return cudaErrorInvalidValue;
     }
 }

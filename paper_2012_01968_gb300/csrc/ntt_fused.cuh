@@ -1,0 +1,353 @@
+// Both passes of a two-pass transform in one persistent launch.
+//
+// Work unit = one tile of one pass of one limb.  The first-executed pass (A)
+// of a limb has no dependencies; a tile of the second pass (B) may start only
+// after every A tile of its limb has been written back (per-limb counters), so
+// limbs cross the pass boundary through L2 without a grid-wide barrier and
+// without a kernel boundary.
+//
+// Each CTA is warp-specialised:
+//   * NT compute threads transform tiles held in a ring of three shared-memory
+//     buffers; they only wait for a buffer to be filled ("full" mbarrier) and
+//     report it computed ("empty" mbarrier).
+//   * one producer thread (its own warp) runs an event loop: it claims units
+//     from two global queues, preferring a B tile whose limb is already
+//     published and otherwise taking an A tile, so a CTA never idles on a
+//     dependency while other work is left; it loads tiles by TMA (2-D tensor
+//     maps with the 128-byte swizzle the compute rounds expect), together
+//     with the prime's constants and, for column tiles, the twiddles Psi[0,R1)
+//     of the column pass; it stores computed tiles by TMA and, once a store
+//     of an A tile has completed, publishes it on the limb's counter.
+//
+// Deadlock freedom: A tiles never wait.  A producer holds at most one B tile
+// whose limb is not yet published, and while it polls for that limb it keeps
+// storing and publishing its own finished tiles, so every A tile that any B
+// tile waits for is eventually published.  Every wait is bounded; a wait that
+// runs out sets the plan's status word and the CTA stops.
+//
+// Work area (plan-owned, zero between launches): [0] next A ticket, [1] next
+// B ticket, [2] CTAs finished, [4 + limb] published A tiles of the limb.  The
+// last CTA to finish zeroes it again.
+#pragma once
+#include "ntt_pass.cuh"
+#include "tma.cuh"
+
+#ifndef NTT_FUSED_THREADS_PER_SM
+#define NTT_FUSED_THREADS_PER_SM 576    // resident threads per SM the registers are sized for
+#endif
+
+namespace ntt {
+
+// bits of the device status word
+enum : u32 { STATUS_DEP_TIMEOUT = 1u, STATUS_TMA_TIMEOUT = 2u };
+
+struct FusedArgs {
+    const PrimeDev* primes;  // [L]
+    const Tw* tw;            // [L][tw_len]
+    const Tw* ota;           // [L][2^p2]      OT A factors, this direction
+    const Tw* otb;           // [L][p2 << p1]  OT B factors, this direction
+    u32* ctl;                // work area (see the file comment)
+    u32* status;             // persistent error word
+    u32 tw_len;
+    u32 L;                   // primes per polynomial (limb l uses prime l % L)
+    u32 limbs;
+    u32 max_polls;           // bound of every wait loop
+};
+
+template <int P1, int P2, int LOGC_R, int KMAX>
+struct FusedCfg {
+    static constexpr int R1 = 1 << P1, R2 = 1 << P2, CR = 1 << LOGC_R;
+    static constexpr int TILE_C = 16 * R1;             // column tile: 16 columns x R1 rows
+    static constexpr int TILE_R = CR * R2;             // row tile: CR rows of R2 words
+    static constexpr int TILE = TILE_C > TILE_R ? TILE_C : TILE_R;
+    static constexpr int TC = pass_threads(P1, 4, KMAX);
+    static constexpr int TR = pass_threads(P2, LOGC_R, KMAX);
+    static constexpr int NT = TC > TR ? TC : TR;       // compute threads
+    static constexpr int THREADS = NT + 32;            // + the producer warp
+    // per buffer: the tile, the column pass's twiddles Psi[0, R1), the prime's
+    // constants and the unit descriptor, the first three filled by one
+    // mbarrier transaction
+    static constexpr size_t TW_OFF = (size_t)TILE * 8;
+    static constexpr size_t PR_OFF = TW_OFF + (size_t)R1 * sizeof(Tw);
+    static constexpr size_t DESC_OFF = PR_OFF + sizeof(PrimeDev);
+    static constexpr size_t BUF = (DESC_OFF + 16 + 1023) / 1024 * 1024;
+    static constexpr int NBUF = 3;                     // ring of tile buffers
+    static constexpr size_t SMEM = NBUF * BUF + 1024;
+    static constexpr int MIN_CTAS =
+        NTT_FUSED_THREADS_PER_SM / THREADS > 1 ? NTT_FUSED_THREADS_PER_SM / THREADS : 1;
+};
+
+// unit descriptor written by the producer into the buffer it fills
+struct __align__(16) UnitDesc {
+    u32 kind;    // KIND_A, KIND_B or KIND_STOP
+    u32 limb;
+    u32 tile;
+    u32 prime;   // limb % L
+};
+enum : u32 { KIND_A = 0u, KIND_B = 1u, KIND_STOP = 2u };
+
+// all compute threads agree on a flag (named barrier 1 with reduction)
+template <int NT>
+__device__ __forceinline__ bool compute_any(bool flag)
+{
+    u32 r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((u32)flag), "n"(NT)
+        : "memory");
+    return r != 0;
+}
+
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS>
+__global__ void __launch_bounds__(FusedCfg<P1, P2, LOGC_R, KMAX>::THREADS, FusedCfg<P1, P2, LOGC_R, KMAX>::MIN_CTAS)
+ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapR,
+                 const FusedArgs a)
+{
+    using F = FusedCfg<P1, P2, LOGC_R, KMAX>;
+    constexpr int NT = F::NT;
+    constexpr int NBUF = F::NBUF;
+    constexpr u32 UC = F::R2 / 16;          // column tiles per limb
+    constexpr u32 UR = F::R1 / F::CR;       // row tiles per limb
+    constexpr u32 UA = FWD ? UC : UR, UB = FWD ? UR : UC;
+    constexpr int X_B = FWD ? ct_range_after(1, P1) : gs_range_after(1, P2);
+    constexpr u32 NONE = 0xFFFFFFFFu;
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    auto buf_tile = [&](int b) { return reinterpret_cast<u64*>(smem_raw + b * F::BUF); };
+    auto buf_tw = [&](int b) { return reinterpret_cast<Tw*>(smem_raw + b * F::BUF + F::TW_OFF); };
+    auto buf_pr = [&](int b) { return reinterpret_cast<PrimeDev*>(smem_raw + b * F::BUF + F::PR_OFF); };
+    auto buf_desc = [&](int b) { return reinterpret_cast<volatile UnitDesc*>(smem_raw + b * F::BUF + F::DESC_OFF); };
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + NBUF * F::BUF);
+    uint64_t* empty = full + NBUF;
+
+    const u32 tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], NT);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // an A (first-executed pass) tile is a column tile for the forward
+    // transform and a row tile for the inverse
+    auto is_col = [](u32 kind) { return FWD ? kind == KIND_A : kind == KIND_B; };
+
+    if (tid >= (u32)NT) {
+        if (tid != (u32)NT) return;
+        // =================================================== producer ====
+        u32* const done = a.ctl + 4;
+        const u32 totalA = a.limbs * UA, totalB = a.limbs * UB;
+        u32 issued = 0, stored = 0;             // units loaded / stored by this CTA
+        u32 q0 = 0, q1 = 0, q2 = 0, qn = 0;      // committed stores not yet published (FIFO)
+        u32 ready_hint = 0;                      // limbs below it are known published
+        bool a_left = true, b_left = true, stopped = false, failed = false;
+        u32 held = NONE;                         // claimed B ticket waiting for its limb
+        u32 idle = 0;
+
+        auto publish_entry = [&](u32 e) {
+            if (e & 0x80000000u) {
+                fence_proxy_async_global();
+                red_release_add(&done[e & 0x7FFFFFFFu], 1u);
+            }
+        };
+        // publish all committed stores but the newest (their stores are complete)
+        auto publish_older = [&]() {
+            if (qn >= 2) {
+                bulk_wait<1>();
+                publish_entry(q0);
+                if (qn == 3) publish_entry(q1);
+                q0 = qn == 3 ? q2 : q1;
+                qn = 1;
+            }
+        };
+        auto publish_all = [&]() {
+            if (qn) {
+                bulk_wait<0>();
+                publish_entry(q0);
+                if (qn > 1) publish_entry(q1);
+                if (qn > 2) publish_entry(q2);
+                qn = 0;
+            }
+        };
+        auto load = [&](u32 kind, u32 t) {
+            const int b = (int)(issued % NBUF);
+            const u32 U = kind == KIND_A ? UA : UB;
+            const u32 limb = t / U, tile = t % U, pi = limb % a.L;
+            volatile UnitDesc* d = buf_desc(b);
+            d->kind = kind;
+            d->limb = limb;
+            d->tile = tile;
+            d->prime = pi;
+            bulk_wait_read<0>();                 // the buffer's previous store has read it
+            if (kind == KIND_B) fence_proxy_async_global();
+            u64* dst = buf_tile(b);
+            if (is_col(kind)) {
+                mbar_arrive_expect_tx(&full[b], F::TILE_C * 8 + F::R1 * (u32)sizeof(Tw) + (u32)sizeof(PrimeDev));
+                tma_load_2d(dst, &mapC, (int)(tile * 16), (int)(limb * F::R1), &full[b]);
+                bulk_load(buf_tw(b), a.tw + (size_t)pi * a.tw_len, F::R1 * (u32)sizeof(Tw), &full[b]);
+            } else {
+                mbar_arrive_expect_tx(&full[b], F::TILE_R * 8 + (u32)sizeof(PrimeDev));
+                tma_load_2d(dst, &mapR, 0, (int)(limb * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), &full[b]);
+            }
+            bulk_load(buf_pr(b), a.primes + pi, (u32)sizeof(PrimeDev), &full[b]);
+            ++issued;
+        };
+        auto limb_ready = [&](u32 limb) {
+            if (limb < ready_hint) return true;
+            if (ld_acquire(&done[limb]) >= UA) {
+                if (limb + 1 > ready_hint) ready_hint = limb + 1;
+                return true;
+            }
+            return false;
+        };
+        auto claim_b = [&](bool& claimed) {
+            const u32 t = atomicAdd(&a.ctl[1], 1u);
+            if (t < totalB) {
+                if (limb_ready(t / UB)) load(KIND_B, t);
+                else held = t;
+                claimed = true;
+            } else {
+                b_left = false;
+            }
+        };
+
+        prefetch_tensormap(&mapC);
+        prefetch_tensormap(&mapR);
+        for (;;) {
+            bool progress = false;
+            // store computed tiles, in order
+            while (stored < issued && mbar_test(&empty[stored % NBUF], (stored / NBUF) & 1u)) {
+                const int b = (int)(stored % NBUF);
+                const volatile UnitDesc* d = buf_desc(b);
+                const u32 kind = d->kind, limb = d->limb, tile = d->tile;
+                const u64* src = buf_tile(b);
+                if (is_col(kind))
+                    tma_store_2d(&mapC, (int)(tile * 16), (int)(limb * F::R1), src);
+                else
+                    tma_store_2d(&mapR, 0, (int)(limb * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), src);
+                bulk_commit();
+                const u32 e = kind == KIND_A ? (0x80000000u | limb) : 0u;
+                if (qn == 0) q0 = e;
+                else if (qn == 1) q1 = e;
+                else q2 = e;
+                ++qn;
+                ++stored;
+                publish_older();
+                progress = true;
+            }
+            if (stopped) {
+                if (stored + 1 == issued) break;     // every real unit stored (the last slot is the stop)
+            } else if (issued - stored < (u32)NBUF) {
+                // a buffer is free: pick the next unit
+                if (held != NONE) {
+                    if (limb_ready(held / UB)) {
+                        load(KIND_B, held);
+                        held = NONE;
+                        progress = true;
+                    }
+                } else {
+                    bool claimed = false;
+                    if (b_left && a_left) {
+                        // prefer a second-pass tile whose limb is already published
+                        const u32 peek = ld_relaxed(&a.ctl[1]);
+                        if (peek >= totalB) b_left = false;
+                        else if (limb_ready(peek / UB)) claim_b(claimed);
+                    }
+                    if (!claimed && a_left) {
+                        const u32 t = atomicAdd(&a.ctl[0], 1u);
+                        if (t < totalA) {
+                            load(KIND_A, t);
+                            claimed = true;
+                        } else {
+                            a_left = false;
+                        }
+                    }
+                    if (!claimed && b_left) claim_b(claimed);
+                    if (claimed) progress = true;
+                    if (!a_left && !b_left && held == NONE) {
+                        // no work left: a stop descriptor in the next buffer
+                        const int b = (int)(issued % NBUF);
+                        buf_desc(b)->kind = KIND_STOP;
+                        mbar_arrive(&full[b]);
+                        ++issued;
+                        stopped = true;
+                        progress = true;
+                    }
+                }
+            }
+            if (progress) {
+                idle = 0;
+                continue;
+            }
+            // nothing moved: publish what is complete (another limb may wait on it), then back off
+            publish_all();
+            if (++idle > a.max_polls) {
+                failed = true;
+                break;
+            }
+            __nanosleep(64);
+        }
+        publish_all();
+        if (failed) {
+            atomicOr(a.status, held != NONE ? STATUS_DEP_TIMEOUT : STATUS_TMA_TIMEOUT);
+            if (!stopped && issued - stored < (u32)NBUF) {
+                const int b = (int)(issued % NBUF);
+                buf_desc(b)->kind = KIND_STOP;
+                mbar_arrive(&full[b]);
+            }
+        }
+        // the last CTA to finish zeroes the work area for the next launch
+        __threadfence();
+        if (atomicAdd(&a.ctl[2], 1u) == gridDim.x - 1) {
+            for (u32 i = 0; i < a.limbs + 4; ++i) a.ctl[i] = 0u;
+            __threadfence();
+        }
+        return;
+    }
+
+    // ===================================================== compute ======
+    for (u32 k = 0;; ++k) {
+        const int b = (int)(k % NBUF);
+        const bool got = mbar_wait(&full[b], (k / NBUF) & 1u, a.max_polls);
+        if (compute_any<NT>(!got)) {
+            if (tid == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
+            break;
+        }
+        const u32 kind = buf_desc(b)->kind;
+        if (kind == KIND_STOP) break;
+        const u32 tile = buf_desc(b)->tile;
+        const u32 pi = buf_desc(b)->prime;
+        u64* sm = buf_tile(b);
+        const PrimeDev& pr = *buf_pr(b);
+        if (is_col(kind)) {
+            // column pass: twiddles Psi[0, R1) staged with the tile
+            if constexpr (FWD)
+                compute_tile<P1, 4, KMAX, false, true, 1, false, true, 0, true, NT, NoHook, true>(
+                    sm, pr, buf_tw(b), nullptr, nullptr, 0u, 0u, tid);
+            else
+                compute_tile<P1, 4, KMAX, false, false, X_B, true, true, 0, true, NT, NoHook, true>(
+                    sm, pr, buf_tw(b), nullptr, nullptr, 0u, 0u, tid);
+        } else {
+            const Tw* tw = a.tw + (size_t)pi * a.tw_len;
+            const Tw* ota = a.ota ? a.ota + (size_t)pi * F::R2 : nullptr;
+            const Tw* otb = a.otb ? a.otb + (size_t)pi * ((size_t)P2 << P1) : nullptr;
+            if constexpr (FWD)
+                compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
+                    sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
+            else
+                compute_tile<P2, LOGC_R, KMAX, true, false, 1, false, false, OTS, false, NT, NoHook, true>(
+                    sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
+        }
+        // make this thread's shared-memory writes visible to the TMA store
+        fence_proxy_async_shared();
+        mbar_arrive(&empty[b]);
+    }
+}
+
+}  // namespace ntt

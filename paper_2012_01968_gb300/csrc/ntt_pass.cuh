@@ -53,6 +53,19 @@ __host__ __device__ constexpr int gs_range_max(int X, int stages)
 // strided per-thread accesses of every round conflict-free.
 __device__ __forceinline__ u32 swz(u32 w) { return w ^ (((w >> 4) & 7u) << 1); }
 
+// Twiddle slots.  Within stage s the butterfly with index j = (u << sl) |
+// (hi << k) | pre (u: sub-transform bits, hi: bits of the round digit fixed
+// per thread, pre: the butterfly's group inside the thread's radix-2^KR
+// block, k = sl - K0) reads table slot (u << sl) | (pre << K0) | hi, so that
+// for each pre the lanes of a warp (consecutive hi) read consecutive slots.
+// The plan stores Psi in that order (tw_slot); the order is a bit
+// permutation, so complementing j complements its slot and the inverse can
+// still read Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j] at the mirrored slot.
+__host__ __device__ constexpr unsigned tw_slot(unsigned j, int sl, int K0, int k)
+{
+    return (j >> sl << sl) | ((j & ((1u << k) - 1u)) << K0) | ((j >> k) & ((1u << K0) - 1u));
+}
+
 // Everything one item (one thread's 2^KR elements of one sub-transform in one
 // round) needs besides its data.
 struct ItemCtx {
@@ -77,7 +90,7 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[E], const ItemCtx& c)
         constexpr bool ot = sl >= P - OTS;
 #pragma unroll
         for (int pre = 0; pre < (1 << k); ++pre) {
-            const u32 jlo = (c.hi << k) | (u32)pre;
+            const u32 jlo = ((u32)pre << K0) | c.hi;      // twiddle slot, see tw_slot
             if constexpr (ot) {
                 const Tw f1 = c.otb[((u32)sl << c.s0) + c.u];
                 const Tw f2 = c.ota[(1u << sl) + jlo];
@@ -115,7 +128,7 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[E], const ItemCtx& c)
         } else {
 #pragma unroll
             for (int pre = 0; pre < (1 << k); ++pre) {
-                const u32 jlo = (c.hi << k) | (u32)pre;
+                const u32 jlo = ((u32)pre << K0) | c.hi;  // twiddle slot, see tw_slot
                 if constexpr (ot) {
                     const Tw f1 = c.otb[((u32)sl << c.s0) + c.u];
                     const Tw f2 = c.ota[(1u << sl) + jlo];
@@ -141,7 +154,7 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[E], const ItemCtx& c)
 // One round: every item of the tile reads its 2^KR elements from shared
 // memory, runs KR stages in registers and writes them back.
 template <int P, int LOGC, int KMAX, int r, bool ROWS, bool FWD, int XR, int OTS,
-          bool HAS_S0, int CANON, bool TWG>
+          bool HAS_S0, int CANON, bool TWG, int NT>
 __device__ __forceinline__ void run_round(u64* sm, ItemCtx c, const u32 u_base, const u32 tid)
 {
     constexpr int KR = rsize(P, KMAX, r);
@@ -149,12 +162,10 @@ __device__ __forceinline__ void run_round(u64* sm, ItemCtx c, const u32 u_base, 
     constexpr int E = 1 << KR;
     constexpr int NLO = P - K0 - KR;              // bits of v below the digit
     constexpr int R = 1 << P, C = 1 << LOGC;
-    constexpr int T = pass_threads(P, LOGC, KMAX);
     constexpr int ITEMS = C << (P - KR);
-    static_assert(ITEMS % T == 0, "items");
     constexpr bool PAIRS = ROWS && NLO == 0 && E >= 2;   // contiguous in smem
 #pragma unroll 1
-    for (int it = tid; it < ITEMS; it += T) {
+    for (int it = tid; it < ITEMS; it += NT) {
         u32 cc, hi, lo;
         if constexpr (ROWS) {
             lo = (u32)it & ((1u << NLO) - 1u);
@@ -216,6 +227,96 @@ __host__ __device__ constexpr int round_in_range()
 {
     if constexpr (FWD) return ct_range_after(XIN, rstart(P, KMAX, r));
     else return gs_range_after(XIN, P - rstart(P, KMAX, r) - rsize(P, KMAX, r));
+}
+
+// Run all P stages of one tile held in shared memory (rounds separated by
+// block barriers; no barrier after the last round).
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// Barrier between rounds: the whole block, or (NAMED) named barrier 1 over
+// the NT compute threads only (when other warps of the block do not take part).
+template <int NT, bool NAMED>
+__device__ __forceinline__ void round_barrier()
+{
+    if constexpr (NAMED)
+        asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    else
+        __syncthreads();
+}
+
+// `mid` runs (in every thread) after the first round executed, before the
+// barrier that follows it.
+template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
+          bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false>
+__device__ __forceinline__ void compute_tile(u64* sm, const PrimeDev& pr, const Tw* tw, const Tw* ota,
+                                             const Tw* otb, const u32 u_base, const u32 s0, const u32 tid,
+                                             Hook mid = Hook())
+{
+    constexpr int NR = nrounds(P, KMAX);
+    static_assert(NR <= 4, "at most four rounds per pass");
+    static_assert(FWD ? ct_range_max(XIN, P) <= 16 : gs_range_max(XIN, P) <= 8, "lazy range");
+    ItemCtx c;
+    c.q = pr.q;
+    c.q4 = pr.q << 2;
+    c.mbar = pr.mbar;
+    c.u = u_base;
+    c.hi = 0;
+    c.s0 = s0;
+    c.ninv = pr.ninv;
+    c.w1ninv = pr.w1ninv;
+    c.tw = tw;
+    c.ota = ota;
+    c.otb = otb;
+
+    // canonical output written by the last round executed
+    constexpr int FWD_OUT = ct_range_after(XIN, P);
+    constexpr int CANON_FWD = FINAL ? FWD_OUT : 0;
+    constexpr int CANON_INV = FINAL ? (HAS_S0 ? 4 : gs_range_after(XIN, P)) : 0;
+
+    if constexpr (FWD) {
+        run_round<P, LOGC, KMAX, 0, ROWS, true, round_in_range<P, KMAX, true, XIN, 0>(), OTS, false,
+                  (NR == 1 ? CANON_FWD : 0), !TW_SMEM, NT>(sm, c, u_base, tid);
+        mid();
+        if constexpr (NR > 1) {
+            round_barrier<NT, NAMED>();
+            run_round<P, LOGC, KMAX, 1, ROWS, true, round_in_range<P, KMAX, true, XIN, 1>(), OTS, false,
+                      (NR == 2 ? CANON_FWD : 0), !TW_SMEM, NT>(sm, c, u_base, tid);
+        }
+        if constexpr (NR > 2) {
+            round_barrier<NT, NAMED>();
+            run_round<P, LOGC, KMAX, 2, ROWS, true, round_in_range<P, KMAX, true, XIN, 2>(), OTS, false,
+                      (NR == 3 ? CANON_FWD : 0), !TW_SMEM, NT>(sm, c, u_base, tid);
+        }
+        if constexpr (NR > 3) {
+            round_barrier<NT, NAMED>();
+            run_round<P, LOGC, KMAX, 3, ROWS, true, round_in_range<P, KMAX, true, XIN, 3>(), OTS, false,
+                      CANON_FWD, !TW_SMEM, NT>(sm, c, u_base, tid);
+        }
+    } else {
+        if constexpr (NR > 3) {
+            run_round<P, LOGC, KMAX, 3, ROWS, false, round_in_range<P, KMAX, false, XIN, 3>(), OTS, false, 0, !TW_SMEM, NT>(
+                sm, c, u_base, tid);
+            if constexpr (NR == 4) mid();
+            round_barrier<NT, NAMED>();
+        }
+        if constexpr (NR > 2) {
+            run_round<P, LOGC, KMAX, 2, ROWS, false, round_in_range<P, KMAX, false, XIN, 2>(), OTS, false, 0, !TW_SMEM, NT>(
+                sm, c, u_base, tid);
+            if constexpr (NR == 3) mid();
+            round_barrier<NT, NAMED>();
+        }
+        if constexpr (NR > 1) {
+            run_round<P, LOGC, KMAX, 1, ROWS, false, round_in_range<P, KMAX, false, XIN, 1>(), OTS, false, 0, !TW_SMEM, NT>(
+                sm, c, u_base, tid);
+            if constexpr (NR == 2) mid();
+            round_barrier<NT, NAMED>();
+        }
+        run_round<P, LOGC, KMAX, 0, ROWS, false, round_in_range<P, KMAX, false, XIN, 0>(), OTS, HAS_S0,
+                  CANON_INV, !TW_SMEM, NT>(sm, c, u_base, tid);
+        if constexpr (NR == 1) mid();
+    }
 }
 
 // ------------------------------------------------------------------ pass ---
@@ -292,61 +393,9 @@ ntt_pass_kernel(const PassArgs a)
     }
     __syncthreads();
 
-    ItemCtx c;
-    c.q = pr.q;
-    c.q4 = pr.q << 2;
-    c.mbar = pr.mbar;
-    c.u = u_base;
-    c.hi = 0;
-    c.s0 = a.s0;
-    c.ninv = pr.ninv;
-    c.w1ninv = pr.w1ninv;
-    c.tw = TW_SMEM ? sm_tw : a.tw + (size_t)pi * a.tw_len;
-    c.ota = sm_ota;
-    c.otb = a.otb ? a.otb + (size_t)pi * ((size_t)P << a.s0) : nullptr;
-
-    // canonical output written by the last round executed
-    constexpr int FWD_OUT = ct_range_after(XIN, P);
-    constexpr int CANON_FWD = FINAL ? FWD_OUT : 0;
-    constexpr int CANON_INV = FINAL ? (HAS_S0 ? 4 : gs_range_after(XIN, P)) : 0;
-
-    if constexpr (FWD) {
-        run_round<P, LOGC, KMAX, 0, ROWS, true, round_in_range<P, KMAX, true, XIN, 0>(), OTS, false,
-                  (NR == 1 ? CANON_FWD : 0), !TW_SMEM>(sm, c, u_base, tid);
-        if constexpr (NR > 1) {
-            __syncthreads();
-            run_round<P, LOGC, KMAX, 1, ROWS, true, round_in_range<P, KMAX, true, XIN, 1>(), OTS, false,
-                      (NR == 2 ? CANON_FWD : 0), !TW_SMEM>(sm, c, u_base, tid);
-        }
-        if constexpr (NR > 2) {
-            __syncthreads();
-            run_round<P, LOGC, KMAX, 2, ROWS, true, round_in_range<P, KMAX, true, XIN, 2>(), OTS, false,
-                      (NR == 3 ? CANON_FWD : 0), !TW_SMEM>(sm, c, u_base, tid);
-        }
-        if constexpr (NR > 3) {
-            __syncthreads();
-            run_round<P, LOGC, KMAX, 3, ROWS, true, round_in_range<P, KMAX, true, XIN, 3>(), OTS, false,
-                      CANON_FWD, !TW_SMEM>(sm, c, u_base, tid);
-        }
-    } else {
-        if constexpr (NR > 3) {
-            run_round<P, LOGC, KMAX, 3, ROWS, false, round_in_range<P, KMAX, false, XIN, 3>(), OTS, false, 0, !TW_SMEM>(
-                sm, c, u_base, tid);
-            __syncthreads();
-        }
-        if constexpr (NR > 2) {
-            run_round<P, LOGC, KMAX, 2, ROWS, false, round_in_range<P, KMAX, false, XIN, 2>(), OTS, false, 0, !TW_SMEM>(
-                sm, c, u_base, tid);
-            __syncthreads();
-        }
-        if constexpr (NR > 1) {
-            run_round<P, LOGC, KMAX, 1, ROWS, false, round_in_range<P, KMAX, false, XIN, 1>(), OTS, false, 0, !TW_SMEM>(
-                sm, c, u_base, tid);
-            __syncthreads();
-        }
-        run_round<P, LOGC, KMAX, 0, ROWS, false, round_in_range<P, KMAX, false, XIN, 0>(), OTS, HAS_S0,
-                  CANON_INV, !TW_SMEM>(sm, c, u_base, tid);
-    }
+    compute_tile<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, T>(
+        sm, pr, TW_SMEM ? sm_tw : a.tw + (size_t)pi * a.tw_len, sm_ota,
+        a.otb ? a.otb + (size_t)pi * ((size_t)P << a.s0) : nullptr, u_base, a.s0, tid);
     __syncthreads();
 
     // shared -> global

@@ -27,6 +27,28 @@ namespace nt = ntt::nt;
 
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
 
+// Make the fused kernel's work area cover `limbs` limbs (zero-filled).  A
+// larger area replaces the old one after the device has drained.
+cudaError_t ntt_internal_grow_work(ntt_plan* p, uint32_t limbs)
+{
+    std::lock_guard<std::mutex> g(p->work_mu);
+    if (p->work_limbs >= limbs) return cudaSuccess;
+    if (p->d_work) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return e;
+        cudaFree(p->d_work);
+        p->d_work = nullptr;
+        p->work_limbs = 0;
+    }
+    const size_t bytes = ((size_t)limbs + 4) * sizeof(uint32_t);
+    cudaError_t e = cudaMalloc(&p->d_work, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(p->d_work, 0, bytes);
+    if (e != cudaSuccess) return e;
+    p->work_limbs = limbs;
+    return cudaSuccess;
+}
+
 namespace {
 
 struct HostTables {
@@ -46,8 +68,14 @@ void build_prime(const ntt_plan& p, uint32_t l, HostTables& h)
     auto fwd = [&](uint64_t e) { return pw[e]; };                          // e < N
     auto inv = [&](uint64_t e) { return e == 0 ? 1 : q - pw[N - e]; };    // psi^{-e}, e < N
 
+    // Psi[2^s + j] goes to slot 2^s + tw_slot(j) of the pass holding stage s
     Tw* tw = h.tw.data() + (size_t)l * p.tw_len;
-    for (uint32_t i = 0; i < p.tw_len; ++i) tw[i] = make_tw(fwd(nt::brv(i, n)), q);
+    tw[0] = make_tw(1, q);
+    for (uint32_t s = 0; (1u << s) < p.tw_len; ++s) {
+        const ntt::StageSlot g = ntt::stage_slot_params(n, p.p1, s);
+        for (uint32_t j = 0; j < (1u << s); ++j)
+            tw[(1u << s) + ntt::tw_slot(j, g.sl, g.K0, g.k)] = make_tw(fwd(nt::brv((1u << s) + j, n)), q);
+    }
 
     PrimeDev& d = h.pd[l];
     d.q = q;
@@ -64,12 +92,15 @@ void build_prime(const ntt_plan& p, uint32_t l, HostTables& h)
         Tw* af = h.ota_f.data() + (size_t)l * R;
         Tw* ai = h.ota_i.data() + (size_t)l * R;
         af[0] = ai[0] = make_tw(1, q);
-        for (uint32_t sl = 0; sl < p2; ++sl)
+        for (uint32_t sl = 0; sl < p2; ++sl) {
+            const ntt::StageSlot g = ntt::stage_slot_params(n, p.p1, p.p1 + sl);
             for (uint32_t j = 0; j < (1u << sl); ++j) {
                 const uint64_t e = ((uint64_t)nt::brv(j, sl)) << (n - sl);
-                af[(1u << sl) + j] = make_tw(fwd(e), q);
-                ai[(1u << sl) + j] = make_tw(inv(e), q);
+                const uint32_t slot = (1u << sl) + ntt::tw_slot(j, g.sl, g.K0, g.k);
+                af[slot] = make_tw(fwd(e), q);
+                ai[slot] = make_tw(inv(e), q);
             }
+        }
         const size_t bl = (size_t)p2 << s0;
         Tw* bf = h.otb_f.data() + (size_t)l * bl;
         Tw* bi = h.otb_i.data() + (size_t)l * bl;
@@ -104,6 +135,8 @@ void free_plan(ntt_plan* p)
     cudaFree(p->d_ota_i);
     cudaFree(p->d_otb_i);
     cudaFree(p->d_stage);
+    cudaFree(p->d_status);
+    cudaFree(p->d_work);
     delete p;
 }
 
@@ -120,6 +153,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     for (uint32_t r : o.reserved)
         if (r) return NTT_ERR_INVALID_ARG;
     if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
+    if (o.kernel > NTT_KERNEL_PER_PASS) return NTT_ERR_INVALID_ARG;
     const uint32_t n = (uint32_t)__builtin_ctz(N);
     const uint32_t p1 = (uint32_t)ntt::split_p1((int)n);
     const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
@@ -148,6 +182,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     p->passes = two_pass ? 2 : 1;
     p->twiddle_mode = mode;
     p->ot_stages = ots;
+    p->kernel = (o.kernel == NTT_KERNEL_PER_PASS) ? NTT_KERNEL_PER_PASS : NTT_KERNEL_FUSED;
     cudaError_t ce = cudaGetDevice(&p->device);
     if (ce != cudaSuccess) {
         ntt_internal_set_cuda_error(ce);
@@ -191,7 +226,10 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
         for (auto& t : th) t.join();
     }
 
-    ce = upload(&p->d_primes, h.pd, p->device_bytes);
+    ce = cudaMalloc(&p->d_status, sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(p->d_status, 0, sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = ntt_internal_grow_work(p, L * 16u);
+    if (ce == cudaSuccess) ce = upload(&p->d_primes, h.pd, p->device_bytes);
     if (ce == cudaSuccess) ce = upload(&p->d_tw, h.tw, p->device_bytes);
     if (ce == cudaSuccess) ce = upload(&p->d_ota_f, h.ota_f, p->device_bytes);
     if (ce == cudaSuccess) ce = upload(&p->d_otb_f, h.otb_f, p->device_bytes);
@@ -221,7 +259,23 @@ extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
     info->twiddle_mode = p->twiddle_mode;
     info->ot_stages = p->ot_stages;
     info->device = (uint32_t)p->device;
+    info->kernel = p->kernel;
     info->device_bytes = p->device_bytes;
+    return NTT_OK;
+}
+
+extern "C" ntt_status ntt_plan_device_status(const ntt_plan* p, uint32_t* status)
+{
+    if (!p || !status) return NTT_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    uint32_t v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(v));
+    if (e != cudaSuccess) {
+        ntt_internal_set_cuda_error(e);
+        return NTT_ERR_CUDA;
+    }
+    *status = v;
     return NTT_OK;
 }
 

@@ -6,8 +6,9 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/ntt_gb300.h"
+#include "ntt_gb300.h"
 #include "device_types.cuh"
+#include "ntt_pass.cuh"
 
 namespace ntt {
 
@@ -15,6 +16,30 @@ namespace ntt {
 // of p1 = n - ceil(n/2) and p2 = ceil(n/2) stages.
 constexpr int SINGLE_PASS_MAX = 12;
 inline int split_p1(int n) { return n <= SINGLE_PASS_MAX ? n : n - (n + 1) / 2; }
+
+// Round geometry of the pass that holds stage s (per-thread radix 2^KMAX), used
+// to lay out the twiddle table in the slot order the kernels read.
+#ifndef NTT_KMAX
+#define NTT_KMAX 4      // stages per thread per round (per-thread radix 2^NTT_KMAX)
+#endif
+constexpr int KMAX_ALL = NTT_KMAX;
+struct StageSlot {
+    int sl, K0, k;
+};
+inline StageSlot stage_slot_params(int n, int p1, int s)
+{
+    const int s0 = (n <= SINGLE_PASS_MAX || s < p1) ? 0 : p1;
+    const int P = (n <= SINGLE_PASS_MAX) ? n : (s < p1 ? p1 : n - p1);
+    const int sl = s - s0;
+    const int nr = (P + KMAX_ALL - 1) / KMAX_ALL;
+    int K0 = 0;
+    for (int r = 0; r < nr; ++r) {
+        const int sz = P / nr + (r < P % nr ? 1 : 0);
+        if (sl < K0 + sz) return StageSlot{sl, K0, sl - K0};
+        K0 += sz;
+    }
+    return StageSlot{sl, 0, sl};
+}
 
 // Everything a launch needs (device pointers are the plan's).
 struct LaunchCtx {
@@ -31,6 +56,10 @@ struct LaunchCtx {
     u32 n;
     u32 p1;
     u32 ots;                 // OT stages (0 = table mode)
+    u32 separate_passes;     // 1: one launch per pass instead of the fused kernel
+    u32* status;             // persistent device status word of the plan
+    u32* work;               // fused kernel's work area (zero between launches)
+    u32 work_limbs;          // limbs the work area covers
     cudaStream_t stream;
 };
 
@@ -62,6 +91,11 @@ struct ntt_plan {
     ntt::Tw* d_ota_i = nullptr;
     ntt::Tw* d_otb_i = nullptr;
     uint64_t device_bytes = 0;
+    uint32_t kernel = 0;                  // NTT_KERNEL_*
+    uint32_t* d_status = nullptr;         // device status word (kernel error bits)
+    uint32_t* d_work = nullptr;           // fused kernel's work area: 4 + work_limbs words
+    uint32_t work_limbs = 0;
+    std::mutex work_mu;
     // staging for ntt_execute_host
     std::mutex stage_mu;
     uint64_t* d_stage = nullptr;
@@ -83,6 +117,10 @@ struct ntt_plan {
         c.n = n;
         c.p1 = p1;
         c.ots = twiddle_mode == NTT_TWIDDLE_OT ? ot_stages : 0;
+        c.separate_passes = kernel == NTT_KERNEL_PER_PASS ? 1u : 0u;
+        c.status = d_status;
+        c.work = d_work;
+        c.work_limbs = work_limbs;
         c.stream = s;
         return c;
     }

@@ -56,7 +56,7 @@ def ct_reduces(X):
 
 
 def ct_next(X):
-    return 7 if ct_reduces(X) else X + 4
+    return 12 if ct_reduces(X) else X + 4
 
 
 def gs_reduces(X):
@@ -64,7 +64,12 @@ def gs_reduces(X):
 
 
 def gs_next(X):
-    return 4 if gs_reduces(X) else (2 * X if 2 * X > 4 else 4)
+    return 8 if gs_reduces(X) else (2 * X if 2 * X > 4 else 4)
+
+
+def csub(x, c):
+    assert 0 <= x < 2 * c
+    return x - c if x >= c else x
 
 
 def ct_after(X, k):
@@ -86,6 +91,27 @@ def rounds(P, KMAX):
     return sizes, starts
 
 
+def tw_slot(j, sl, K0, k):
+    """Table slot of butterfly j of a stage (mirror of tw_slot in ntt_pass.cuh)."""
+    return (j >> sl << sl) | ((j & ((1 << k) - 1)) << K0) | ((j >> k) & ((1 << K0) - 1))
+
+
+def stage_slot_params(n, p1, s, KMAX=4):
+    """(sl, K0, k) of stage s in the pass that holds it (mirror of plan.h)."""
+    if n <= 12:
+        s0, P = 0, n
+    elif s < p1:
+        s0, P = 0, p1
+    else:
+        s0, P = p1, n - p1
+    sl = s - s0
+    sizes, starts = rounds(P, KMAX)
+    for sz, st in zip(sizes, starts):
+        if sl < st + sz:
+            return sl, st, sl - st
+    return sl, 0, sl
+
+
 def swz(w):
     return w ^ (((w >> 4) & 7) << 1)
 
@@ -103,7 +129,15 @@ class PrimeTables:
         inv = lambda e: 1 if e == 0 else q - pw[N - e]
         comp = lambda w: (w << 64) // q
         self.tw_len = N >> ots
-        self.tw = [(fwd(brv(i, n)), comp(fwd(brv(i, n)))) for i in range(self.tw_len)]
+        self.tw = [None] * self.tw_len
+        self.tw[0] = (1, comp(1))
+        s = 0
+        while (1 << s) < self.tw_len:
+            sl, K0, k = stage_slot_params(n, p1, s)
+            for j in range(1 << s):
+                w = fwd(brv((1 << s) + j, n))
+                self.tw[(1 << s) + tw_slot(j, sl, K0, k)] = (w, comp(w))
+            s += 1
         self.mbar = M64 // q
         ninv = pow(N, q - 2, q)
         self.ninv = (ninv, comp(ninv))
@@ -114,10 +148,12 @@ class PrimeTables:
         self.ota_f = [(1, comp(1))] * R
         self.ota_i = [(1, comp(1))] * R
         for sl in range(p2):
+            _, K0, k = stage_slot_params(n, p1, p1 + sl)
             for j in range(1 << sl):
                 e = brv(j, sl) << (n - sl)
-                self.ota_f[(1 << sl) + j] = (fwd(e), comp(fwd(e)))
-                self.ota_i[(1 << sl) + j] = (inv(e), comp(inv(e)))
+                slot = (1 << sl) + tw_slot(j, sl, K0, k)
+                self.ota_f[slot] = (fwd(e), comp(fwd(e)))
+                self.ota_i[slot] = (inv(e), comp(inv(e)))
         s0 = p1
         self.otb_f = [None] * (p2 << s0)
         self.otb_i = [None] * (p2 << s0)
@@ -222,7 +258,7 @@ def run_pass(data, T: PrimeTables, *, P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_
                             x[i + half] = shoup_lazy(d, T.w1ninv[0], T.w1ninv[1], q)
                         continue
                     for pre in range(1 << k):
-                        jlo = (hi << k) | pre
+                        jlo = (pre << K0) | hi
                         if ot:
                             B = (T.otb_f if FWD else T.otb_i)[(sl << s0) + u]
                             A = (T.ota_f if FWD else T.ota_i)[(1 << sl) + jlo]
@@ -240,7 +276,7 @@ def run_pass(data, T: PrimeTables, *, P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_
                             if FWD:
                                 assert a < X * q and bb < X * q
                                 if ct_reduces(X):
-                                    a = reduce3(a, q, T.mbar)
+                                    a = csub(a, 8 * q)
                                 t = shoup_lazy(shoup_lazy(bb, *B, q), *A, q) if ot else shoup_lazy(bb, tw[0], tw[1], q)
                                 x[ia] = a + t
                                 x[ib] = a + q4 - t
@@ -251,7 +287,7 @@ def run_pass(data, T: PrimeTables, *, P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_
                                 d = (a + Xq - bb) if ot else (bb + Xq - a)
                                 s = a + bb
                                 if gs_reduces(X):
-                                    s = reduce3(s, q, T.mbar)
+                                    s = csub(s, 8 * q)
                                 x[ia] = s
                                 x[ib] = shoup_lazy(shoup_lazy(d, *B, q), *A, q) if ot else shoup_lazy(d, tw[0], tw[1], q)
                     if FWD:
@@ -310,3 +346,11 @@ def transform(a, q, psi, n, fwd, ots=0):
         run_pass(data, T, P=p1, LOGC=4, KMAX=4, ROWS=False, FWD=False, XIN=gs_after(1, p2), FINAL=True,
                  HAS_S0=True, OTS=0, TW_SMEM=True, s0=0)
     return data
+
+
+def fused_geometry(n):
+    """(UA, UB, threads) of the fused kernel for N = 2^n, forward direction."""
+    p1, p2 = split(n)
+    lr = logc_rows(p2)
+    UC, UR = (1 << p2) // 16, (1 << p1) >> lr
+    return UC, UR

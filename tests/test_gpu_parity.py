@@ -214,3 +214,44 @@ def test_plan_query_and_psi(orc):
         assert info.twiddle_mode == G.NTT_TWIDDLE_OT and info.ot_stages == 2
         for l in range(3):
             assert G.ntt_plan_psi(p.handle, l) == orc.psi(w.primes[l], w.N)
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+@pytest.mark.parametrize("mode,ots", [(G.NTT_TWIDDLE_TABLE, 0), (G.NTT_TWIDDLE_OT, 1)])
+def test_fused_equals_per_pass(orc, n, mode, ots):
+    """The one-launch fused kernel and the launch-per-pass kernels agree, and
+    no bounded wait of the fused kernel ran out."""
+    N = 1 << n
+    primes = I.prime_chain(5, 2 * N)
+    data = I.batch_uniform(90 + n, 3, primes, N)               # 15 limbs
+    outs = []
+    for kernel in (G.NTT_KERNEL_FUSED, G.NTT_KERNEL_PER_PASS):
+        with G.Plan(N, primes, mode, ots, kernel) as p:
+            d = dev(data)
+            p.forward(d, 3)
+            torch.cuda.synchronize()
+            f = host(d)
+            p.inverse(d, 3)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(d), data)
+            assert p.device_status() == 0
+            outs.append(f)
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], oracle_fwd(orc, data, primes))
+
+
+def test_fused_many_limbs_and_single_limb(orc):
+    """Lag larger than the limb count (1 limb) and many limbs (400)."""
+    N = 1 << 14
+    primes = I.prime_chain(4, 2 * N)
+    for batch, L in ((1, 1), (100, 4)):
+        data = I.batch_uniform(7, batch, primes[:L], N)
+        with G.Plan(N, primes[:L]) as p:
+            d = dev(data)
+            p.forward(d, batch)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(d)[:2], oracle_fwd(orc, data[:2], primes[:L]))
+            p.inverse(d, batch)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(d), data)
+            assert p.device_status() == 0
