@@ -54,13 +54,23 @@ def dist_env():
     return ws, rank, local
 
 
+KERNEL_SOURCES = ("arith.cuh", "device_types.cuh", "ntt_pass.cuh", "tma.cuh", "ntt_fused.cuh",
+                  "launch.cuh", "fused_host.cu", "plan.h", "k_n16.cu")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources the N = 2^16 transform kernels are built from, with
+    comments and blank space removed (a comment edit keeps a profile valid)."""
+    import re
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2012_01968_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode())
-            h.update(fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(d, f)) as fh:
+            txt = fh.read()
+        txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", " ", txt)
+        h.update(f.encode())
+        h.update(" ".join(txt.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,7 +5,7 @@
 // fits in a word, so the butterflies keep values lazily in [0, X*q) for a
 // compile-time bound X <= 16 and reduce only when the bound would overflow.
 //
-// shoup_lazy is Shoup's modular multiplication (Algorithm 3) with the
+// shoup_lazy is Shoup's modular multiplication (Algorithm 4) with the
 // quotient estimated from three 32x32-bit partial products instead of the
 // exact high word of the 128-bit product:
 //   qhat = yh*wh' + hi32(yh*wl') + hi32(yl*wh')   (w' = floor(w 2^64 / q))

@@ -1,6 +1,6 @@
 // Plan creation: validate the primes, derive psi, build the device tables.
 //
-// Tables per prime q (paper: Sec. III-C Psi list, Algorithm 3 companions,
+// Tables per prime q (paper: Sec. III-C Psi list, Algorithm 4 companions,
 // Sec. VII on-the-fly twiddling):
 //   tw[i]  = (Psi[i], floor(Psi[i] 2^64 / q)),  Psi[i] = psi^{brv(i)},  i < tw_len
 //            (tw_len = N in table mode; 2^{n - ot} with OT, since the last ot
