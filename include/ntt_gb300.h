@@ -56,7 +56,8 @@ typedef enum ntt_status {
     NTT_ERR_OOM = 5,          /* device or host allocation failed */
     NTT_ERR_BUSY = 6,         /* admission refused (serving) */
     NTT_ERR_TIMEOUT = 7,      /* a bounded wait expired */
-    NTT_ERR_DEVICE = 8        /* a kernel reported an error status */
+    NTT_ERR_DEVICE = 8,       /* a kernel reported an error status */
+    NTT_ERR_LIMIT = 9         /* batch * levels above NTT_NOALLOC_MAX_LIMBS */
 } ntt_status;
 
 /* Opaque plan: N, the primes, psi per prime and the device tables. */
@@ -157,6 +158,43 @@ enum {
  */
 ntt_status ntt_execute_host(const ntt_plan* plan, const uint64_t* host_in, uint64_t* host_out,
                             uint32_t batch, uint32_t ops, void* stream);
+
+/*
+ * No-allocation transform.  The paper has no counterpart: this is a library
+ * interface for callers that may not allocate device memory while they run,
+ * e.g. a serving loop whose device memory is fully reserved up front, code
+ * called back from inside a memory allocator, or a runtime that forbids
+ * allocation in its steady state.  ntt_forward / ntt_inverse may grow the
+ * plan's work area (a device synchronisation and an allocation) when a call
+ * has more limbs than the plan was sized for; this call never allocates,
+ * frees or synchronises.
+ *
+ * op is NTT_OP_FORWARD or NTT_OP_INVERSE (exactly one); data, batch and
+ * levels (1 <= levels <= L, layout [batch][levels][N]) are as for
+ * ntt_forward_levels / ntt_inverse_levels, and results are identical to
+ * theirs.  The call's scratch (dependency counters of the one-launch two-pass
+ * kernel, 4 + batch * levels words) lives in a fixed device array of this
+ * library, one per device, sized for NTT_NOALLOC_MAX_LIMBS limbs (32 KB).  It
+ * starts at zero when the library is loaded on a device, and every launch
+ * leaves it at zero again.
+ *
+ * The first call on a device does a one-time set-up (it looks up the
+ * array's device address, which may load the library's device code): make
+ * it before any stream capture.  All calls to this function on one device
+ * share the one array, whatever the plan: calls that overlap in time (on
+ * different streams, or from different host threads without ordering) race
+ * on it and give wrong results.  Order them on one stream or with events.
+ * Must run with the plan's device current.
+ *
+ * Errors: NTT_ERR_INVALID_ARG (NULL, batch or levels 0, levels > L, bad op,
+ * current device is not the plan's), NTT_ERR_MISALIGNED, NTT_ERR_LIMIT
+ * (batch * levels > NTT_NOALLOC_MAX_LIMBS; nothing is enqueued), NTT_ERR_CUDA
+ * (set-up or launch failure).
+ */
+#define NTT_NOALLOC_MAX_LIMBS 8192u
+
+ntt_status ntt_transform_noalloc(const ntt_plan* plan, uint64_t* data, uint32_t batch,
+                                 uint32_t levels, uint32_t op, void* stream);
 
 /* Plan facts, for callers and tests. */
 typedef struct ntt_plan_info {

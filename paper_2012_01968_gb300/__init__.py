@@ -28,6 +28,9 @@ NTT_ERR_OOM = 5
 NTT_ERR_BUSY = 6
 NTT_ERR_TIMEOUT = 7
 NTT_ERR_DEVICE = 8
+NTT_ERR_LIMIT = 9
+
+NTT_NOALLOC_MAX_LIMBS = 8192
 
 NTT_TWIDDLE_AUTO = 0
 NTT_TWIDDLE_TABLE = 1
@@ -97,6 +100,8 @@ def _lib():
             L.ntt_mul_pointwise.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
             L.ntt_execute_host.restype = S
             L.ntt_execute_host.argtypes = [_vp, _vp, _vp, _u32, _u32, _vp]
+            L.ntt_transform_noalloc.restype = S
+            L.ntt_transform_noalloc.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp]
             L.ntt_plan_query.restype = S
             L.ntt_plan_query.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
             L.ntt_plan_device_status.restype = S
@@ -218,6 +223,13 @@ def ntt_execute_host(plan: int, host_in, host_out, batch: int, ops: int, stream=
         return int(x)
     _check(_lib().ntt_execute_host(plan, hp(host_in), hp(host_out), batch, ops, _stream(stream)),
            "ntt_execute_host")
+
+
+def ntt_transform_noalloc(plan: int, data, batch: int, levels: int, op: int, stream=None) -> None:
+    """One forward or inverse transform that allocates nothing (fixed device
+    work area shared by all such calls on a device; calls must not overlap)."""
+    _check(_lib().ntt_transform_noalloc(plan, _addr(data), batch, levels, op, _stream(stream, data)),
+           "ntt_transform_noalloc")
 
 
 def ntt_plan_query(plan: int) -> PlanInfo:

@@ -193,6 +193,7 @@ const char* ntt_status_string(ntt_status s)
     case NTT_ERR_BUSY: return "NTT_ERR_BUSY: admission refused";
     case NTT_ERR_TIMEOUT: return "NTT_ERR_TIMEOUT: bounded wait expired";
     case NTT_ERR_DEVICE: return "NTT_ERR_DEVICE: kernel reported an error";
+    case NTT_ERR_LIMIT: return "NTT_ERR_LIMIT: batch * levels exceeds the fixed work area of the no-allocation call";
     }
     return "unknown ntt_status";
 }
