@@ -3,7 +3,10 @@
 
 One step = the forward then the inverse transform of one RNS polynomial of 45
 limbs (the 45 largest primes < 2^60 with q = 1 mod 2^17), uint64 residues,
-seeded uniform inputs.  Metric: limb-NTT/s (each limb forward or inverse
+seeded uniform inputs.  Steps are independent polynomials; step i runs on
+stream i mod --streams (one plan per stream), so one step's tail overlaps the
+next step's start.  The roofline figure uses per-launch CUDA-event durations
+from a separate single-stream pass.  Metric: limb-NTT/s (each limb forward or inverse
 counts as one), with the fraction of the HBM roofline for one read plus one
 write of the data per transform.
 
@@ -44,6 +47,10 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "per_pass"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--streams", type=int, default=2,
+                    help="independent steps spread over this many streams (one plan each)")
+    ap.add_argument("--launch-steps", type=int, default=500,
+                    help="steps of the single-stream pass that times each launch")
     return ap.parse_args()
 
 
@@ -219,6 +226,8 @@ def config_dict(w, args, ws):
     return {"workload": "c2_n65536_l45_fwd_inv", "N": w.N, "L": len(w.primes), "polys_per_step": 1,
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
             "twiddle": args.twiddle, "parallelism": f"replicas{ws}",
+            "streams": args.streams,
+            "overlap": "step i runs on stream i mod streams with its own plan; steps are independent polynomials",
             "l2": "inputs rotate over buffers totalling > 2x L2 (129 MB)"}
 
 
@@ -252,26 +261,30 @@ def main():
     mode = {"auto": (G.NTT_TWIDDLE_AUTO, 0), "table": (G.NTT_TWIDDLE_TABLE, 0),
             "ot1": (G.NTT_TWIDDLE_OT, 1), "ot2": (G.NTT_TWIDDLE_OT, 2)}[args.twiddle]
     kern = {"auto": G.NTT_KERNEL_AUTO, "fused": G.NTT_KERNEL_FUSED, "per_pass": G.NTT_KERNEL_PER_PASS}[args.kernel]
-    plan = G.Plan(N, primes, *mode, kern)
+    S = max(1, args.streams)
+    # one plan (tables + work area) per stream: steps on different streams are
+    # independent polynomials and may overlap on the device
+    plans = [G.Plan(N, primes, *mode, kern) for _ in range(S)]
+    plan = plans[0]
     info = plan.info()
     poly_bytes = N * L * 8
-    nbuf = max(2, -(-2 * L2_BYTES // poly_bytes) + 1)
+    nbuf = max(2 * S, -(-2 * L2_BYTES // poly_bytes) + 1)
     host = I.batch_uniform(w.seed, 1, primes, N)
     src = torch.from_numpy(host.view(np.int64).copy()).cuda()
     bufs = [src.clone() for _ in range(nbuf)]
-    stream = torch.cuda.Stream()
-    sh = stream.cuda_stream
+    streams = [torch.cuda.Stream() for _ in range(S)]
     lib = G.lib()
-    ph = plan.handle
+    handles = [p.handle for p in plans]
 
     def step(i):
+        j = i % S
         b = bufs[i % nbuf].data_ptr()
-        if lib.ntt_forward(ph, b, 1, sh) or lib.ntt_inverse(ph, b, 1, sh):
+        sh = streams[j].cuda_stream
+        if lib.ntt_forward(handles[j], b, 1, sh) or lib.ntt_inverse(handles[j], b, 1, sh):
             raise RuntimeError("launch failed: " + G.ntt_last_cuda_error())
 
-    with torch.cuda.stream(stream):
-        for i in range(args.warmup):
-            step(i)
+    for i in range(max(args.warmup, S)):
+        step(i)
     torch.cuda.synchronize()
     # correctness of the timed path: forward + inverse restores the input
     for b in bufs:
@@ -279,30 +292,29 @@ def main():
             raise RuntimeError("round trip mismatch before timing")
 
     K = args.steps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    cur = torch.cuda.current_stream()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(dev_index)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
     time.sleep(0.15)
-    with torch.cuda.stream(stream):
-        ev[0].record(stream)
-        for i in range(K):
-            b = bufs[i % nbuf].data_ptr()
-            if lib.ntt_forward(ph, b, 1, sh):
-                raise RuntimeError(G.ntt_last_cuda_error())
-            ev[2 * i + 1].record(stream)
-            if lib.ntt_inverse(ph, b, 1, sh):
-                raise RuntimeError(G.ntt_last_cuda_error())
-            ev[2 * i + 2].record(stream)
+    e_start.record(cur)
+    for st in streams:
+        st.wait_event(e_start)
+    for i in range(K):
+        step(i)
+    for st in streams:
+        e = torch.cuda.Event()
+        e.record(st)
+        cur.wait_event(e)
+    e_end.record(cur)
     torch.cuda.synchronize()
     clocks = clk.stop()
     if dist is not None:
         dist.barrier()
-    total_ms = ev[0].elapsed_time(ev[2 * K])
-    fwd_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)]
-    inv_ms = [ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(K)]
+    total_ms = e_start.elapsed_time(e_end)
     if dist is not None:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -310,10 +322,30 @@ def main():
     for b in bufs:
         if not torch.equal(b, src):
             raise RuntimeError("round trip mismatch after timing")
-    if plan.device_status() != 0:
-        raise RuntimeError("device status reports a failed bounded wait")
+    for p in plans:
+        if p.device_status() != 0:
+            raise RuntimeError("device status reports a failed bounded wait")
     limb_ntts = 2 * L * K * ws
     value = limb_ntts / (total_ms / 1e3)
+
+    # per-launch durations of the transform kernels, one stream, CUDA events
+    # around every call (launches do not overlap here)
+    Kp = min(K, args.launch_steps)
+    s0 = streams[0]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Kp + 1)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s0):
+        ev[0].record(s0)
+        for i in range(Kp):
+            b = bufs[i % nbuf].data_ptr()
+            lib.ntt_forward(handles[0], b, 1, s0.cuda_stream)
+            ev[2 * i + 1].record(s0)
+            lib.ntt_inverse(handles[0], b, 1, s0.cuda_stream)
+            ev[2 * i + 2].record(s0)
+    torch.cuda.synchronize()
+    fwd_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Kp)]
+    inv_ms = [ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(Kp)]
+    single_ms = ev[0].elapsed_time(ev[2 * Kp]) / Kp
 
     peak, peak_src = measured_peak_hbm()
     fwd_avg = float(np.mean(fwd_ms))
@@ -331,11 +363,11 @@ def main():
         hout = torch.empty_like(hin).pin_memory()
         ops = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
         for _ in range(3):
-            G.ntt_execute_host(ph, hin, hout, 1, ops, stream)
+            G.ntt_execute_host(handles[0], hin, hout, 1, ops, streams[0])
         E = args.e2e_steps
         t0 = time.perf_counter()
         for _ in range(E):
-            G.ntt_execute_host(ph, hin, hout, 1, ops, stream)
+            G.ntt_execute_host(handles[0], hin, hout, 1, ops, streams[0])
         el = time.perf_counter() - t0
         if not torch.equal(hout, hin):
             raise RuntimeError("e2e round trip mismatch")
@@ -360,9 +392,11 @@ def main():
                      "frac": achieved / peak, "traffic": profile_traffic(),
                      "kernel": f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})",
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
+                     "launch_timing": f"CUDA events around each of {Kp} forward and inverse launches on one stream",
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
         "per_transform_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3,
-                             "sum_of_calls_vs_wall": (sum(fwd_ms) + sum(inv_ms)) / total_ms},
+                             "timed_region_per_transform": total_ms * 1e3 / (2 * K),
+                             "single_stream_per_transform": single_ms * 1e3 / 2},
         "plan": {"twiddle_mode": int(info.twiddle_mode), "ot_stages": int(info.ot_stages),
                  "passes": int(info.passes), "pass1_log2": int(info.pass1_log2),
                  "kernel": "fused" if info.kernel == G.NTT_KERNEL_FUSED else "per_pass"},
@@ -372,7 +406,8 @@ def main():
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
-    plan.close()
+    for p in plans:
+        p.close()
     if dist is not None:
         dist.destroy_process_group()
 

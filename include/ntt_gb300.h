@@ -173,8 +173,8 @@ ntt_status ntt_execute_host(const ntt_plan* plan, const uint64_t* host_in, uint6
  * levels (1 <= levels <= L, layout [batch][levels][N]) are as for
  * ntt_forward_levels / ntt_inverse_levels, and results are identical to
  * theirs.  The call's scratch (dependency counters of the one-launch two-pass
- * kernel, 4 + batch * levels words) lives in a fixed device array of this
- * library, one per device, sized for NTT_NOALLOC_MAX_LIMBS limbs (32 KB).  It
+ * kernel, 4 + 2 * batch * levels words) lives in a fixed device array of this
+ * library, one per device, sized for NTT_NOALLOC_MAX_LIMBS limbs (64 KB).  It
  * starts at zero when the library is loaded on a device, and every launch
  * leaves it at zero again.
  *

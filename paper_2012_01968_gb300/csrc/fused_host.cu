@@ -61,4 +61,16 @@ int device_sm_count()
     return sms > 0 ? sms : 1;
 }
 
+// Limbs whose first-pass results may wait in L2 for their second pass: the
+// window of the fused kernel's A queue, sized to 3/8 of the device's L2.
+u32 fused_window_limbs(size_t limb_bytes)
+{
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const size_t budget = (size_t)(l2 > 0 ? l2 : (32 << 20)) / 8 * 3;
+    const size_t w = budget / (limb_bytes ? limb_bytes : 1);
+    return (u32)(w < 2 ? 2 : (w > 0xFFFFFFu ? 0xFFFFFFu : w));
+}
+
 }  // namespace ntt

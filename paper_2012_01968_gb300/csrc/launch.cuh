@@ -77,6 +77,7 @@ cudaError_t launch_two_pass_ots(const LaunchCtx& c, bool fwd)
 }
 
 // host helpers for the fused launch (fused_host.cu)
+u32 fused_window_limbs(size_t limb_bytes);
 cudaError_t encode_tile_maps(const LaunchCtx& c, int p1, int row_tile_words, CUtensorMap* mapC, CUtensorMap* mapR);
 int device_sm_count();
 
@@ -113,6 +114,7 @@ cudaError_t launch_fused_dir(const LaunchCtx& c)
     a.tw_len = c.tw_len;
     a.L = c.L;
     a.limbs = c.limbs;
+    a.a_window = fused_window_limbs(sizeof(u64) << (P1 + P2));
     a.max_polls = 1u << 22;
     kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(mapC, mapR, a);
     return cudaGetLastError();

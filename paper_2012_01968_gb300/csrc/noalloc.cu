@@ -3,10 +3,10 @@
 // paper has no counterpart; this is a library interface.
 //
 // The only per-call scratch of the transform is the work area of the one-launch
-// two-pass kernel (N >= 2^13): 4 + limbs 32-bit counters that must all be zero
-// when a launch starts and that the launch's last CTA zeroes again before it
-// exits.  Here that area is a file-scope __device__ array, sized for
-// NTT_NOALLOC_MAX_LIMBS limbs (32 KB).  The CUDA runtime zero-initialises it when
+// two-pass kernel (N >= 2^13): 4 + 2 * limbs 32-bit words that must all be
+// zero when a launch starts and that the launch's last CTA zeroes again before
+// it exits.  Here that area is a file-scope __device__ array, sized for
+// NTT_NOALLOC_MAX_LIMBS limbs (64 KB).  The CUDA runtime zero-initialises it when
 // it loads this module on a device, so the zero-at-start condition holds for the
 // first launch and every completed launch restores it.  The kernel itself is the
 // same one the plan's own entry points launch; only the work area differs.
@@ -26,7 +26,7 @@
 
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
 
-static __device__ __align__(256) uint32_t g_noalloc_work[NTT_NOALLOC_MAX_LIMBS + 4];
+static __device__ __align__(256) uint32_t g_noalloc_work[ntt::fused_work_words(NTT_NOALLOC_MAX_LIMBS)];
 
 namespace {
 

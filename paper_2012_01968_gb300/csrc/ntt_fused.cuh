@@ -4,20 +4,35 @@
 // of a limb has no dependencies; a tile of the second pass (B) may start only
 // after every A tile of its limb has been written back (per-limb counters), so
 // limbs cross the pass boundary through L2 without a grid-wide barrier and
-// without a kernel boundary.
+// without a kernel boundary.  A limb whose A tiles are all written back is
+// "published": appended to a list in publication order, and B tickets are
+// handed out in that order, so a B tile waits only while no further limb has
+// been published, never for one particular slow limb.
 //
 // Each CTA is warp-specialised:
 //   * NT compute threads transform tiles held in a ring of three shared-memory
 //     buffers; they only wait for a buffer to be filled ("full" mbarrier) and
 //     report it computed ("empty" mbarrier).
 //   * one producer thread (its own warp) runs an event loop: it claims units
-//     from two global queues, preferring a B tile whose limb is already
-//     published and otherwise taking an A tile, so a CTA never idles on a
-//     dependency while other work is left; it loads tiles by TMA (2-D tensor
+//     from two global queues, at most one unit ahead of the one being
+//     computed (so the last units spread over the CTAs instead of queueing
+//     behind a few), preferring a B tile whose limb is already published and
+//     otherwise taking an A tile, so a CTA never idles on a dependency while
+//     other work is left; it loads tiles by TMA (2-D tensor
 //     maps with the 128-byte swizzle the compute rounds expect), together
 //     with the prime's constants and, for column tiles, the twiddles Psi[0,R1)
 //     of the column pass; it stores computed tiles by TMA and, once a store
 //     of an A tile has completed, publishes it on the limb's counter.
+//
+// Order: A tiles are taken first while the A queue is less than a_window
+// limbs ahead of the B queue (the host sizes the window so that the
+// intermediate results of that many limbs stay in L2); beyond it a B tile
+// whose limb is published goes first.  Taking A tiles early keeps the
+// dependency waits off the end of the launch.
+//
+// Row tiles read the twiddles of their second pass from the global table; the
+// producer prefetches the runs a row tile will read into L2 when it loads the
+// tile, so the compute warps' loads of them hit L2.
 //
 // Deadlock freedom: A tiles never wait.  A producer holds at most one B tile
 // whose limb is not yet published, and while it polls for that limb it keeps
@@ -25,9 +40,11 @@
 // tile waits for is eventually published.  Every wait is bounded; a wait that
 // runs out sets the plan's status word and the CTA stops.
 //
-// Work area (plan-owned, zero between launches): [0] next A ticket, [1] next
-// B ticket, [2] CTAs finished, [4 + limb] published A tiles of the limb.  The
-// last CTA to finish zeroes it again.
+// Work area (plan-owned, zero between launches; 4 + 2 * limbs words): [0]
+// next A ticket, [1] next B ticket, [2] CTAs finished, [3] limbs published,
+// [4 + limb] A tiles of the limb written back, [4 + limbs + i] the i-th
+// published limb plus one (0 while not yet published).  The last CTA to
+// finish zeroes it again.
 #pragma once
 #include "ntt_pass.cuh"
 #include "tma.cuh"
@@ -51,6 +68,7 @@ struct FusedArgs {
     u32 tw_len;
     u32 L;                   // primes per polynomial (limb l uses prime l % L)
     u32 limbs;
+    u32 a_window;            // limbs the A queue may run ahead before ready B tiles are preferred
     u32 max_polls;           // bound of every wait loop
 };
 
@@ -142,18 +160,23 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
         if (tid != (u32)NT) return;
         // =================================================== producer ====
         u32* const done = a.ctl + 4;
+        u32* const order = a.ctl + 4 + a.limbs;  // published limbs + 1, in publication order
         const u32 totalA = a.limbs * UA, totalB = a.limbs * UB;
         u32 issued = 0, stored = 0;             // units loaded / stored by this CTA
         u32 q0 = 0, q1 = 0, q2 = 0, qn = 0;      // committed stores not yet published (FIFO)
-        u32 ready_hint = 0;                      // limbs below it are known published
         bool a_left = true, b_left = true, stopped = false, failed = false;
         u32 held = NONE;                         // claimed B ticket waiting for its limb
         u32 idle = 0;
 
         auto publish_entry = [&](u32 e) {
             if (e & 0x80000000u) {
+                const u32 limb = e & 0x7FFFFFFFu;
                 fence_proxy_async_global();
-                red_release_add(&done[e & 0x7FFFFFFFu], 1u);
+                if (atom_acq_rel_add(&done[limb], 1u) == UA - 1u) {
+                    // this tile completed the limb: append it to the publication order
+                    const u32 pos = atomicAdd(&a.ctl[3], 1u);
+                    st_release(&order[pos], limb + 1u);
+                }
             }
         };
         // publish all committed stores but the newest (their stores are complete)
@@ -175,16 +198,18 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
                 qn = 0;
             }
         };
-        auto load = [&](u32 kind, u32 t) {
+        auto load = [&](u32 kind, u32 limb, u32 tile) {
             const int b = (int)(issued % NBUF);
-            const u32 U = kind == KIND_A ? UA : UB;
-            const u32 limb = t / U, tile = t % U, pi = limb % a.L;
+            const u32 pi = limb % a.L;
             volatile UnitDesc* d = buf_desc(b);
             d->kind = kind;
             d->limb = limb;
             d->tile = tile;
             d->prime = pi;
-            bulk_wait_read<0>();                 // the buffer's previous store has read it
+            // the buffer's previous store has read it: at most one unit is
+            // unstored when a unit is claimed, so at most two stores were
+            // committed after that one; waiting for all but the newest suffices
+            bulk_wait_read<1>();
             if (kind == KIND_B) fence_proxy_async_global();
             u64* dst = buf_tile(b);
             if (is_col(kind)) {
@@ -194,22 +219,30 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
             } else {
                 mbar_arrive_expect_tx(&full[b], F::TILE_R * 8 + (u32)sizeof(PrimeDev));
                 tma_load_2d(dst, &mapR, 0, (int)(limb * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), &full[b]);
+                // table runs of the row pass, into L2: stage sl of rows [u0, u0 + CR)
+                // reads CR << sl consecutive entries (mirrored for the inverse)
+                const Tw* base = a.tw + (size_t)pi * a.tw_len;
+                const u32 u0 = tile * (u32)F::CR;
+#pragma unroll
+                for (int sl = 0; sl < P2 - OTS; ++sl) {
+                    const u32 start = FWD ? (1u << (P1 + sl)) + (u0 << sl)
+                                          : (2u << (P1 + sl)) - ((u0 + (u32)F::CR) << sl);
+                    bulk_prefetch_l2(base + start, ((u32)F::CR << sl) * (u32)sizeof(Tw));
+                }
             }
             bulk_load(buf_pr(b), a.primes + pi, (u32)sizeof(PrimeDev), &full[b]);
             ++issued;
         };
-        auto limb_ready = [&](u32 limb) {
-            if (limb < ready_hint) return true;
-            if (ld_acquire(&done[limb]) >= UA) {
-                if (limb + 1 > ready_hint) ready_hint = limb + 1;
-                return true;
-            }
-            return false;
+        // limb of B ticket t: the (t / UB)-th published limb, NONE while unpublished
+        auto b_limb = [&](u32 t) -> u32 {
+            const u32 v = ld_acquire(&order[t / UB]);
+            return v ? v - 1u : NONE;
         };
         auto claim_b = [&](bool& claimed) {
             const u32 t = atomicAdd(&a.ctl[1], 1u);
             if (t < totalB) {
-                if (limb_ready(t / UB)) load(KIND_B, t);
+                const u32 limb = b_limb(t);
+                if (limb != NONE) load(KIND_B, limb, t % UB);
                 else held = t;
                 claimed = true;
             } else {
@@ -243,26 +276,28 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
             }
             if (stopped) {
                 if (stored + 1 == issued) break;     // every real unit stored (the last slot is the stop)
-            } else if (issued - stored < (u32)NBUF) {
-                // a buffer is free: pick the next unit
+            } else if (issued - stored < 2u) {
+                // nothing but the unit in compute is pending: pick the next unit
                 if (held != NONE) {
-                    if (limb_ready(held / UB)) {
-                        load(KIND_B, held);
+                    const u32 limb = b_limb(held);
+                    if (limb != NONE) {
+                        load(KIND_B, limb, held % UB);
                         held = NONE;
                         progress = true;
                     }
                 } else {
                     bool claimed = false;
                     if (b_left && a_left) {
-                        // prefer a second-pass tile whose limb is already published
+                        // A queue a_window limbs ahead: prefer a published B tile
                         const u32 peek = ld_relaxed(&a.ctl[1]);
                         if (peek >= totalB) b_left = false;
-                        else if (limb_ready(peek / UB)) claim_b(claimed);
+                        else if (ld_relaxed(&a.ctl[0]) / UA >= peek / UB + a.a_window && b_limb(peek) != NONE)
+                            claim_b(claimed);
                     }
                     if (!claimed && a_left) {
                         const u32 t = atomicAdd(&a.ctl[0], 1u);
                         if (t < totalA) {
-                            load(KIND_A, t);
+                            load(KIND_A, t / UA, t % UA);
                             claimed = true;
                         } else {
                             a_left = false;
@@ -305,7 +340,7 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
         // the last CTA to finish zeroes the work area for the next launch
         __threadfence();
         if (atomicAdd(&a.ctl[2], 1u) == gridDim.x - 1) {
-            for (u32 i = 0; i < a.limbs + 4; ++i) a.ctl[i] = 0u;
+            for (u32 i = 0; i < 2 * a.limbs + 4; ++i) a.ctl[i] = 0u;
             __threadfence();
         }
         return;

@@ -40,7 +40,7 @@ cudaError_t ntt_internal_grow_work(ntt_plan* p, uint32_t limbs)
         p->d_work = nullptr;
         p->work_limbs = 0;
     }
-    const size_t bytes = ((size_t)limbs + 4) * sizeof(uint32_t);
+    const size_t bytes = ntt::fused_work_words(limbs) * sizeof(uint32_t);
     cudaError_t e = cudaMalloc(&p->d_work, bytes);
     if (e != cudaSuccess) return e;
     e = cudaMemset(p->d_work, 0, bytes);

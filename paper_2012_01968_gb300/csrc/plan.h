@@ -23,6 +23,10 @@ inline int split_p1(int n) { return n <= SINGLE_PASS_MAX ? n : n - (n + 1) / 2; 
 #define NTT_KMAX 4      // stages per thread per round (per-thread radix 2^NTT_KMAX)
 #endif
 constexpr int KMAX_ALL = NTT_KMAX;
+// 32-bit words of the fused kernel's work area for `limbs` limbs: four
+// counters, a published-tile count per limb and the publication order.
+constexpr size_t fused_work_words(size_t limbs) { return 4 + 2 * limbs; }
+
 struct StageSlot {
     int sl, K0, k;
 };
@@ -59,7 +63,7 @@ struct LaunchCtx {
     u32 separate_passes;     // 1: one launch per pass instead of the fused kernel
     u32* status;             // persistent device status word of the plan
     u32* work;               // fused kernel's work area (zero between launches)
-    u32 work_limbs;          // limbs the work area covers
+    u32 work_limbs;          // limbs the work area covers (fused_work_words(work_limbs) words)
     cudaStream_t stream;
 };
 
@@ -93,7 +97,7 @@ struct ntt_plan {
     uint64_t device_bytes = 0;
     uint32_t kernel = 0;                  // NTT_KERNEL_*
     uint32_t* d_status = nullptr;         // device status word (kernel error bits)
-    uint32_t* d_work = nullptr;           // fused kernel's work area: 4 + work_limbs words
+    uint32_t* d_work = nullptr;           // fused kernel's work area: fused_work_words(work_limbs) words
     uint32_t work_limbs = 0;
     std::mutex work_mu;
     // staging for ntt_execute_host

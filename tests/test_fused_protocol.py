@@ -2,8 +2,10 @@
 
 Each CTA of ntt_fused_kernel has compute warps (a consumer of a ring of three
 tile buffers) and one producer thread (an event loop that claims units from
-two queues, loads tiles, stores computed tiles and publishes first-pass tiles
-on per-limb counters).  Here both sides of every CTA are generators mirroring
+two queues, at most one ahead of the unit in compute, loads tiles, stores
+computed tiles and publishes first-pass tiles on per-limb counters; the
+producer whose tile completes a limb appends the limb to the publication
+order, and second-pass tickets map to limbs in that order).  Here both sides of every CTA are generators mirroring
 that control flow; a random scheduler interleaves them and completes the
 asynchronous copies after random delays.  Checked for many seeds and shapes:
   * a second-pass tile is loaded only after every first-pass tile of its limb
@@ -11,7 +13,8 @@ asynchronous copies after random delays.  Checked for many seeds and shapes:
   * a buffer is refilled only after the store that last used it has read it;
   * a limb counter is raised only for stores that completed;
   * every unit is computed exactly once, the run finishes (no deadlock), and
-    every CTA reaches the finished count.
+    every CTA reaches the finished count;
+for B-first ordering (window 0), a small look-ahead window and A-first.
 """
 import random
 
@@ -28,6 +31,7 @@ class Sim:
         self.totalA, self.totalB = limbs * UA, limbs * UB
         self.ctl = [0, 0, 0]            # next A ticket, next B ticket, CTAs finished
         self.done = [0] * limbs
+        self.order = []                 # published limbs, in publication order
         self.a_stored = [set() for _ in range(limbs)]
         self.computedA = [0] * self.totalA
         self.computedB = [0] * self.totalB
@@ -40,9 +44,10 @@ class Sim:
 
 
 class Cta:
-    def __init__(self, sim, peek=True):
+    def __init__(self, sim, peek=True, window=0):
         self.s = sim
         self.peek = peek
+        self.window = window
         self.full = [0] * NBUF          # completed phases per buffer
         self.empty = [0] * NBUF
         self.desc = [None] * NBUF
@@ -50,11 +55,9 @@ class Cta:
         self.bufstore = {}
 
     # async copies ------------------------------------------------------
-    def load(self, kind, t, issued):
+    def load(self, kind, limb, tile, t, issued):
         s = self.s
         b = issued % NBUF
-        U = s.UA if kind == "A" else s.UB
-        limb, tile = t // U, t % U
         if kind == "B":
             assert len(s.a_stored[limb]) == s.UA, "B tile loaded before its limb's A tiles were stored"
         st = self.bufstore.get(b)
@@ -88,10 +91,15 @@ class Cta:
         s = self.s
         issued = stored = 0
         fifo = []                       # (store, limb or None)
-        ready_hint = 0
         a_left = b_left = True
         stopped = False
         held = None
+
+        def publish(limb):
+            if limb is not None:
+                s.done[limb] += 1
+                if s.done[limb] == s.UA:
+                    s.order.append(limb)
 
         def wait_all_but(n):
             while not all(x["done"] for x in (self.stores[:-n] if n else self.stores)):
@@ -103,8 +111,7 @@ class Cta:
                 yield from wait_all_but(1)
                 for st, limb in fifo[:-1]:
                     assert st["done"], "limb counter raised before the store completed"
-                    if limb is not None:
-                        s.done[limb] += 1
+                    publish(limb)
                 fifo = fifo[-1:]
 
         def publish_all():
@@ -113,27 +120,21 @@ class Cta:
                 yield from wait_all_but(0)
                 for st, limb in fifo:
                     assert st["done"]
-                    if limb is not None:
-                        s.done[limb] += 1
+                    publish(limb)
                 fifo = []
 
         def wait_read_all():
             while not all(x["read"] for x in self.stores):
                 yield
 
-        def limb_ready(limb):
-            nonlocal ready_hint
-            if limb < ready_hint:
-                return True
-            if s.done[limb] >= s.UA:
-                ready_hint = max(ready_hint, limb + 1)
-                return True
-            return False
+        def b_limb(t):
+            pos = t // s.UB
+            return s.order[pos] if pos < len(s.order) else None
 
-        def do_load(kind, t):
+        def do_load(kind, limb, tile, t):
             nonlocal issued
             yield from wait_read_all()
-            self.load(kind, t, issued)
+            self.load(kind, limb, tile, t, issued)
             issued += 1
 
         while True:
@@ -149,10 +150,10 @@ class Cta:
             if stopped:
                 if stored + 1 == issued:
                     break
-            elif issued - stored < NBUF:
+            elif issued - stored < 2:
                 if held is not None:
-                    if limb_ready(held // s.UB):
-                        yield from do_load("B", held)
+                    if b_limb(held) is not None:
+                        yield from do_load("B", b_limb(held), held % s.UB, held)
                         held = None
                         progress = True
                 else:
@@ -161,12 +162,12 @@ class Cta:
                         pk = s.ctl[1]
                         if pk >= s.totalB:
                             b_left = False
-                        elif limb_ready(pk // s.UB):
+                        elif s.ctl[0] // s.UA >= pk // s.UB + self.window and b_limb(pk) is not None:
                             t = s.ctl[1]
                             s.ctl[1] += 1
                             if t < s.totalB:
-                                if limb_ready(t // s.UB):
-                                    yield from do_load("B", t)
+                                if b_limb(t) is not None:
+                                    yield from do_load("B", b_limb(t), t % s.UB, t)
                                 else:
                                     held = t
                                 claimed = True
@@ -176,7 +177,7 @@ class Cta:
                         t = s.ctl[0]
                         s.ctl[0] += 1
                         if t < s.totalA:
-                            yield from do_load("A", t)
+                            yield from do_load("A", t // s.UA, t % s.UA, t)
                             claimed = True
                         else:
                             a_left = False
@@ -184,8 +185,8 @@ class Cta:
                         t = s.ctl[1]
                         s.ctl[1] += 1
                         if t < s.totalB:
-                            if limb_ready(t // s.UB):
-                                yield from do_load("B", t)
+                            if b_limb(t) is not None:
+                                yield from do_load("B", b_limb(t), t % s.UB, t)
                             else:
                                 held = t
                             claimed = True
@@ -224,17 +225,17 @@ class Cta:
             if kind == "A":
                 s.computedA[t] += 1
             else:
-                s.computedB[t] += 1
+                s.computedB[limb * s.UB + tile] += 1     # every (limb, tile), not every ticket
             self.empty[b] += 1
             k += 1
 
 
-def simulate(limbs, UA, UB, ctas, seed, peek=True, max_steps=3_000_000):
+def simulate(limbs, UA, UB, ctas, seed, peek=True, window=0, max_steps=3_000_000):
     rng = random.Random(seed)
     sim = Sim(limbs, UA, UB, rng)
     gens = []
     for _ in range(ctas):
-        c = Cta(sim, peek)
+        c = Cta(sim, peek, window)
         gens += [c.producer(), c.compute()]
     alive = list(range(len(gens)))
     steps = 0
@@ -255,6 +256,7 @@ def simulate(limbs, UA, UB, ctas, seed, peek=True, max_steps=3_000_000):
         fn()
     assert all(c == 1 for c in sim.computedA) and all(c == 1 for c in sim.computedB)
     assert sim.done == [UA] * limbs
+    assert sorted(sim.order) == list(range(limbs))
     assert sim.ctl[2] == ctas
 
 
@@ -262,9 +264,9 @@ def simulate(limbs, UA, UB, ctas, seed, peek=True, max_steps=3_000_000):
                                                (45, 16, 16, 304), (1, 4, 4, 8), (20, 2, 8, 7),
                                                (120, 32, 32, 64)])
 @pytest.mark.parametrize("seed", range(3))
-@pytest.mark.parametrize("peek", [True, False])
-def test_protocol_random_interleavings(limbs, UA, UB, ctas, seed, peek):
-    simulate(limbs, UA, UB, ctas, seed, peek)
+@pytest.mark.parametrize("peek,window", [(True, 0), (False, 0), (True, 2), (True, 1 << 24)])
+def test_protocol_random_interleavings(limbs, UA, UB, ctas, seed, peek, window):
+    simulate(limbs, UA, UB, ctas, seed, peek, window)
 
 
 @pytest.mark.parametrize("n", [13, 14, 15, 16, 17])

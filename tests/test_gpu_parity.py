@@ -255,3 +255,24 @@ def test_fused_many_limbs_and_single_limb(orc):
             torch.cuda.synchronize()
             assert np.array_equal(host(d), data)
             assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("n", [13, 16, 17])
+def test_chained_launches_without_sync(orc, n):
+    """Dependent transforms queued back to back on one stream: forward /
+    inverse chains on one buffer, alternating between two plans (two work
+    areas), with no host synchronisation."""
+    N = 1 << n
+    primes = I.prime_chain(6, 2 * N)
+    data = I.batch_uniform(110 + n, 1, primes, N)
+    with G.Plan(N, primes) as p, G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1) as p2:
+        d = dev(data)
+        for _ in range(10):
+            p.forward(d, 1)
+            p2.inverse(d, 1)
+            p2.forward(d, 1)
+            p.inverse(d, 1)
+        p.forward(d, 1)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
+        assert p.device_status() == 0 and p2.device_status() == 0
