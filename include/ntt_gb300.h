@@ -82,7 +82,7 @@ enum {
 };
 
 typedef struct ntt_plan_opts {
-    uint32_t twiddle_mode;    /* NTT_TWIDDLE_*; AUTO picks per N */
+    uint32_t twiddle_mode;    /* NTT_TWIDDLE_*; AUTO: OT (ot_stages, default 1) for N >= 2^13, TABLE below */
     uint32_t ot_stages;       /* OT: final stages built on the fly, 1 or 2 (0 = 1) */
     uint32_t kernel;          /* NTT_KERNEL_* */
     uint32_t reserved[5];     /* must be zero */

@@ -157,7 +157,10 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     const uint32_t n = (uint32_t)__builtin_ctz(N);
     const uint32_t p1 = (uint32_t)ntt::split_p1((int)n);
     const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
-    uint32_t mode = o.twiddle_mode == NTT_TWIDDLE_AUTO ? NTT_TWIDDLE_TABLE : o.twiddle_mode;
+    // AUTO: OT on the last stage for two-pass sizes (measured faster than the
+    // table there, and half the last stage's twiddle traffic), table below
+    uint32_t mode = o.twiddle_mode;
+    if (mode == NTT_TWIDDLE_AUTO) mode = two_pass ? NTT_TWIDDLE_OT : NTT_TWIDDLE_TABLE;
     uint32_t ots = 0;
     if (mode == NTT_TWIDDLE_OT) {
         ots = o.ot_stages ? o.ot_stages : 1;

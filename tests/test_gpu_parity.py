@@ -276,3 +276,12 @@ def test_chained_launches_without_sync(orc, n):
         torch.cuda.synchronize()
         assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
         assert p.device_status() == 0 and p2.device_status() == 0
+
+
+@pytest.mark.parametrize("n,want_mode,want_ots", [(12, G.NTT_TWIDDLE_TABLE, 0), (13, G.NTT_TWIDDLE_OT, 1),
+                                                  (16, G.NTT_TWIDDLE_OT, 1), (17, G.NTT_TWIDDLE_OT, 1)])
+def test_auto_twiddle_mode(n, want_mode, want_ots):
+    N = 1 << n
+    with G.Plan(N, I.prime_chain(1, 2 * N)) as p:
+        info = p.info()
+        assert (info.twiddle_mode, info.ot_stages) == (want_mode, want_ots)
