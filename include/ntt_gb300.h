@@ -196,6 +196,57 @@ ntt_status ntt_execute_host(const ntt_plan* plan, const uint64_t* host_in, uint6
 ntt_status ntt_transform_noalloc(const ntt_plan* plan, uint64_t* data, uint32_t batch,
                                  uint32_t levels, uint32_t op, void* stream);
 
+/*
+ * Uneven batches (Sec. V and Sec. VI-A batch the limbs of equal transforms;
+ * this extends it to jobs of different sizes, levels and directions, as met
+ * at the different levels of an HE computation).
+ *
+ * A job transforms one array [batch][levels][N] of one plan in place, in one
+ * direction.  ntt_batch_submit runs a list of jobs in few launches: jobs of
+ * the same N >= 2^13, direction and OT setting (plans with the fused kernel)
+ * share one launch of the fused two-pass kernel, up to 16 jobs per launch, and
+ * these launches run concurrently on the batch object's internal streams,
+ * forked from and joined back to `stream`; jobs of N <= 2^12 or of
+ * NTT_KERNEL_PER_PASS plans are launched one by one on the same streams.  The
+ * whole submission is ordered on `stream` like a single call.  Results equal
+ * those of ntt_forward_levels / ntt_inverse_levels on each job.
+ *
+ * Ownership and concurrency: the caller keeps its plans and arrays alive until
+ * the work has finished; arrays of one submission must not overlap (rejected).
+ * The batch object owns internal streams and a work area; calls on one batch
+ * object must not overlap in time.  The work area grows when a submission
+ * needs more (a device synchronisation and an allocation), so make one
+ * submission of the largest shape before capturing submissions into a CUDA
+ * graph.  Must run with the batch's device current.
+ */
+typedef struct ntt_batch ntt_batch;
+
+typedef struct ntt_job {
+    const ntt_plan* plan;
+    uint64_t* data;           /* device, 16-byte aligned, [batch][levels][N] of the plan's N */
+    uint32_t batch;           /* >= 1 */
+    uint32_t levels;          /* 1 <= levels <= plan L: the plan's first `levels` primes */
+    uint32_t op;              /* NTT_OP_FORWARD or NTT_OP_INVERSE */
+    uint32_t reserved;        /* must be zero */
+} ntt_job;
+
+/* Create a batch object on the current device.  Errors: NTT_ERR_INVALID_ARG,
+ * NTT_ERR_OOM, NTT_ERR_CUDA. */
+ntt_status ntt_batch_create(ntt_batch** out);
+
+/* Free a batch object.  NULL is allowed.  Work it enqueued must have finished. */
+void ntt_batch_destroy(ntt_batch* batch);
+
+/* Enqueue njobs jobs.  Errors (nothing is enqueued): NTT_ERR_INVALID_ARG
+ * (NULL, njobs == 0, a bad job field, overlapping arrays, a plan or batch of
+ * another device), NTT_ERR_MISALIGNED, NTT_ERR_OOM (growing the work area);
+ * NTT_ERR_CUDA if a launch fails (earlier launches stay enqueued). */
+ntt_status ntt_batch_submit(ntt_batch* batch, const ntt_job* jobs, uint32_t njobs, void* stream);
+
+/* Device status word of the batch's fused launches (bits as for
+ * ntt_plan_device_status).  Synchronises the device, reads and clears it. */
+ntt_status ntt_batch_device_status(ntt_batch* batch, uint32_t* status);
+
 /* Plan facts, for callers and tests. */
 typedef struct ntt_plan_info {
     uint32_t N, L;

@@ -57,6 +57,11 @@ class PlanInfo(ctypes.Structure):
                 ("device", _u32), ("kernel", _u32), ("device_bytes", _u64)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("plan", _vp), ("data", _vp), ("batch", _u32), ("levels", _u32), ("op", _u32),
+                ("reserved", _u32)]
+
+
 class NttError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -102,6 +107,14 @@ def _lib():
             L.ntt_execute_host.argtypes = [_vp, _vp, _vp, _u32, _u32, _vp]
             L.ntt_transform_noalloc.restype = S
             L.ntt_transform_noalloc.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp]
+            L.ntt_batch_create.restype = S
+            L.ntt_batch_create.argtypes = [ctypes.POINTER(_vp)]
+            L.ntt_batch_destroy.restype = None
+            L.ntt_batch_destroy.argtypes = [_vp]
+            L.ntt_batch_submit.restype = S
+            L.ntt_batch_submit.argtypes = [_vp, ctypes.POINTER(Job), _u32, _vp]
+            L.ntt_batch_device_status.restype = S
+            L.ntt_batch_device_status.argtypes = [_vp, ctypes.POINTER(_u32)]
             L.ntt_plan_query.restype = S
             L.ntt_plan_query.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
             L.ntt_plan_device_status.restype = S
@@ -232,6 +245,41 @@ def ntt_transform_noalloc(plan: int, data, batch: int, levels: int, op: int, str
            "ntt_transform_noalloc")
 
 
+def ntt_batch_create() -> int:
+    h = _vp()
+    _check(_lib().ntt_batch_create(ctypes.byref(h)), "ntt_batch_create")
+    return h.value
+
+
+def ntt_batch_destroy(batch: int) -> None:
+    _lib().ntt_batch_destroy(batch)
+
+
+def make_jobs(jobs):
+    """jobs: iterable of (plan handle, data, batch, levels, op) -> ctypes array of Job."""
+    jobs = list(jobs)
+    arr = (Job * len(jobs))()
+    for i, (plan, data, batch, levels, op) in enumerate(jobs):
+        arr[i] = Job(plan, _addr(data), batch, levels, op, 0)
+    return arr
+
+
+def ntt_batch_submit(batch: int, jobs, stream=None) -> None:
+    """jobs: a ctypes Job array (make_jobs) or an iterable of (plan, data, batch, levels, op)."""
+    like = None
+    if not isinstance(jobs, ctypes.Array):
+        jobs = list(jobs)
+        like = next((j[1] for j in jobs if hasattr(j[1], "data_ptr")), None)
+        jobs = make_jobs(jobs)
+    _check(_lib().ntt_batch_submit(batch, jobs, len(jobs), _stream(stream, like)), "ntt_batch_submit")
+
+
+def ntt_batch_device_status(batch: int) -> int:
+    v = _u32()
+    _check(_lib().ntt_batch_device_status(batch, ctypes.byref(v)), "ntt_batch_device_status")
+    return v.value
+
+
 def ntt_plan_query(plan: int) -> PlanInfo:
     info = PlanInfo()
     _check(_lib().ntt_plan_query(plan, ctypes.byref(info)), "ntt_plan_query")
@@ -304,3 +352,33 @@ def declared_symbols() -> list[str]:
     with open(HEADER) as f:
         txt = f.read()
     return sorted(set(re.findall(r"^(?:ntt_status|void|const char\*)\s+(ntt_\w+)\s*\(", txt, re.M)))
+
+
+class Batch:
+    """Owner of an ntt_batch handle (usable as a context manager)."""
+
+    def __init__(self):
+        self.handle = ntt_batch_create()
+
+    def submit(self, jobs, stream=None):
+        ntt_batch_submit(self.handle, jobs, stream)
+
+    def device_status(self) -> int:
+        return ntt_batch_device_status(self.handle)
+
+    def close(self):
+        if self.handle:
+            ntt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

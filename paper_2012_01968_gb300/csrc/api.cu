@@ -34,6 +34,18 @@ cudaError_t launch_transform(const LaunchCtx& c, bool fwd)
     }
 }
 
+cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd)
+{
+    switch (c.n) {
+    case 13: return launch_jobs_n13(c, fwd);
+    case 14: return launch_jobs_n14(c, fwd);
+    case 15: return launch_jobs_n15(c, fwd);
+    case 16: return launch_jobs_n16(c, fwd);
+    case 17: return launch_jobs_n17(c, fwd);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // c = a * b mod q_l, two words per thread per step, canonical output.
 __global__ void __launch_bounds__(256) pointwise_kernel(const PrimeDev* __restrict__ primes, u32 L, u32 n,
                                                         const u64* __restrict__ a, const u64* __restrict__ b,

@@ -45,12 +45,13 @@ cudaError_t encode_2d(CUtensorMap* m, void* base, uint64_t inner, uint64_t outer
 
 // Column view: [N1 * limbs rows][N2 words], box 16 words x R1 rows.
 // Row view:    [N / 16 * limbs lines][16 words], box 16 words x row_tile/16 lines.
-cudaError_t encode_tile_maps(const LaunchCtx& c, int p1, int row_tile_words, CUtensorMap* mapC, CUtensorMap* mapR)
+cudaError_t encode_tile_maps(u64* data, u32 limbs, u32 n, int p1, int row_tile_words, CUtensorMap* mapC,
+                             CUtensorMap* mapR)
 {
-    const uint64_t N = 1ull << c.n, N1 = 1ull << p1, N2 = N >> p1;
-    cudaError_t e = encode_2d(mapC, c.data, N2, N1 * c.limbs, N2 * 8, 16, (uint32_t)N1);
+    const uint64_t N = 1ull << n, N1 = 1ull << p1, N2 = N >> p1;
+    cudaError_t e = encode_2d(mapC, data, N2, N1 * limbs, N2 * 8, 16, (uint32_t)N1);
     if (e != cudaSuccess) return e;
-    return encode_2d(mapR, c.data, 16, (N / 16) * c.limbs, 128, 16, (uint32_t)(row_tile_words / 16));
+    return encode_2d(mapR, data, 16, (N / 16) * limbs, 128, 16, (uint32_t)(row_tile_words / 16));
 }
 
 int device_sm_count()

@@ -4,5 +4,6 @@
 namespace ntt {
 
 cudaError_t launch_n15(const LaunchCtx& c, bool fwd) { return launch_two_pass<7, 8, 4, KMAX_ALL>(c, fwd); }
+cudaError_t launch_jobs_n15(const JobsCtx& c, bool fwd) { return launch_jobs<7, 8, 4, KMAX_ALL>(c, fwd); }
 
 }  // namespace ntt

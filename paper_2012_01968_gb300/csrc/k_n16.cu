@@ -4,5 +4,6 @@
 namespace ntt {
 
 cudaError_t launch_n16(const LaunchCtx& c, bool fwd) { return launch_two_pass<8, 8, 4, KMAX_ALL>(c, fwd); }
+cudaError_t launch_jobs_n16(const JobsCtx& c, bool fwd) { return launch_jobs<8, 8, 4, KMAX_ALL>(c, fwd); }
 
 }  // namespace ntt

@@ -78,14 +78,16 @@ cudaError_t launch_two_pass_ots(const LaunchCtx& c, bool fwd)
 
 // host helpers for the fused launch (fused_host.cu)
 u32 fused_window_limbs(size_t limb_bytes);
-cudaError_t encode_tile_maps(const LaunchCtx& c, int p1, int row_tile_words, CUtensorMap* mapC, CUtensorMap* mapR);
+cudaError_t encode_tile_maps(u64* data, u32 limbs, u32 n, int p1, int row_tile_words, CUtensorMap* mapC,
+                             CUtensorMap* mapR);
 int device_sm_count();
 
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS>
-cudaError_t launch_fused_dir(const LaunchCtx& c)
+// One persistent launch over all limbs of all jobs, both passes.
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ>
+cudaError_t launch_fused_dir(const JobsCtx& c)
 {
     using F = FusedCfg<P1, P2, LOGC_R, KMAX>;
-    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS>;
+    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS, MAXJ>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int occ = 0;
@@ -96,37 +98,52 @@ cudaError_t launch_fused_dir(const LaunchCtx& c)
     });
     if (attr_err != cudaSuccess) return attr_err;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    if (!c.work || c.work_limbs < c.limbs) return cudaErrorInvalidValue;
-    CUtensorMap mapC, mapR;
-    cudaError_t e = encode_tile_maps(c, P1, F::TILE_R, &mapC, &mapR);
-    if (e != cudaSuccess) return e;
+    if (c.njobs < 1 || c.njobs > (u32)MAXJ) return cudaErrorInvalidValue;
+    FusedParams<MAXJ> a{};
+    u64 limbs = 0;
+    for (u32 j = 0; j < c.njobs; ++j) {
+        const JobCtx& J = c.jobs[j];
+        cudaError_t e = encode_tile_maps(J.data, J.limbs, c.n, P1, F::TILE_R, &a.mapC[j], &a.mapR[j]);
+        if (e != cudaSuccess) return e;
+        a.job[j].primes = J.primes;
+        a.job[j].tw = J.tw;
+        a.job[j].ota = FWD ? J.ota_f : J.ota_i;
+        a.job[j].otb = FWD ? J.otb_f : J.otb_i;
+        a.job[j].tw_len = J.tw_len;
+        a.job[j].L = J.L;
+        a.job[j].limb0 = (u32)limbs;
+        limbs += J.limbs;
+    }
+    if (limbs == 0 || limbs > 0x7FFFFFFFull || !c.work || c.work_limbs < limbs) return cudaErrorInvalidValue;
     constexpr u32 UC = F::R2 / 16, UR = F::R1 / F::CR;
-    const u64 units = (u64)c.limbs * (UC + UR);
+    const u64 units = limbs * (UC + UR);
     const u64 slots = (u64)device_sm_count() * (u64)occ;
     const u32 grid = (u32)(units < slots ? units : slots);
-    FusedArgs a;
-    a.primes = c.primes;
-    a.tw = c.tw;
-    a.ota = FWD ? c.ota_f : c.ota_i;
-    a.otb = FWD ? c.otb_f : c.otb_i;
     a.ctl = c.work;
     a.status = c.status;
-    a.tw_len = c.tw_len;
-    a.L = c.L;
-    a.limbs = c.limbs;
+    a.njobs = c.njobs;
+    a.limbs = (u32)limbs;
     a.a_window = fused_window_limbs(sizeof(u64) << (P1 + P2));
     a.max_polls = 1u << 22;
-    kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(mapC, mapR, a);
+    kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(a);
     return cudaGetLastError();
 }
 
-template <int P1, int P2, int LOGC_R, int KMAX, int OTS>
-cudaError_t launch_fused(const LaunchCtx& c, bool fwd)
+template <int P1, int P2, int LOGC_R, int KMAX, int MAXJ>
+cudaError_t launch_fused(const JobsCtx& c, bool fwd)
 {
-    return fwd ? launch_fused_dir<P1, P2, LOGC_R, KMAX, true, OTS>(c)
-               : launch_fused_dir<P1, P2, LOGC_R, KMAX, false, OTS>(c);
+    switch (c.ots) {
+    case 0: return fwd ? launch_fused_dir<P1, P2, LOGC_R, KMAX, true, 0, MAXJ>(c)
+                       : launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 0, MAXJ>(c);
+    case 1: return fwd ? launch_fused_dir<P1, P2, LOGC_R, KMAX, true, 1, MAXJ>(c)
+                       : launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 1, MAXJ>(c);
+    case 2: return fwd ? launch_fused_dir<P1, P2, LOGC_R, KMAX, true, 2, MAXJ>(c)
+                       : launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 2, MAXJ>(c);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
+// A single call: one launch per pass, or the fused kernel with one job.
 template <int P1, int P2, int LOGC_R, int KMAX_R>
 cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
 {
@@ -138,12 +155,16 @@ cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
         default: return cudaErrorInvalidValue;
         }
     }
-    switch (c.ots) {
-    case 0: return launch_fused<P1, P2, LOGC_R, KMAX_R, 0>(c, fwd);
-    case 1: return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(c, fwd);
-    case 2: return launch_fused<P1, P2, LOGC_R, KMAX_R, 2>(c, fwd);
-    default: return cudaErrorInvalidValue;
-    }
+    const JobCtx job{c.data, c.limbs, c.L, c.primes, c.tw, c.tw_len, c.ota_f, c.otb_f, c.ota_i, c.otb_i};
+    const JobsCtx jc{&job, 1u, c.n, c.ots, c.status, c.work, c.work_limbs, c.stream};
+    return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(jc, fwd);
+}
+
+// Several jobs of one size in one fused launch.
+template <int P1, int P2, int LOGC_R, int KMAX_R>
+cudaError_t launch_jobs(const JobsCtx& c, bool fwd)
+{
+    return launch_fused<P1, P2, LOGC_R, KMAX_R, FUSED_MAX_JOBS>(c, fwd);
 }
 
 }  // namespace ntt

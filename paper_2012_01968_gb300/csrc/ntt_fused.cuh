@@ -40,10 +40,17 @@
 // tile waits for is eventually published.  Every wait is bounded; a wait that
 // runs out sets the plan's status word and the CTA stops.
 //
-// Work area (plan-owned, zero between launches; 4 + 2 * limbs words): [0]
-// next A ticket, [1] next B ticket, [2] CTAs finished, [3] limbs published,
-// [4 + limb] A tiles of the limb written back, [4 + limbs + i] the i-th
-// published limb plus one (0 while not yet published).  The last CTA to
+// Jobs: one launch may transform several independent arrays ("jobs", up to
+// MAXJ), each with its own tensor maps and its own plan tables, all of the
+// same size and direction.  Limbs are numbered over the launch (job j owns
+// limbs [limb0_j, limb0_j + limbs_j)); tickets, counters and the publication
+// order use that numbering, and the producer finds a limb's job by binary
+// search over limb0.
+//
+// Work area (owned by the caller, zero between launches; 4 + 2 * limbs
+// words): [0] next A ticket, [1] next B ticket, [2] CTAs finished, [3] limbs
+// published, [4 + limb] A tiles of the limb written back, [4 + limbs + i] the
+// i-th published limb plus one (0 while not yet published).  The last CTA to
 // finish zeroes it again.
 #pragma once
 #include "ntt_pass.cuh"
@@ -58,16 +65,29 @@ namespace ntt {
 // bits of the device status word
 enum : u32 { STATUS_DEP_TIMEOUT = 1u, STATUS_TMA_TIMEOUT = 2u };
 
-struct FusedArgs {
+// One job of a launch: a [batch][L][N] array and the tables of its plan.
+struct FusedJob {
     const PrimeDev* primes;  // [L]
     const Tw* tw;            // [L][tw_len]
     const Tw* ota;           // [L][2^p2]      OT A factors, this direction
     const Tw* otb;           // [L][p2 << p1]  OT B factors, this direction
+    u32 tw_len;
+    u32 L;                   // primes per polynomial (local limb l uses prime l % L)
+    u32 limb0;               // first limb of the job in the launch's numbering
+    u32 reserved;
+};
+
+// Kernel parameters (passed by value as one __grid_constant__ block, so the
+// tensor maps live in parameter space).
+template <int MAXJ>
+struct FusedParams {
+    CUtensorMap mapC[MAXJ];  // column view of each job's data
+    CUtensorMap mapR[MAXJ];  // row view of each job's data
+    FusedJob job[MAXJ];
     u32* ctl;                // work area (see the file comment)
     u32* status;             // persistent error word
-    u32 tw_len;
-    u32 L;                   // primes per polynomial (limb l uses prime l % L)
-    u32 limbs;
+    u32 njobs;
+    u32 limbs;               // all jobs
     u32 a_window;            // limbs the A queue may run ahead before ready B tiles are preferred
     u32 max_polls;           // bound of every wait loop
 };
@@ -88,7 +108,7 @@ struct FusedCfg {
     static constexpr size_t TW_OFF = (size_t)TILE * 8;
     static constexpr size_t PR_OFF = TW_OFF + (size_t)R1 * sizeof(Tw);
     static constexpr size_t DESC_OFF = PR_OFF + sizeof(PrimeDev);
-    static constexpr size_t BUF = (DESC_OFF + 16 + 1023) / 1024 * 1024;
+    static constexpr size_t BUF = (DESC_OFF + 32 + 1023) / 1024 * 1024;
     static constexpr int NBUF = 3;                     // ring of tile buffers
     static constexpr size_t SMEM = NBUF * BUF + 1024;
     static constexpr int MIN_CTAS =
@@ -98,9 +118,12 @@ struct FusedCfg {
 // unit descriptor written by the producer into the buffer it fills
 struct __align__(16) UnitDesc {
     u32 kind;    // KIND_A, KIND_B or KIND_STOP
-    u32 limb;
+    u32 limb;    // in the launch's numbering
     u32 tile;
-    u32 prime;   // limb % L
+    u32 prime;   // local limb % L of its job
+    u32 job;
+    u32 local;   // limb within its job
+    u32 pad[2];
 };
 enum : u32 { KIND_A = 0u, KIND_B = 1u, KIND_STOP = 2u };
 
@@ -120,10 +143,9 @@ __device__ __forceinline__ bool compute_any(bool flag)
     return r != 0;
 }
 
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS>
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ>
 __global__ void __launch_bounds__(FusedCfg<P1, P2, LOGC_R, KMAX>::THREADS, FusedCfg<P1, P2, LOGC_R, KMAX>::MIN_CTAS)
-ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant__ CUtensorMap mapR,
-                 const FusedArgs a)
+ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ> a)
 {
     using F = FusedCfg<P1, P2, LOGC_R, KMAX>;
     constexpr int NT = F::NT;
@@ -168,6 +190,20 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
         u32 held = NONE;                         // claimed B ticket waiting for its limb
         u32 idle = 0;
 
+        // job of a limb of the launch (binary search over limb0)
+        auto job_of = [&](u32 limb) -> u32 {
+            u32 lo = 0;
+            if constexpr (MAXJ > 1) {
+                u32 hi = a.njobs;
+                while (hi - lo > 1) {
+                    const u32 mid = (lo + hi) >> 1;
+                    if (a.job[mid].limb0 <= limb) lo = mid;
+                    else hi = mid;
+                }
+            }
+            return lo;
+        };
+
         auto publish_entry = [&](u32 e) {
             if (e & 0x80000000u) {
                 const u32 limb = e & 0x7FFFFFFFu;
@@ -200,12 +236,16 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
         };
         auto load = [&](u32 kind, u32 limb, u32 tile) {
             const int b = (int)(issued % NBUF);
-            const u32 pi = limb % a.L;
+            const u32 j = job_of(limb);
+            const FusedJob& J = a.job[j];
+            const u32 local = limb - J.limb0, pi = local % J.L;
             volatile UnitDesc* d = buf_desc(b);
             d->kind = kind;
             d->limb = limb;
             d->tile = tile;
             d->prime = pi;
+            d->job = j;
+            d->local = local;
             // the buffer's previous store has read it: at most one unit is
             // unstored when a unit is claimed, so at most two stores were
             // committed after that one; waiting for all but the newest suffices
@@ -214,14 +254,14 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
             u64* dst = buf_tile(b);
             if (is_col(kind)) {
                 mbar_arrive_expect_tx(&full[b], F::TILE_C * 8 + F::R1 * (u32)sizeof(Tw) + (u32)sizeof(PrimeDev));
-                tma_load_2d(dst, &mapC, (int)(tile * 16), (int)(limb * F::R1), &full[b]);
-                bulk_load(buf_tw(b), a.tw + (size_t)pi * a.tw_len, F::R1 * (u32)sizeof(Tw), &full[b]);
+                tma_load_2d(dst, &a.mapC[j], (int)(tile * 16), (int)(local * F::R1), &full[b]);
+                bulk_load(buf_tw(b), J.tw + (size_t)pi * J.tw_len, F::R1 * (u32)sizeof(Tw), &full[b]);
             } else {
                 mbar_arrive_expect_tx(&full[b], F::TILE_R * 8 + (u32)sizeof(PrimeDev));
-                tma_load_2d(dst, &mapR, 0, (int)(limb * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), &full[b]);
+                tma_load_2d(dst, &a.mapR[j], 0, (int)(local * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), &full[b]);
                 // table runs of the row pass, into L2: stage sl of rows [u0, u0 + CR)
                 // reads CR << sl consecutive entries (mirrored for the inverse)
-                const Tw* base = a.tw + (size_t)pi * a.tw_len;
+                const Tw* base = J.tw + (size_t)pi * J.tw_len;
                 const u32 u0 = tile * (u32)F::CR;
 #pragma unroll
                 for (int sl = 0; sl < P2 - OTS; ++sl) {
@@ -230,7 +270,7 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
                     bulk_prefetch_l2(base + start, ((u32)F::CR << sl) * (u32)sizeof(Tw));
                 }
             }
-            bulk_load(buf_pr(b), a.primes + pi, (u32)sizeof(PrimeDev), &full[b]);
+            bulk_load(buf_pr(b), J.primes + pi, (u32)sizeof(PrimeDev), &full[b]);
             ++issued;
         };
         // limb of B ticket t: the (t / UB)-th published limb, NONE while unpublished
@@ -250,20 +290,23 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
             }
         };
 
-        prefetch_tensormap(&mapC);
-        prefetch_tensormap(&mapR);
+        for (u32 j = 0; j < a.njobs && j < (u32)MAXJ; ++j) {
+            prefetch_tensormap(&a.mapC[j]);
+            prefetch_tensormap(&a.mapR[j]);
+        }
         for (;;) {
             bool progress = false;
             // store computed tiles, in order
             while (stored < issued && mbar_test(&empty[stored % NBUF], (stored / NBUF) & 1u)) {
                 const int b = (int)(stored % NBUF);
                 const volatile UnitDesc* d = buf_desc(b);
-                const u32 kind = d->kind, limb = d->limb, tile = d->tile;
+                const u32 kind = d->kind, limb = d->limb, tile = d->tile, local = d->local;
+                const u32 j = MAXJ > 1 ? d->job : 0u;
                 const u64* src = buf_tile(b);
                 if (is_col(kind))
-                    tma_store_2d(&mapC, (int)(tile * 16), (int)(limb * F::R1), src);
+                    tma_store_2d(&a.mapC[j], (int)(tile * 16), (int)(local * F::R1), src);
                 else
-                    tma_store_2d(&mapR, 0, (int)(limb * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), src);
+                    tma_store_2d(&a.mapR[j], 0, (int)(local * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), src);
                 bulk_commit();
                 const u32 e = kind == KIND_A ? (0x80000000u | limb) : 0u;
                 if (qn == 0) q0 = e;
@@ -369,9 +412,10 @@ ntt_fused_kernel(const __grid_constant__ CUtensorMap mapC, const __grid_constant
                 compute_tile<P1, 4, KMAX, false, false, X_B, true, true, 0, true, NT, NoHook, true>(
                     sm, pr, buf_tw(b), nullptr, nullptr, 0u, 0u, tid);
         } else {
-            const Tw* tw = a.tw + (size_t)pi * a.tw_len;
-            const Tw* ota = a.ota ? a.ota + (size_t)pi * F::R2 : nullptr;
-            const Tw* otb = a.otb ? a.otb + (size_t)pi * ((size_t)P2 << P1) : nullptr;
+            const FusedJob& J = a.job[MAXJ > 1 ? buf_desc(b)->job : 0u];
+            const Tw* tw = J.tw + (size_t)pi * J.tw_len;
+            const Tw* ota = J.ota ? J.ota + (size_t)pi * F::R2 : nullptr;
+            const Tw* otb = J.otb ? J.otb + (size_t)pi * ((size_t)P2 << P1) : nullptr;
             if constexpr (FWD)
                 compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
                     sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);

@@ -68,6 +68,36 @@ struct LaunchCtx {
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
+
+// One job of a multi-job fused launch: an array [batch][L][N] and the tables
+// of its plan.
+struct JobCtx {
+    u64* data;
+    u32 limbs;               // batch x L
+    u32 L;                   // primes per polynomial (local limb l uses prime l % L)
+    const PrimeDev* primes;
+    const Tw* tw;
+    u32 tw_len;
+    const Tw* ota_f;
+    const Tw* otb_f;
+    const Tw* ota_i;
+    const Tw* otb_i;
+};
+
+// Jobs of one size N = 2^n and one OT setting in one launch of the fused
+// two-pass kernel (13 <= n <= 17, 1 <= njobs <= FUSED_MAX_JOBS).
+constexpr int FUSED_MAX_JOBS = 16;
+struct JobsCtx {
+    const JobCtx* jobs;
+    u32 njobs;
+    u32 n;
+    u32 ots;
+    u32* status;
+    u32* work;               // zero, fused_work_words(work_limbs) words
+    u32 work_limbs;          // >= the jobs' limbs
+    cudaStream_t stream;
+};
+cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
 cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a, const u64* b,
                              u64* out, u32 limbs, cudaStream_t s);
 
@@ -78,6 +108,11 @@ cudaError_t launch_n14(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n15(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n16(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n17(const LaunchCtx& c, bool fwd);
+cudaError_t launch_jobs_n13(const JobsCtx& c, bool fwd);
+cudaError_t launch_jobs_n14(const JobsCtx& c, bool fwd);
+cudaError_t launch_jobs_n15(const JobsCtx& c, bool fwd);
+cudaError_t launch_jobs_n16(const JobsCtx& c, bool fwd);
+cudaError_t launch_jobs_n17(const JobsCtx& c, bool fwd);
 
 }  // namespace ntt
 
