@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--streams", type=int, default=2,
                     help="independent steps spread over this many streams (one plan each)")
+    ap.add_argument("--no-batch-compare", action="store_true",
+                    help="skip the per-limb C2 path and the uneven 96-job batch")
     ap.add_argument("--launch-steps", type=int, default=500,
                     help="steps of the single-stream pass that times each launch")
     return ap.parse_args()
@@ -222,6 +224,98 @@ def run_reference(args, metric, unit, w):
     print(json.dumps(line), flush=True)
 
 
+def per_limb_c2(G, torch, w, host, steps):
+    """The plain per-limb path on the C2 polynomial: one single-prime plan per
+    limb and one launch per limb and direction (45 x 2 launches per step)."""
+    L = len(w.primes)
+    plans = [G.Plan(w.N, [q]) for q in w.primes]
+    lib = G.lib()
+    try:
+        bufs = [torch.from_numpy(host[0, l].view(np.int64).copy()).cuda() for l in range(L)]
+        ref = [b.clone() for b in bufs]
+        s = torch.cuda.Stream()
+
+        def step():
+            for l in range(L):
+                lib.ntt_forward(plans[l].handle, bufs[l].data_ptr(), 1, s.cuda_stream)
+                lib.ntt_inverse(plans[l].handle, bufs[l].data_ptr(), 1, s.cuda_stream)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        if not all(torch.equal(a, b) for a, b in zip(bufs, ref)):
+            raise RuntimeError("per-limb round trip mismatch")
+        ms = e0.elapsed_time(e1)
+        return {"value": 2 * L * steps / (ms / 1e3), "unit": "limb-NTT/s", "steps": steps,
+                "launches_per_step": 2 * L, "ms_per_step": ms / steps}
+    finally:
+        for p in plans:
+            p.close()
+
+
+def batched_c4(G, torch, reps):
+    """The uneven 96-job workload (N in 2^14..2^17, L in [1, 60], mixed
+    directions): one ntt_batch_submit, its CUDA-graph replay, and the same
+    jobs as 96 single calls on one stream."""
+    w = I.workload_c4()
+    chain = I.chain_2_18_60()
+    plans = {n: G.Plan(1 << n, chain) for n in range(14, 18)}
+    lib = G.lib()
+    try:
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(w.seed)
+        # residues below 2^59 < every prime of the chain (timing input; parity is tested elsewhere)
+        bufs = [torch.randint(0, 1 << 59, (j.L * j.N,), generator=gen, dtype=torch.int64, device="cuda")
+                for j in w.jobs]
+        spec = [(plans[I.log2_exact(j.N)].handle, b, 1, j.L, G.NTT_OP_FORWARD if j.dir > 0 else G.NTT_OP_INVERSE)
+                for j, b in zip(w.jobs, bufs)]
+        jobs = G.make_jobs(spec)
+        limbs = sum(j.L for j in w.jobs)
+        s = torch.cuda.Stream()
+        out = {"jobs": len(w.jobs), "limb_ntts_per_submission": limbs,
+               "bytes_per_submission": sum(16 * j.L * j.N for j in w.jobs)}
+
+        def timed(fn):
+            # everything on stream s: graph replays run on torch's current stream
+            with torch.cuda.stream(s):
+                for _ in range(2):
+                    fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for _ in range(reps):
+                    fn()
+                e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            return {"value": limbs / (ms / 1e3), "unit": "limb-NTT/s", "ms_per_submission": ms}
+
+        with G.Batch() as b:
+            out["batched"] = timed(lambda: b.submit(jobs, s))
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                b.submit(jobs, s)
+            out["graph"] = timed(g.replay)
+            if b.device_status() != 0:
+                raise RuntimeError("batch device status reports a failed bounded wait")
+
+        def singles():
+            for h, buf, bt, lv, op in spec:
+                (lib.ntt_forward_levels if op == G.NTT_OP_FORWARD else lib.ntt_inverse_levels)(
+                    h, buf.data_ptr(), bt, lv, s.cuda_stream)
+        out["per_job_calls"] = timed(singles)
+        return out
+    finally:
+        for p in plans.values():
+            p.close()
+
+
 def config_dict(w, args, ws):
     return {"workload": "c2_n65536_l45_fwd_inv", "N": w.N, "L": len(w.primes), "polys_per_step": 1,
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
@@ -374,6 +468,11 @@ def main():
         e2e = {"value": 2 * L * E / el, "unit": unit, "h2d_bytes_per_step": poly_bytes,
                "d2h_bytes_per_step": poly_bytes, "steps": E}
 
+    per_limb = batched = None
+    if ws == 1 and not args.no_batch_compare:
+        per_limb = per_limb_c2(G, torch, w, host, 100)
+        batched = batched_c4(G, torch, 10)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -401,6 +500,8 @@ def main():
                  "passes": int(info.passes), "pass1_log2": int(info.pass1_log2),
                  "kernel": "fused" if info.kernel == G.NTT_KERNEL_FUSED else "per_pass"},
         "e2e": e2e,
+        "per_limb_path": per_limb,
+        "batched_uneven_c4": batched,
         "gpu_launches": K * 2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes)),
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -151,10 +151,14 @@ enum {
 /*
  * Host-memory convenience call: copy `batch` polynomials from host_in to the
  * device, apply the operations in `ops` (forward, inverse, or forward then
- * inverse), copy the result to host_out, and wait for completion.  Uses a
- * device staging buffer owned by the plan (grown on first use and kept until
- * ntt_plan_destroy); host_in and host_out may be the same array and should be
- * page-locked for full copy bandwidth.  Calls on one plan are serialised.
+ * inverse), copy the result to host_out, and wait for completion.  The data
+ * moves in segments (limb ranges or groups of polynomials) over three internal
+ * streams of the plan, so the copies of one segment overlap the transforms of
+ * the others; the work starts after everything enqueued earlier on `stream`.
+ * Uses a device staging buffer, the streams and per-stream work areas owned by
+ * the plan (grown on first use and kept until ntt_plan_destroy); host_in and
+ * host_out may be the same array and should be page-locked for full copy
+ * bandwidth.  Calls on one plan are serialised.
  */
 ntt_status ntt_execute_host(const ntt_plan* plan, const uint64_t* host_in, uint64_t* host_out,
                             uint32_t batch, uint32_t ops, void* stream);

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <vector>
 #include <cstring>
 
 #include "arith.cuh"
@@ -154,43 +155,115 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
     if (!cp || !host_in || !host_out || batch == 0) return NTT_ERR_INVALID_ARG;
     if (ops == 0 || (ops & ~(uint32_t)(NTT_OP_FORWARD | NTT_OP_INVERSE))) return NTT_ERR_INVALID_ARG;
     ntt_plan* p = const_cast<ntt_plan*>(cp);
-    const size_t bytes = (size_t)batch * p->L * p->N * sizeof(uint64_t);
-    std::lock_guard<std::mutex> g(p->stage_mu);
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaSuccess;
-    if (p->stage_bytes < bytes) {
-        if (p->d_stage) {
-            e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return to_status(e);
-            cudaFree(p->d_stage);
-            p->d_stage = nullptr;
-            p->stage_bytes = 0;
+    const uint64_t limbs64 = (uint64_t)batch * p->L;
+    if (limbs64 > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
+    const uint32_t L = p->L;
+    const size_t N = p->N;
+    const size_t bytes = (size_t)limbs64 * N * sizeof(uint64_t);
+
+    // Segments of the data: a limb range inside one polynomial (tables viewed
+    // from its first prime), or a group of whole polynomials.  All segments
+    // are copied in back to back on one stream, transformed on the compute
+    // streams as soon as their copy has landed, and copied out on another
+    // stream as soon as their transforms are done, so the two copy directions
+    // and the transforms overlap.
+    struct Seg {
+        uint32_t first, count, prime0, lview;
+    };
+    constexpr uint32_t kSegments = ntt_plan::kHostSegments;
+    std::vector<Seg> segs;
+    if (batch >= kSegments) {
+        const uint32_t per = (batch + kSegments - 1) / kSegments;
+        for (uint32_t b0 = 0; b0 < batch; b0 += per) {
+            const uint32_t nb = batch - b0 < per ? batch - b0 : per;
+            segs.push_back(Seg{b0 * L, nb * L, 0, L});
         }
+    } else {
+        const uint32_t pieces = kSegments / batch;                 // batch * pieces <= kSegments
+        const uint32_t c = (L + pieces - 1) / pieces;
+        for (uint32_t b0 = 0; b0 < batch; ++b0)
+            for (uint32_t r = 0; r < L; r += c) {
+                const uint32_t cnt = L - r < c ? L - r : c;
+                segs.push_back(Seg{b0 * L + r, cnt, r, cnt});
+            }
+    }
+    if (segs.size() > kSegments) return NTT_ERR_INVALID_ARG;      // cannot happen: one event pair per segment
+    uint32_t seg_max = 0;
+    for (const Seg& g : segs) seg_max = g.count > seg_max ? g.count : seg_max;
+
+    std::lock_guard<std::mutex> g(p->stage_mu);
+    cudaError_t e = cudaSuccess;
+    auto mk_stream = [&](cudaStream_t& st) {
+        if (e == cudaSuccess && !st) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    };
+    auto mk_event = [&](cudaEvent_t& ev) {
+        if (e == cudaSuccess && !ev) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    };
+    mk_stream(p->h_in);
+    mk_stream(p->h_out);
+    for (int k = 0; k < ntt_plan::kHostCompute; ++k) mk_stream(p->h_comp[k]);
+    mk_event(p->hfork);
+    for (uint32_t k = 0; k < kSegments; ++k) {
+        mk_event(p->h_loaded[k]);
+        mk_event(p->h_done[k]);
+    }
+    if (e != cudaSuccess) return to_status(e);
+    if (p->stage_bytes < bytes || p->hwork_limbs < seg_max) {
+        // the call is synchronous, so nothing of this plan's host path is in flight
+        cudaFree(p->d_stage);
+        cudaFree(p->d_hwork);
+        p->d_stage = nullptr;
+        p->d_hwork = nullptr;
+        p->stage_bytes = 0;
+        p->hwork_limbs = 0;
+        const size_t wwords = ntt::fused_work_words(seg_max) * ntt_plan::kHostCompute;
         e = cudaMalloc(&p->d_stage, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_hwork, wwords * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMemset(p->d_hwork, 0, wwords * sizeof(uint32_t));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return to_status(e);
         }
         p->stage_bytes = bytes;
+        p->hwork_limbs = seg_max;
     }
-    e = cudaMemcpyAsync(p->d_stage, host_in, bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return to_status(e);
-    if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED && p->work_limbs < batch * p->L) {
-        e = ntt_internal_grow_work(p, batch * p->L);
-        if (e != cudaSuccess) return to_status(e);
+
+    // after the caller's earlier work on `stream`
+    e = cudaEventRecord(p->hfork, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->h_in, p->hfork, 0);
+    for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
+        const size_t off = (size_t)segs[i].first * N, nbytes = (size_t)segs[i].count * N * sizeof(uint64_t);
+        e = cudaMemcpyAsync(p->d_stage + off, host_in + off, nbytes, cudaMemcpyHostToDevice, p->h_in);
+        if (e == cudaSuccess) e = cudaEventRecord(p->h_loaded[i], p->h_in);
     }
-    const ntt::LaunchCtx c = p->ctx(p->d_stage, batch * p->L, p->L, s);
-    if (ops & NTT_OP_FORWARD) {
-        e = ntt::launch_transform(c, true);
-        if (e != cudaSuccess) return to_status(e);
+    for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
+        const Seg& sg = segs[i];
+        const int k = (int)(i % ntt_plan::kHostCompute);
+        cudaStream_t s = p->h_comp[k];
+        const size_t off = (size_t)sg.first * N;
+        e = cudaStreamWaitEvent(s, p->h_loaded[i], 0);
+        if (e != cudaSuccess) break;
+        ntt::LaunchCtx c = p->ctx_range(p->d_stage + off, sg.count, sg.lview, sg.prime0, s);
+        c.work = p->d_hwork + ntt::fused_work_words(p->hwork_limbs) * (size_t)k;
+        c.work_limbs = p->hwork_limbs;
+        if (ops & NTT_OP_FORWARD) e = ntt::launch_transform(c, true);
+        if (e == cudaSuccess && (ops & NTT_OP_INVERSE)) e = ntt::launch_transform(c, false);
+        if (e == cudaSuccess) e = cudaEventRecord(p->h_done[i], s);
     }
-    if (ops & NTT_OP_INVERSE) {
-        e = ntt::launch_transform(c, false);
-        if (e != cudaSuccess) return to_status(e);
+    for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
+        const size_t off = (size_t)segs[i].first * N, nbytes = (size_t)segs[i].count * N * sizeof(uint64_t);
+        e = cudaStreamWaitEvent(p->h_out, p->h_done[i], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out + off, p->d_stage + off, nbytes, cudaMemcpyDeviceToHost, p->h_out);
     }
-    e = cudaMemcpyAsync(host_out, p->d_stage, bytes, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return to_status(e);
-    return to_status(cudaStreamSynchronize(s));
+    // drain every stream, also after an error, before the staging can be reused
+    cudaError_t se = cudaStreamSynchronize(p->h_in);
+    for (int k = 0; k < ntt_plan::kHostCompute; ++k) {
+        const cudaError_t sk = cudaStreamSynchronize(p->h_comp[k]);
+        if (se == cudaSuccess) se = sk;
+    }
+    const cudaError_t so = cudaStreamSynchronize(p->h_out);
+    if (se == cudaSuccess) se = so;
+    return to_status(e != cudaSuccess ? e : se);
 }
 
 const char* ntt_status_string(ntt_status s)

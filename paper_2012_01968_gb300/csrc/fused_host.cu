@@ -1,4 +1,5 @@
 // Host helpers for the fused launch: tensor maps and per-launch scratch.
+#include <atomic>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -54,22 +55,40 @@ cudaError_t encode_tile_maps(u64* data, u32 limbs, u32 n, int p1, int row_tile_w
     return encode_2d(mapR, data, 16, (N / 16) * limbs, 128, 16, (uint32_t)(row_tile_words / 16));
 }
 
-int device_sm_count()
+namespace {
+
+// SM count and L2 size of a device, queried once per device
+struct DevAttrs {
+    std::atomic<int> sms{0}, l2{0};
+};
+DevAttrs g_attrs[64];
+
+const DevAttrs& attrs()
 {
-    int dev = 0, sms = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
+    DevAttrs& a = g_attrs[dev >= 0 && dev < 64 ? dev : 0];
+    if (a.sms.load(std::memory_order_relaxed) == 0) {
+        int sms = 0, l2 = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        a.l2.store(l2 > 0 ? l2 : (32 << 20), std::memory_order_relaxed);
+        a.sms.store(sms > 0 ? sms : 1, std::memory_order_release);
+    }
+    return a;
 }
+
+}  // namespace
+
+int device_sm_count() { return attrs().sms.load(std::memory_order_acquire); }
 
 // Limbs whose first-pass results may wait in L2 for their second pass: the
 // window of the fused kernel's A queue, sized to 3/8 of the device's L2.
 u32 fused_window_limbs(size_t limb_bytes)
 {
-    int dev = 0, l2 = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    const size_t budget = (size_t)(l2 > 0 ? l2 : (32 << 20)) / 8 * 3;
+    const DevAttrs& a = attrs();
+    (void)a.sms.load(std::memory_order_acquire);
+    const size_t budget = (size_t)a.l2.load(std::memory_order_relaxed) / 8 * 3;
     const size_t w = budget / (limb_bytes ? limb_bytes : 1);
     return (u32)(w < 2 ? 2 : (w > 0xFFFFFFu ? 0xFFFFFFu : w));
 }

@@ -135,6 +135,16 @@ void free_plan(ntt_plan* p)
     cudaFree(p->d_ota_i);
     cudaFree(p->d_otb_i);
     cudaFree(p->d_stage);
+    cudaFree(p->d_hwork);
+    if (p->h_in) cudaStreamDestroy(p->h_in);
+    if (p->h_out) cudaStreamDestroy(p->h_out);
+    for (int k = 0; k < ntt_plan::kHostCompute; ++k)
+        if (p->h_comp[k]) cudaStreamDestroy(p->h_comp[k]);
+    if (p->hfork) cudaEventDestroy(p->hfork);
+    for (int k = 0; k < ntt_plan::kHostSegments; ++k) {
+        if (p->h_loaded[k]) cudaEventDestroy(p->h_loaded[k]);
+        if (p->h_done[k]) cudaEventDestroy(p->h_done[k]);
+    }
     cudaFree(p->d_status);
     cudaFree(p->d_work);
     delete p;

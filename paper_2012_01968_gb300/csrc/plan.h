@@ -135,10 +135,18 @@ struct ntt_plan {
     uint32_t* d_work = nullptr;           // fused kernel's work area: fused_work_words(work_limbs) words
     uint32_t work_limbs = 0;
     std::mutex work_mu;
-    // staging for ntt_execute_host
+    // staging for ntt_execute_host: device copy of the data; a copy-in
+    // stream, a copy-out stream and kHostCompute compute streams (with one
+    // work area each), ordered per segment by events
+    static constexpr int kHostCompute = 2;
+    static constexpr int kHostSegments = 6;
     std::mutex stage_mu;
     uint64_t* d_stage = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t h_in = nullptr, h_out = nullptr, h_comp[kHostCompute] = {};
+    cudaEvent_t hfork = nullptr, h_loaded[kHostSegments] = {}, h_done[kHostSegments] = {};
+    uint32_t* d_hwork = nullptr;
+    uint32_t hwork_limbs = 0;             // per compute stream
 
     ntt::LaunchCtx ctx(uint64_t* data, uint32_t limbs, uint32_t Lused, cudaStream_t s) const
     {
@@ -161,6 +169,22 @@ struct ntt_plan {
         c.work = d_work;
         c.work_limbs = work_limbs;
         c.stream = s;
+        return c;
+    }
+
+    // The same, for an array whose limb l uses prime prime0 + (l % Lview): the
+    // tables are viewed from prime prime0 on.
+    ntt::LaunchCtx ctx_range(uint64_t* data, uint32_t limbs, uint32_t Lview, uint32_t prime0, cudaStream_t s) const
+    {
+        ntt::LaunchCtx c = ctx(data, limbs, Lview, s);
+        const size_t R = passes == 2 ? (size_t)1 << (n - p1) : 0;           // OT A entries per prime
+        const size_t B = passes == 2 ? (size_t)(n - p1) << p1 : 0;          // OT B entries per prime
+        c.primes = d_primes + prime0;
+        c.tw = d_tw + (size_t)prime0 * tw_len;
+        c.ota_f = d_ota_f ? d_ota_f + prime0 * R : nullptr;
+        c.ota_i = d_ota_i ? d_ota_i + prime0 * R : nullptr;
+        c.otb_f = d_otb_f ? d_otb_f + prime0 * B : nullptr;
+        c.otb_i = d_otb_i ? d_otb_i + prime0 * B : nullptr;
         return c;
     }
 };

@@ -285,3 +285,30 @@ def test_auto_twiddle_mode(n, want_mode, want_ots):
     with G.Plan(N, I.prime_chain(1, 2 * N)) as p:
         info = p.info()
         assert (info.twiddle_mode, info.ot_stages) == (want_mode, want_ots)
+
+
+@pytest.mark.parametrize("n,L,batch,kernel,mode,ots", [
+    (16, 45, 1, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_AUTO, 0),         # limb ranges of one polynomial
+    (17, 4, 3, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_OT, 2),            # ranges of several polynomials, OT2 views
+    (14, 7, 2, G.NTT_KERNEL_PER_PASS, G.NTT_TWIDDLE_TABLE, 0),     # launch-per-pass kernels
+    (12, 3, 7, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_AUTO, 0),          # groups of whole polynomials, one pass
+    (13, 5, 13, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_OT, 1),           # groups, fused
+    (13, 6, 4, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_AUTO, 0),          # one segment per polynomial
+    (15, 2, 5, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_AUTO, 0),
+])
+def test_execute_host_segments(orc, n, L, batch, kernel, mode, ots):
+    """The host-buffer call splits the data into segments on several streams;
+    every shape of split matches the oracle, in place and out of place."""
+    N = 1 << n
+    primes = I.prime_chain(L, 2 * N)
+    data = I.batch_uniform(130 + n, batch, primes, N)
+    with G.Plan(N, primes, mode, ots, kernel) as p:
+        out = np.empty_like(data)
+        G.ntt_execute_host(p.handle, data, out, batch, G.NTT_OP_FORWARD)
+        assert np.array_equal(out, oracle_fwd(orc, data, primes))
+        G.ntt_execute_host(p.handle, out, out, batch, G.NTT_OP_INVERSE)     # in place
+        assert np.array_equal(out, data)
+        both = np.empty_like(data)
+        G.ntt_execute_host(p.handle, data, both, batch, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE)
+        assert np.array_equal(both, data)
+        assert p.device_status() == 0
