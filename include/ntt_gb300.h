@@ -251,6 +251,74 @@ ntt_status ntt_batch_submit(ntt_batch* batch, const ntt_job* jobs, uint32_t njob
  * ntt_plan_device_status).  Synchronises the device, reads and clears it. */
 ntt_status ntt_batch_device_status(ntt_batch* batch, uint32_t* status);
 
+/*
+ * Serving: a request loop with admission by device memory and continuous
+ * batching (a runtime around the transforms; the paper has no counterpart).
+ *
+ * A server owns a scheduler thread, `slots` streams with a batch object each,
+ * and optionally a device arena for host-buffer requests.  Submitted
+ * requests wait in a FIFO queue; the scheduler admits them from its head
+ * while the bytes of all admitted requests stay within hbm_budget_bytes (and,
+ * for NTT_REQ_HOST requests, the arena has room), and starts a batch (up to
+ * max_batch_jobs requests) in the first free slot: copy-in of host requests,
+ * one ntt_batch_submit, copy-out.  Requests arriving while batches are on the
+ * device join the next free slot as memory frees up, so batches overlap.
+ *
+ * Request memory stays owned by the caller and must stay valid until the
+ * request is done.  Device requests are transformed in place; host requests
+ * are read from `data` and written to `host_out` (may be the same array;
+ * page-locked for full copy bandwidth).  The server's plans and device must
+ * stay current as for single calls; submit and wait may be called from any
+ * host thread.
+ */
+#define NTT_REQ_HOST 1u           /* data / host_out are host memory */
+
+typedef struct ntt_server ntt_server;
+
+typedef struct ntt_server_opts {
+    uint64_t hbm_budget_bytes;    /* bytes of admitted requests at any time (> 0) */
+    uint64_t arena_bytes;         /* device staging for NTT_REQ_HOST requests (0: none) */
+    uint32_t max_batch_jobs;      /* requests per batch (0: 32) */
+    uint32_t slots;               /* batches in flight (0: 3; at most 16) */
+    uint32_t max_queue;           /* waiting requests before NTT_ERR_BUSY (0: 2^20) */
+    uint32_t reserved[3];         /* must be zero */
+} ntt_server_opts;
+
+typedef struct ntt_request {
+    const ntt_plan* plan;
+    uint64_t* data;               /* [batch][levels][N]: device array, or host input with NTT_REQ_HOST */
+    uint64_t* host_out;           /* NTT_REQ_HOST: host output; otherwise ignored */
+    uint32_t batch;
+    uint32_t levels;              /* 1 <= levels <= plan L */
+    uint32_t op;                  /* NTT_OP_FORWARD or NTT_OP_INVERSE */
+    uint32_t flags;               /* 0 or NTT_REQ_HOST */
+} ntt_request;
+
+typedef struct ntt_request_times {
+    int64_t submit_ns;            /* steady-clock times of submission, */
+    int64_t start_ns;             /* of admission into a batch, */
+    int64_t done_ns;              /* and of completion (0 while not done) */
+} ntt_request_times;
+
+/* Create a server on the current device.  Errors: NTT_ERR_INVALID_ARG,
+ * NTT_ERR_OOM, NTT_ERR_CUDA. */
+ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts);
+
+/* Drain: wait for every submitted request to finish, then free the server. */
+void ntt_server_destroy(ntt_server* server);
+
+/* Queue a request; *ticket identifies it.  Errors: NTT_ERR_INVALID_ARG (bad
+ * field, or a request larger than the budget or the arena), NTT_ERR_MISALIGNED,
+ * NTT_ERR_BUSY (max_queue requests already waiting: admission refused). */
+ntt_status ntt_server_submit(ntt_server* server, const ntt_request* request, uint64_t* ticket);
+
+/* Wait up to timeout_ns for a request: its status (NTT_OK, or the error of
+ * its batch), or NTT_ERR_TIMEOUT if it is not done yet. */
+ntt_status ntt_server_wait(ntt_server* server, uint64_t ticket, uint64_t timeout_ns);
+
+/* Timestamps of a request (for latency statistics). */
+ntt_status ntt_server_request_times(ntt_server* server, uint64_t ticket, ntt_request_times* times);
+
 /* Plan facts, for callers and tests. */
 typedef struct ntt_plan_info {
     uint32_t N, L;

@@ -43,6 +43,8 @@ NTT_KERNEL_PER_PASS = 2
 NTT_OP_FORWARD = 1
 NTT_OP_INVERSE = 2
 
+NTT_REQ_HOST = 1
+
 _u32, _u64, _vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 
@@ -60,6 +62,20 @@ class PlanInfo(ctypes.Structure):
 class Job(ctypes.Structure):
     _fields_ = [("plan", _vp), ("data", _vp), ("batch", _u32), ("levels", _u32), ("op", _u32),
                 ("reserved", _u32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", _u64), ("arena_bytes", _u64), ("max_batch_jobs", _u32),
+                ("slots", _u32), ("max_queue", _u32), ("reserved", _u32 * 3)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("plan", _vp), ("data", _vp), ("host_out", _vp), ("batch", _u32), ("levels", _u32),
+                ("op", _u32), ("flags", _u32)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
 
 
 class NttError(RuntimeError):
@@ -115,6 +131,16 @@ def _lib():
             L.ntt_batch_submit.argtypes = [_vp, ctypes.POINTER(Job), _u32, _vp]
             L.ntt_batch_device_status.restype = S
             L.ntt_batch_device_status.argtypes = [_vp, ctypes.POINTER(_u32)]
+            L.ntt_server_create.restype = S
+            L.ntt_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(ServerOpts)]
+            L.ntt_server_destroy.restype = None
+            L.ntt_server_destroy.argtypes = [_vp]
+            L.ntt_server_submit.restype = S
+            L.ntt_server_submit.argtypes = [_vp, ctypes.POINTER(Request), ctypes.POINTER(_u64)]
+            L.ntt_server_wait.restype = S
+            L.ntt_server_wait.argtypes = [_vp, _u64, _u64]
+            L.ntt_server_request_times.restype = S
+            L.ntt_server_request_times.argtypes = [_vp, _u64, ctypes.POINTER(RequestTimes)]
             L.ntt_plan_query.restype = S
             L.ntt_plan_query.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
             L.ntt_plan_device_status.restype = S
@@ -369,6 +395,68 @@ class Batch:
     def close(self):
         if self.handle:
             ntt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_addr(x) -> int:
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x)
+
+
+class Server:
+    """Owner of an ntt_server handle: submit requests, wait for them."""
+
+    def __init__(self, hbm_budget_bytes: int, arena_bytes: int = 0, max_batch_jobs: int = 0, slots: int = 0,
+                 max_queue: int = 0):
+        o = ServerOpts(hbm_budget_bytes, arena_bytes, max_batch_jobs, slots, max_queue, (_u32 * 3)())
+        h = _vp()
+        _check(_lib().ntt_server_create(ctypes.byref(h), ctypes.byref(o)), "ntt_server_create")
+        self.handle = h.value
+
+    def submit_status(self, plan: int, data, batch: int, levels: int, op: int, host_out=None):
+        """(status, ticket) without raising; host_out given => a host-buffer request."""
+        host = host_out is not None
+        r = Request(plan, _host_addr(data) if host else _addr(data), _host_addr(host_out) if host else None,
+                    batch, levels, op, NTT_REQ_HOST if host else 0)
+        t = _u64()
+        st = _lib().ntt_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t))
+        return st, t.value
+
+    def submit(self, plan: int, data, batch: int, levels: int, op: int, host_out=None) -> int:
+        st, t = self.submit_status(plan, data, batch, levels, op, host_out)
+        _check(st, "ntt_server_submit")
+        return t
+
+    def wait_status(self, ticket: int, timeout_s: float = 60.0) -> int:
+        return _lib().ntt_server_wait(self.handle, ticket, int(timeout_s * 1e9))
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
+        _check(self.wait_status(ticket, timeout_s), "ntt_server_wait")
+
+    def times(self, ticket: int):
+        """(submit_ns, start_ns, done_ns) on the steady clock."""
+        t = RequestTimes()
+        _check(_lib().ntt_server_request_times(self.handle, ticket, ctypes.byref(t)), "ntt_server_request_times")
+        return t.submit_ns, t.start_ns, t.done_ns
+
+    def close(self):
+        if self.handle:
+            _lib().ntt_server_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -1,0 +1,358 @@
+// Serving: a request loop with admission by device memory and continuous
+// batching (a library runtime around the transforms; the paper measures
+// batches, not request streams).
+//
+// A scheduler thread owns the device side.  Requests wait in a FIFO queue;
+// the scheduler admits them from its head while their bytes fit the budget
+// (and, for host-buffer requests, the device arena), and starts a batch in
+// the first free slot.  A slot is a stream with its own batch object:
+// copy-in of the host-buffer requests, one ntt_batch_submit over all the
+// batch's requests, copy-out, then a host callback that timestamps the
+// requests and wakes the scheduler and the waiters.  Requests that arrive
+// while batches are on the device are admitted into the next free slot as
+// memory frees up, so several batches overlap on the device.
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
+
+namespace {
+
+int64_t now_ns()
+{
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Req {
+    uint64_t ticket = 0;
+    ntt_request r{};
+    size_t bytes = 0;
+    size_t arena_off = 0;         // host-buffer requests: device staging offset
+    bool host = false;
+    int64_t t_submit = 0, t_start = 0, t_done = 0;
+    ntt_status status = NTT_OK;
+    bool done = false;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    ntt_batch* batch = nullptr;
+    std::vector<Req*> reqs;       // of the batch in flight (empty when free)
+    bool busy = false;
+    bool finished = false;        // set by the completion callback
+    struct ntt_server* owner = nullptr;
+};
+
+// First-fit allocator over [0, size) with coalescing free ranges.
+class Arena {
+public:
+    void reset(size_t size)
+    {
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(size_t bytes, size_t* off)
+    {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = (bytes + 255) & ~(size_t)255;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+private:
+    std::map<size_t, size_t> free_;
+};
+
+}  // namespace
+
+struct ntt_server {
+    ntt_server_opts opts{};
+    int device = 0;
+    uint8_t* arena_mem = nullptr;
+    Arena arena;
+    size_t admitted_bytes = 0;
+    std::vector<Slot> slots;
+    std::deque<Req*> pending;
+    std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+    uint64_t next_ticket = 1;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    cudaError_t fatal = cudaSuccess;
+};
+
+namespace {
+
+void CUDART_CB on_batch_done(void* arg)
+{
+    Slot* s = static_cast<Slot*>(arg);
+    ntt_server* srv = s->owner;
+    const int64_t t = now_ns();
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        for (Req* r : s->reqs) r->t_done = t;
+        s->finished = true;
+    }
+    srv->cv_work.notify_one();
+}
+
+// Start one batch in slot `s` from the head of the queue (called with the
+// lock held; returns false when nothing could be admitted).
+bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
+{
+    std::vector<Req*> take;
+    while (!srv->pending.empty() && take.size() < srv->opts.max_batch_jobs) {
+        Req* r = srv->pending.front();
+        if (srv->admitted_bytes + r->bytes > srv->opts.hbm_budget_bytes) break;
+        if (r->host && !srv->arena.alloc(r->bytes, &r->arena_off)) break;
+        srv->admitted_bytes += r->bytes;
+        srv->pending.pop_front();
+        take.push_back(r);
+    }
+    if (take.empty()) return false;
+    s.busy = true;
+    s.finished = false;
+    s.reqs = take;
+    const int64_t t = now_ns();
+    for (Req* r : take) r->t_start = t;
+    lk.unlock();
+
+    cudaError_t e = cudaSuccess;
+    std::vector<ntt_job> jobs;
+    jobs.reserve(take.size());
+    for (Req* r : take) {
+        uint64_t* dev = r->r.data;
+        if (r->host) {
+            dev = reinterpret_cast<uint64_t*>(srv->arena_mem + r->arena_off);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dev, r->r.data, r->bytes, cudaMemcpyHostToDevice, s.stream);
+        }
+        jobs.push_back(ntt_job{r->r.plan, dev, r->r.batch, r->r.levels, r->r.op, 0});
+    }
+    ntt_status st = e == cudaSuccess ? ntt_batch_submit(s.batch, jobs.data(), (uint32_t)jobs.size(), s.stream)
+                                     : NTT_ERR_CUDA;
+    for (Req* r : take) {
+        if (st == NTT_OK && r->host) {
+            const uint64_t* dev = reinterpret_cast<const uint64_t*>(srv->arena_mem + r->arena_off);
+            e = cudaMemcpyAsync(r->r.host_out, dev, r->bytes, cudaMemcpyDeviceToHost, s.stream);
+            if (e != cudaSuccess) st = NTT_ERR_CUDA;
+        }
+    }
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(s.stream, on_batch_done, &s);
+    lk.lock();
+    if (e != cudaSuccess || st != NTT_OK) {
+        // nothing will call back: finish the batch here once the stream drains
+        lk.unlock();
+        cudaStreamSynchronize(s.stream);
+        cudaGetLastError();
+        lk.lock();
+        const int64_t t2 = now_ns();
+        for (Req* r : take) {
+            r->status = st != NTT_OK ? st : NTT_ERR_CUDA;
+            r->t_done = t2;
+        }
+        s.finished = true;
+        if (e != cudaSuccess) srv->fatal = e;
+    }
+    return true;
+}
+
+// Retire finished batches (lock held): free their memory, publish results.
+bool retire(ntt_server* srv)
+{
+    bool any = false;
+    for (Slot& s : srv->slots) {
+        if (!s.busy || !s.finished) continue;
+        for (Req* r : s.reqs) {
+            srv->admitted_bytes -= r->bytes;
+            if (r->host) srv->arena.release(r->arena_off, r->bytes);
+            r->done = true;
+        }
+        s.reqs.clear();
+        s.busy = false;
+        s.finished = false;
+        any = true;
+    }
+    if (any) srv->cv_done.notify_all();
+    return any;
+}
+
+void scheduler(ntt_server* srv)
+{
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    for (;;) {
+        retire(srv);
+        bool started = false;
+        for (Slot& s : srv->slots)
+            if (!s.busy && !srv->pending.empty()) started |= start_batch(srv, s, lk);
+        bool inflight = false;
+        for (const Slot& s : srv->slots) inflight |= s.busy;
+        if (srv->stop && srv->pending.empty() && !inflight) break;
+        if (started) continue;
+        // wait for a completion callback or a new request
+        srv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
+{
+    if (!out || !opts || opts->hbm_budget_bytes == 0) return NTT_ERR_INVALID_ARG;
+    for (uint32_t r : opts->reserved)
+        if (r) return NTT_ERR_INVALID_ARG;
+    std::unique_ptr<ntt_server> srv(new (std::nothrow) ntt_server());
+    if (!srv) return NTT_ERR_OOM;
+    srv->opts = *opts;
+    if (!srv->opts.max_batch_jobs) srv->opts.max_batch_jobs = 32;
+    if (!srv->opts.slots) srv->opts.slots = 3;
+    if (!srv->opts.max_queue) srv->opts.max_queue = 1u << 20;
+    if (srv->opts.slots > 16) return NTT_ERR_INVALID_ARG;
+    cudaError_t e = cudaGetDevice(&srv->device);
+    const size_t arena = (size_t)srv->opts.arena_bytes;
+    if (e == cudaSuccess && arena) e = cudaMalloc(&srv->arena_mem, arena);
+    srv->arena.reset(e == cudaSuccess ? arena : 0);
+    srv->slots.resize(srv->opts.slots);
+    for (Slot& s : srv->slots) {
+        s.owner = srv.get();
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess && ntt_batch_create(&s.batch) != NTT_OK) e = cudaErrorMemoryAllocation;
+    }
+    if (e != cudaSuccess) {
+        for (Slot& s : srv->slots) {
+            if (s.batch) ntt_batch_destroy(s.batch);
+            if (s.stream) cudaStreamDestroy(s.stream);
+        }
+        cudaFree(srv->arena_mem);
+        ntt_internal_set_cuda_error(e);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? NTT_ERR_OOM : NTT_ERR_CUDA;
+    }
+    ntt_server* raw = srv.release();
+    raw->worker = std::thread(scheduler, raw);
+    *out = raw;
+    return NTT_OK;
+}
+
+void ntt_server_destroy(ntt_server* srv)
+{
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_one();
+    if (srv->worker.joinable()) srv->worker.join();
+    for (Slot& s : srv->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.batch) ntt_batch_destroy(s.batch);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    cudaFree(srv->arena_mem);
+    delete srv;
+}
+
+ntt_status ntt_server_submit(ntt_server* srv, const ntt_request* req, uint64_t* ticket)
+{
+    if (!srv || !req || !ticket) return NTT_ERR_INVALID_ARG;
+    const ntt_request& q = *req;
+    if (!q.plan || !q.data || q.batch == 0 || q.levels == 0 || q.levels > q.plan->L) return NTT_ERR_INVALID_ARG;
+    if (q.op != NTT_OP_FORWARD && q.op != NTT_OP_INVERSE) return NTT_ERR_INVALID_ARG;
+    if (q.flags & ~(uint32_t)NTT_REQ_HOST) return NTT_ERR_INVALID_ARG;
+    const bool host = (q.flags & NTT_REQ_HOST) != 0;
+    if (host && !q.host_out) return NTT_ERR_INVALID_ARG;
+    if (!host && ((uintptr_t)q.data & 15u)) return NTT_ERR_MISALIGNED;
+    if (q.plan->device != srv->device) return NTT_ERR_INVALID_ARG;
+    const uint64_t limbs = (uint64_t)q.batch * q.levels;
+    if (limbs > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)limbs * q.plan->N * sizeof(uint64_t);
+    if (bytes > srv->opts.hbm_budget_bytes) return NTT_ERR_INVALID_ARG;          // could never be admitted
+    if (host && bytes > srv->opts.arena_bytes) return NTT_ERR_INVALID_ARG;
+    std::unique_ptr<Req> r(new (std::nothrow) Req());
+    if (!r) return NTT_ERR_OOM;
+    r->r = q;
+    r->bytes = bytes;
+    r->host = host;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        if (srv->stop) return NTT_ERR_INVALID_ARG;
+        if (srv->pending.size() >= srv->opts.max_queue) return NTT_ERR_BUSY;
+        r->ticket = srv->next_ticket++;
+        r->t_submit = now_ns();
+        *ticket = r->ticket;
+        srv->pending.push_back(r.get());
+        srv->reqs.emplace(r->ticket, std::move(r));
+    }
+    srv->cv_work.notify_one();
+    return NTT_OK;
+}
+
+ntt_status ntt_server_wait(ntt_server* srv, uint64_t ticket, uint64_t timeout_ns)
+{
+    if (!srv) return NTT_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return NTT_ERR_INVALID_ARG;
+    Req* r = it->second.get();
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns);
+    while (!r->done) {
+        if (srv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !r->done) return NTT_ERR_TIMEOUT;
+    }
+    return r->status;
+}
+
+ntt_status ntt_server_request_times(ntt_server* srv, uint64_t ticket, ntt_request_times* times)
+{
+    if (!srv || !times) return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return NTT_ERR_INVALID_ARG;
+    const Req* r = it->second.get();
+    times->submit_ns = r->t_submit;
+    times->start_ns = r->t_start;
+    times->done_ns = r->done ? r->t_done : 0;
+    return NTT_OK;
+}
+
+}  // extern "C"
