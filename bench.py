@@ -51,6 +51,8 @@ def parse():
                     help="independent steps spread over this many streams (one plan each)")
     ap.add_argument("--no-batch-compare", action="store_true",
                     help="skip the per-limb C2 path and the uneven 96-job batch")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--launch-steps", type=int, default=500,
                     help="steps of the single-stream pass that times each launch")
     return ap.parse_args()
@@ -316,6 +318,72 @@ def batched_c4(G, torch, reps):
             p.close()
 
 
+def serve_c5(G, torch, count, budget_gb=64, ring_gb=80):
+    """The serving workload: `count` requests (N in 2^15..2^17, L in [4, 60],
+    mixed directions) on device-resident data, admitted by an HBM budget.
+    A capacity run (every request submitted at once), then Poisson arrivals at
+    50 / 80 / 95% of that capacity; latency = submission to completion."""
+    import collections
+    chain = I.chain_2_18_60()
+    plans = {n: G.Plan(1 << n, chain) for n in (15, 16, 17)}
+    word = 8
+    ring_words = (ring_gb << 30) // word
+    ring = torch.empty(ring_words, dtype=torch.int64, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    ring.random_(0, 1 << 59, generator=gen)         # residues below every prime of the chain
+    base = I.serving_requests(count, 1.0, seed=5)   # sizes and directions; gaps rescaled per rate
+    sizes = [r.L * r.N for r in base]
+    limbs_total = sum(r.L for r in base)
+    try:
+        def run(rate):
+            with G.Server(budget_gb << 30, max_batch_jobs=32, slots=3) as srv:
+                inflight = collections.deque()          # (ticket, start, end) in ring order
+                tickets = []
+                off = 0
+                gaps = [r.t_arrival for r in base]
+                t0 = time.perf_counter()
+                for i, r in enumerate(base):
+                    n = r.N.bit_length() - 1
+                    if off + sizes[i] > ring_words:
+                        off = 0
+                    lo, hi = off, off + sizes[i]
+                    # recycle: wait for older requests whose bytes this one overwrites
+                    while inflight and inflight[0][1] < hi and inflight[0][2] > lo:
+                        srv.wait(inflight.popleft()[0])
+                    if rate is not None:
+                        due = t0 + gaps[i] / rate
+                        while time.perf_counter() < due:
+                            pass
+                    t = srv.submit(plans[n].handle, ring[lo:hi], 1, r.L,
+                                   G.NTT_OP_FORWARD if r.dir > 0 else G.NTT_OP_INVERSE)
+                    inflight.append((t, lo, hi))
+                    tickets.append(t)
+                    off = hi + ((-hi) % 2)              # 16-byte aligned starts
+                for t in tickets:
+                    srv.wait(t)
+                times = [srv.times(t) for t in tickets]
+            sub = np.array([x[0] for x in times], dtype=np.float64)
+            done = np.array([x[2] for x in times], dtype=np.float64)
+            lat = (done - sub) / 1e3
+            span = (done.max() - sub.min()) / 1e9
+            return {"limb_ntt_per_s": limbs_total / span, "requests_per_s": count / span,
+                    "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                   "mean": float(lat.mean())}}
+
+        cap = run(None)
+        out = {"requests": count, "budget_gb": budget_gb, "data": "device-resident, in place",
+               "capacity": cap}
+        for frac in (0.5, 0.8, 0.95):
+            out[f"poisson_{int(frac * 100)}pct"] = dict(run(frac * cap["requests_per_s"]),
+                                                       offered_requests_per_s=frac * cap["requests_per_s"])
+        return out
+    finally:
+        for p in plans.values():
+            p.close()
+        del ring
+
+
 def config_dict(w, args, ws):
     return {"workload": "c2_n65536_l45_fwd_inv", "N": w.N, "L": len(w.primes), "polys_per_step": 1,
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
@@ -472,6 +540,9 @@ def main():
     if ws == 1 and not args.no_batch_compare:
         per_limb = per_limb_c2(G, torch, w, host, 100)
         batched = batched_c4(G, torch, 10)
+    served = None
+    if ws == 1 and not args.no_serve:
+        served = serve_c5(G, torch, args.serve_requests)
 
     if rank != 0:
         if dist is not None:
@@ -502,6 +573,7 @@ def main():
         "e2e": e2e,
         "per_limb_path": per_limb,
         "batched_uneven_c4": batched,
+        "served_c5": served,
         "gpu_launches": K * 2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes)),
         "clocks": clocks,
         "cpu_baseline": cpu,
