@@ -72,13 +72,17 @@ enum {
     NTT_TWIDDLE_OT = 2
 };
 
-/* Kernel organisation for two-pass sizes (N >= 2^13): one persistent launch
+/* Kernel organisation: for two-pass sizes (N >= 2^13) one persistent launch
  * that runs both passes with per-limb dependency counters (FUSED, the
- * default), or one launch per pass (PER_PASS).  Results are identical. */
+ * default), or one launch per pass (PER_PASS); for every size, RADIX2 is the
+ * paper's starting point (Sec. VI): one launch per radix-2 stage with its
+ * operands in global memory, table twiddles only, kept for comparison.
+ * Results are identical. */
 enum {
     NTT_KERNEL_AUTO = 0,
     NTT_KERNEL_FUSED = 1,
-    NTT_KERNEL_PER_PASS = 2
+    NTT_KERNEL_PER_PASS = 2,
+    NTT_KERNEL_RADIX2 = 3
 };
 
 typedef struct ntt_plan_opts {
@@ -141,6 +145,19 @@ ntt_status ntt_inverse_levels(const ntt_plan* plan, uint64_t* data, uint32_t bat
  */
 ntt_status ntt_mul_pointwise(const ntt_plan* plan, const uint64_t* a, const uint64_t* b,
                              uint64_t* c, uint32_t batch, void* stream);
+
+/*
+ * Negacyclic product in coefficient form (Sec. III-A: NTT, element-wise
+ * product, iNTT):  c = a * b mod (X^N + 1), limb by limb mod q_l, for
+ * `batch` pairs of polynomials [batch][L][N].  Both forward transforms run in
+ * one launch (fused plans), then the element-wise product into c, then the
+ * inverse of c.  a and b are left holding their forward transforms (natural
+ * input order in, bit-reversed transform out, as ntt_forward); c may alias
+ * a or b; a and b must not overlap.  Errors as ntt_forward, and
+ * NTT_ERR_INVALID_ARG for overlapping a and b.
+ */
+ntt_status ntt_mul_negacyclic(const ntt_plan* plan, uint64_t* a, uint64_t* b, uint64_t* c, uint32_t batch,
+                              void* stream);
 
 /* Operation flags for ntt_execute_host. */
 enum {
@@ -328,7 +345,7 @@ typedef struct ntt_plan_info {
     uint32_t twiddle_mode;    /* NTT_TWIDDLE_TABLE or NTT_TWIDDLE_OT */
     uint32_t ot_stages;       /* OT: final stages built on the fly */
     uint32_t device;          /* CUDA device ordinal */
-    uint32_t kernel;          /* NTT_KERNEL_FUSED or NTT_KERNEL_PER_PASS */
+    uint32_t kernel;          /* NTT_KERNEL_FUSED, NTT_KERNEL_PER_PASS or NTT_KERNEL_RADIX2 */
     uint64_t device_bytes;    /* device memory held by the plan (tables) */
 } ntt_plan_info;
 

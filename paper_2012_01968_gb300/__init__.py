@@ -39,6 +39,7 @@ NTT_TWIDDLE_OT = 2
 NTT_KERNEL_AUTO = 0
 NTT_KERNEL_FUSED = 1
 NTT_KERNEL_PER_PASS = 2
+NTT_KERNEL_RADIX2 = 3
 
 NTT_OP_FORWARD = 1
 NTT_OP_INVERSE = 2
@@ -117,6 +118,8 @@ def _lib():
             for f in ("ntt_forward_levels", "ntt_inverse_levels"):
                 getattr(L, f).restype = S
                 getattr(L, f).argtypes = [_vp, _vp, _u32, _u32, _vp]
+            L.ntt_mul_negacyclic.restype = S
+            L.ntt_mul_negacyclic.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
             L.ntt_mul_pointwise.restype = S
             L.ntt_mul_pointwise.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
             L.ntt_execute_host.restype = S
@@ -250,6 +253,12 @@ def ntt_inverse_levels(plan: int, data, batch: int, levels: int, stream=None) ->
 def ntt_mul_pointwise(plan: int, a, b, c, batch: int, stream=None) -> None:
     _check(_lib().ntt_mul_pointwise(plan, _addr(a), _addr(b), _addr(c), batch, _stream(stream, a)),
            "ntt_mul_pointwise")
+
+
+def ntt_mul_negacyclic(plan: int, a, b, c, batch: int, stream=None) -> None:
+    """c = a * b mod (X^N + 1) per limb; a and b are left holding their transforms."""
+    _check(_lib().ntt_mul_negacyclic(plan, _addr(a), _addr(b), _addr(c), batch, _stream(stream, a)),
+           "ntt_mul_negacyclic")
 
 
 def ntt_execute_host(plan: int, host_in, host_out, batch: int, ops: int, stream=None) -> None:

@@ -24,6 +24,7 @@ namespace ntt {
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd)
 {
     if (c.limbs == 0) return cudaSuccess;
+    if (c.radix2) return launch_radix2(c, fwd);
     if (c.n <= (u32)SINGLE_PASS_MAX) return launch_single(c, fwd);
     switch (c.n) {
     case 13: return launch_n13(c, fwd);
@@ -147,6 +148,45 @@ ntt_status ntt_mul_pointwise(const ntt_plan* p, const uint64_t* a, const uint64_
                                            reinterpret_cast<const ntt::u64*>(b), reinterpret_cast<ntt::u64*>(c),
                                            (uint32_t)limbs,
                                            (cudaStream_t)stream));
+}
+
+ntt_status ntt_mul_negacyclic(const ntt_plan* p, uint64_t* a, uint64_t* b, uint64_t* c, uint32_t batch,
+                              void* stream)
+{
+    if (!p || !a || !b || !c || batch == 0 || a == b) return NTT_ERR_INVALID_ARG;
+    if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return NTT_ERR_MISALIGNED;
+    const uint64_t limbs = (uint64_t)batch * p->L;
+    if (2 * limbs > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)limbs * p->N * sizeof(uint64_t);
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    if (pa < pb + bytes && pb < pa + bytes) return NTT_ERR_INVALID_ARG;    // a and b overlap
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED) {
+        // both forward transforms in one launch of the fused kernel (two jobs)
+        if (p->work_limbs < 2 * limbs) {
+            e = ntt_internal_grow_work(const_cast<ntt_plan*>(p), (uint32_t)(2 * limbs));
+            if (e != cudaSuccess) return to_status(e);
+        }
+        const ntt::JobCtx ja{reinterpret_cast<ntt::u64*>(a), (uint32_t)limbs, p->L, p->d_primes, p->d_tw, p->tw_len,
+                             p->d_ota_f, p->d_otb_f, p->d_ota_i, p->d_otb_i};
+        ntt::JobCtx jb = ja;
+        jb.data = reinterpret_cast<ntt::u64*>(b);
+        const ntt::JobCtx jobs[2] = {ja, jb};
+        const uint32_t ots = p->twiddle_mode == NTT_TWIDDLE_OT ? p->ot_stages : 0;
+        const ntt::JobsCtx jc{jobs, 2u, p->n, ots, p->d_status, p->d_work, p->work_limbs, s};
+        e = ntt::launch_fused_jobs(jc, true);
+    } else {
+        const ntt::LaunchCtx ca = p->ctx(a, (uint32_t)limbs, p->L, s);
+        e = ntt::launch_transform(ca, true);
+        if (e == cudaSuccess) e = ntt::launch_transform(p->ctx(b, (uint32_t)limbs, p->L, s), true);
+    }
+    if (e == cudaSuccess)
+        e = ntt::launch_pointwise(p->d_primes, p->L, p->n, reinterpret_cast<const ntt::u64*>(a),
+                                  reinterpret_cast<const ntt::u64*>(b), reinterpret_cast<ntt::u64*>(c),
+                                  (uint32_t)limbs, s);
+    if (e == cudaSuccess) e = ntt::launch_transform(p->ctx(c, (uint32_t)limbs, p->L, s), false);
+    return to_status(e);
 }
 
 ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_t* host_out, uint32_t batch,

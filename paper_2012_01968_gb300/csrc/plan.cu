@@ -69,12 +69,15 @@ void build_prime(const ntt_plan& p, uint32_t l, HostTables& h)
     auto inv = [&](uint64_t e) { return e == 0 ? 1 : q - pw[N - e]; };    // psi^{-e}, e < N
 
     // Psi[2^s + j] goes to slot 2^s + tw_slot(j) of the pass holding stage s
+    // (natural order, slot 2^s + j, for the radix-2 organisation)
     Tw* tw = h.tw.data() + (size_t)l * p.tw_len;
     tw[0] = make_tw(1, q);
     for (uint32_t s = 0; (1u << s) < p.tw_len; ++s) {
         const ntt::StageSlot g = ntt::stage_slot_params(n, p.p1, s);
-        for (uint32_t j = 0; j < (1u << s); ++j)
-            tw[(1u << s) + ntt::tw_slot(j, g.sl, g.K0, g.k)] = make_tw(fwd(nt::brv((1u << s) + j, n)), q);
+        for (uint32_t j = 0; j < (1u << s); ++j) {
+            const uint32_t slot = p.kernel == NTT_KERNEL_RADIX2 ? j : ntt::tw_slot(j, g.sl, g.K0, g.k);
+            tw[(1u << s) + slot] = make_tw(fwd(nt::brv((1u << s) + j, n)), q);
+        }
     }
 
     PrimeDev& d = h.pd[l];
@@ -163,14 +166,16 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     for (uint32_t r : o.reserved)
         if (r) return NTT_ERR_INVALID_ARG;
     if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
-    if (o.kernel > NTT_KERNEL_PER_PASS) return NTT_ERR_INVALID_ARG;
+    if (o.kernel > NTT_KERNEL_RADIX2) return NTT_ERR_INVALID_ARG;
     const uint32_t n = (uint32_t)__builtin_ctz(N);
     const uint32_t p1 = (uint32_t)ntt::split_p1((int)n);
     const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
     // AUTO: OT on the last stage for two-pass sizes (measured faster than the
     // table there, and half the last stage's twiddle traffic), table below
+    const bool radix2 = o.kernel == NTT_KERNEL_RADIX2;
+    if (radix2 && o.twiddle_mode == NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;   // table twiddles only
     uint32_t mode = o.twiddle_mode;
-    if (mode == NTT_TWIDDLE_AUTO) mode = two_pass ? NTT_TWIDDLE_OT : NTT_TWIDDLE_TABLE;
+    if (mode == NTT_TWIDDLE_AUTO) mode = two_pass && !radix2 ? NTT_TWIDDLE_OT : NTT_TWIDDLE_TABLE;
     uint32_t ots = 0;
     if (mode == NTT_TWIDDLE_OT) {
         ots = o.ot_stages ? o.ot_stages : 1;
@@ -195,7 +200,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     p->passes = two_pass ? 2 : 1;
     p->twiddle_mode = mode;
     p->ot_stages = ots;
-    p->kernel = (o.kernel == NTT_KERNEL_PER_PASS) ? NTT_KERNEL_PER_PASS : NTT_KERNEL_FUSED;
+    p->kernel = radix2 ? NTT_KERNEL_RADIX2 : o.kernel == NTT_KERNEL_PER_PASS ? NTT_KERNEL_PER_PASS : NTT_KERNEL_FUSED;
     cudaError_t ce = cudaGetDevice(&p->device);
     if (ce != cudaSuccess) {
         ntt_internal_set_cuda_error(ce);

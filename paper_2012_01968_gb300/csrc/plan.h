@@ -61,6 +61,7 @@ struct LaunchCtx {
     u32 p1;
     u32 ots;                 // OT stages (0 = table mode)
     u32 separate_passes;     // 1: one launch per pass instead of the fused kernel
+    u32 radix2;              // 1: one launch per radix-2 stage (natural-order table)
     u32* status;             // persistent device status word of the plan
     u32* work;               // fused kernel's work area (zero between launches)
     u32 work_limbs;          // limbs the work area covers (fused_work_words(work_limbs) words)
@@ -103,6 +104,7 @@ cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a,
 
 // per-n launchers (one translation unit each, compiled in parallel)
 cudaError_t launch_single(const LaunchCtx& c, bool fwd);
+cudaError_t launch_radix2(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n13(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n14(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n15(const LaunchCtx& c, bool fwd);
@@ -165,6 +167,7 @@ struct ntt_plan {
         c.p1 = p1;
         c.ots = twiddle_mode == NTT_TWIDDLE_OT ? ot_stages : 0;
         c.separate_passes = kernel == NTT_KERNEL_PER_PASS ? 1u : 0u;
+        c.radix2 = kernel == NTT_KERNEL_RADIX2 ? 1u : 0u;
         c.status = d_status;
         c.work = d_work;
         c.work_limbs = work_limbs;

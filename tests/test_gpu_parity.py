@@ -23,9 +23,9 @@ def _built():
     G.lib()
 
 
-def _roundtrip_case(orc, N, primes, batch, seed, mode=G.NTT_TWIDDLE_TABLE, ots=0):
+def _roundtrip_case(orc, N, primes, batch, seed, mode=G.NTT_TWIDDLE_TABLE, ots=0, kernel=G.NTT_KERNEL_AUTO):
     data = I.batch_uniform(seed, batch, primes, N)
-    with G.Plan(N, primes, mode, ots) as p:
+    with G.Plan(N, primes, mode, ots, kernel) as p:
         d = dev(data)
         p.forward(d, batch)
         torch.cuda.synchronize()
@@ -312,3 +312,48 @@ def test_execute_host_segments(orc, n, L, batch, kernel, mode, ots):
         G.ntt_execute_host(p.handle, data, both, batch, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE)
         assert np.array_equal(both, data)
         assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("n,kernel,mode,ots", [(10, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_AUTO, 0),
+                                               (14, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_OT, 2),
+                                               (16, G.NTT_KERNEL_PER_PASS, G.NTT_TWIDDLE_TABLE, 0),
+                                               (17, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_AUTO, 0)])
+def test_mul_negacyclic(orc, n, kernel, mode, ots):
+    """c = a * b mod (X^N + 1): against the schoolbook product (small N) or the
+    oracle's transforms; a and b keep their forward transforms; c may alias a."""
+    N = 1 << n
+    primes = I.prime_chain(3, 2 * N)
+    a = I.batch_uniform(150 + n, 2, primes, N)
+    b = I.batch_uniform(160 + n, 2, primes, N)
+    A = oracle_fwd(orc, a, primes)
+    B = oracle_fwd(orc, b, primes)
+    if n <= 10:
+        want = np.stack([np.stack([orc.negacyclic_schoolbook(a[k, l], b[k, l], primes[l]) for l in range(3)])
+                         for k in range(2)])
+    else:
+        want = oracle_inv(orc, orc.pointwise_batch(A, B, primes), primes)
+    with G.Plan(N, primes, mode, ots, kernel) as p:
+        da, db, dc = dev(a), dev(b), torch.empty(a.shape, dtype=torch.int64, device="cuda")
+        G.ntt_mul_negacyclic(p.handle, da, db, dc, 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(dc), want)
+        assert np.array_equal(host(da), A) and np.array_equal(host(db), B)
+        da, db = dev(a), dev(b)
+        G.ntt_mul_negacyclic(p.handle, da, db, da, 2)                      # c aliases a
+        torch.cuda.synchronize()
+        assert np.array_equal(host(da), want)
+        assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 12, 13, 16, 17])
+def test_radix2_organisation(orc, n):
+    """One launch per radix-2 stage (the paper's starting point), natural-order
+    table: the same transforms as the oracle."""
+    N = 1 << n
+    primes = I.prime_chain(3, 2 * N)
+    _roundtrip_case(orc, N, primes, 2, 170 + n, G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_RADIX2)
+    with G.Plan(N, primes, G.NTT_TWIDDLE_AUTO, 0, G.NTT_KERNEL_RADIX2) as p:
+        info = p.info()
+        assert (info.kernel, info.twiddle_mode) == (G.NTT_KERNEL_RADIX2, G.NTT_TWIDDLE_TABLE)
+    with pytest.raises(G.NttError):
+        G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_RADIX2)
