@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-batch-compare", action="store_true",
                     help="skip the per-limb C2 path and the uneven 96-job batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the N sweep of kernel organisations")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--launch-steps", type=int, default=500,
                     help="steps of the single-stream pass that times each launch")
@@ -384,6 +385,50 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80):
         del ring
 
 
+def paper_ablation(G, torch, reps=40):
+    """The structure of the paper's N sweep (21 limbs, forward transform,
+    log N = 14..17) on this GPU: the radix-2 launch-per-stage organisation
+    the paper starts from, the launch-per-pass organisation (the paper's
+    two-kernel shared-memory design), and the one-launch fused kernel, each
+    with table and OT twiddles.  Buffers rotate over more than 2x L2."""
+    chain = I.prime_chain(21, 1 << 18)          # 21 largest primes < 2^60 = 1 mod 2^18
+    configs = (("radix2", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_RADIX2),
+               ("per_pass_table", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_PER_PASS),
+               ("per_pass_ot1", G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_PER_PASS),
+               ("fused_table", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_FUSED),
+               ("fused_ot1", G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_FUSED))
+    lib = G.lib()
+    s = torch.cuda.Stream()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(21)
+    out = {"limbs": 21, "unit": "us per forward transform of all 21 limbs (one stream, events)"}
+    for n in (14, 15, 16, 17):
+        N = 1 << n
+        words = 21 * N
+        nbuf = max(2, -(-2 * L2_BYTES // (words * 8)) + 1)
+        pool = torch.empty(nbuf * words, dtype=torch.int64, device="cuda")
+        pool.random_(0, 1 << 59, generator=gen)
+        row = {}
+        for name, mode, ots, kern in configs:
+            with G.Plan(N, chain, mode, ots, kern) as p:
+                ptr = [pool[i * words:(i + 1) * words].data_ptr() for i in range(nbuf)]
+                for i in range(5):
+                    lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for i in range(reps):
+                    lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream)
+                e1.record(s)
+                torch.cuda.synchronize()
+                row[name] = e0.elapsed_time(e1) * 1e3 / reps
+        row["speedup_fused_ot1_vs_radix2"] = row["radix2"] / row["fused_ot1"]
+        row["speedup_per_pass_ot1_vs_radix2"] = row["radix2"] / row["per_pass_ot1"]
+        out[f"logN{n}"] = row
+        del pool
+    return out
+
+
 def config_dict(w, args, ws):
     return {"workload": "c2_n65536_l45_fwd_inv", "N": w.N, "L": len(w.primes), "polys_per_step": 1,
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
@@ -540,6 +585,9 @@ def main():
     if ws == 1 and not args.no_batch_compare:
         per_limb = per_limb_c2(G, torch, w, host, 100)
         batched = batched_c4(G, torch, 10)
+    ablation = None
+    if ws == 1 and not args.no_ablation:
+        ablation = paper_ablation(G, torch)
     served = None
     if ws == 1 and not args.no_serve:
         served = serve_c5(G, torch, args.serve_requests)
@@ -574,6 +622,7 @@ def main():
         "per_limb_path": per_limb,
         "batched_uneven_c4": batched,
         "served_c5": served,
+        "paper_ablation": ablation,
         "gpu_launches": K * 2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes)),
         "clocks": clocks,
         "cpu_baseline": cpu,
