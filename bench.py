@@ -70,6 +70,22 @@ KERNEL_SOURCES = ("arith.cuh", "device_types.cuh", "ntt_pass.cuh", "tma.cuh", "n
                   "launch.cuh", "fused_host.cu", "plan.h", "k_n16.cu")
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(limbs_per_step: int, steps: int, ranks: int, total_ms: float) -> float:
+    """limb-NTT/s of the whole job: every rank transforms its own polynomials
+    (replicas), each step one forward and one inverse of limbs_per_step limbs."""
+    return 2 * limbs_per_step * steps * ranks / (total_ms / 1e3)
+
+
 def kernel_source_hash() -> str:
     """Hash of the sources the N = 2^16 transform kernels are built from, with
     comments and blank space removed (a comment edit keeps a profile valid)."""
@@ -521,19 +537,14 @@ def main():
     clocks = clk.stop()
     if dist is not None:
         dist.barrier()
-    total_ms = e_start.elapsed_time(e_end)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(e_start.elapsed_time(e_end), dist, "cuda")
     for b in bufs:
         if not torch.equal(b, src):
             raise RuntimeError("round trip mismatch after timing")
     for p in plans:
         if p.device_status() != 0:
             raise RuntimeError("device status reports a failed bounded wait")
-    limb_ntts = 2 * L * K * ws
-    value = limb_ntts / (total_ms / 1e3)
+    value = whole_job_value(L, K, ws, total_ms)
 
     # per-launch durations of the transform kernels, one stream, CUDA events
     # around every call (launches do not overlap here)

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "arith.cuh"
+#include "host_logic.h"
 #include "plan.h"
 
 namespace {
@@ -207,26 +208,9 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
     // streams as soon as their copy has landed, and copied out on another
     // stream as soon as their transforms are done, so the two copy directions
     // and the transforms overlap.
-    struct Seg {
-        uint32_t first, count, prime0, lview;
-    };
+    using Seg = ntt::host::Segment;
     constexpr uint32_t kSegments = ntt_plan::kHostSegments;
-    std::vector<Seg> segs;
-    if (batch >= kSegments) {
-        const uint32_t per = (batch + kSegments - 1) / kSegments;
-        for (uint32_t b0 = 0; b0 < batch; b0 += per) {
-            const uint32_t nb = batch - b0 < per ? batch - b0 : per;
-            segs.push_back(Seg{b0 * L, nb * L, 0, L});
-        }
-    } else {
-        const uint32_t pieces = kSegments / batch;                 // batch * pieces <= kSegments
-        const uint32_t c = (L + pieces - 1) / pieces;
-        for (uint32_t b0 = 0; b0 < batch; ++b0)
-            for (uint32_t r = 0; r < L; r += c) {
-                const uint32_t cnt = L - r < c ? L - r : c;
-                segs.push_back(Seg{b0 * L + r, cnt, r, cnt});
-            }
-    }
+    const std::vector<Seg> segs = ntt::host::split_segments(batch, L, kSegments);
     if (segs.size() > kSegments) return NTT_ERR_INVALID_ARG;      // cannot happen: one event pair per segment
     uint32_t seg_max = 0;
     for (const Seg& g : segs) seg_max = g.count > seg_max ? g.count : seg_max;

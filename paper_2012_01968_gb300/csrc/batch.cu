@@ -14,6 +14,7 @@
 
 #include <cuda_runtime.h>
 
+#include "host_logic.h"
 #include "plan.h"
 
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
@@ -54,15 +55,6 @@ void release(ntt_batch* b)
     cudaFree(b->d_status);
     delete b;
 }
-
-// A fused launch: jobs (indices into the call's list) of one group.
-struct Chunk {
-    std::vector<uint32_t> jobs;
-    uint64_t limbs = 0;
-    uint32_t n = 0, ots = 0;
-    bool fwd = true;
-    double work = 0;              // limbs x N, for balancing the streams
-};
 
 }  // namespace
 
@@ -115,44 +107,33 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         const uintptr_t lo = (uintptr_t)j.data;
         ranges[i] = {lo, lo + (uintptr_t)(limbs * j.plan->N * sizeof(uint64_t))};
     }
-    std::sort(ranges.begin(), ranges.end());
-    for (uint32_t i = 1; i < njobs; ++i)
-        if (ranges[i].first < ranges[i - 1].second) return NTT_ERR_INVALID_ARG;
+    if (ntt::host::any_overlap(ranges)) return NTT_ERR_INVALID_ARG;
 
     // group the fused jobs by (size, direction, OT stages); the rest run alone
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<uint32_t>> groups;
-    std::vector<uint32_t> direct;
+    std::vector<uint32_t> fused, direct;
+    std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> keys;
+    std::vector<uint64_t> limbs, sizes;
     for (uint32_t i = 0; i < njobs; ++i) {
         const ntt_plan* p = jobs[i].plan;
         if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED) {
             const uint32_t ots = p->twiddle_mode == NTT_TWIDDLE_OT ? p->ot_stages : 0;
-            groups[std::make_tuple(p->n, jobs[i].op, ots)].push_back(i);
+            fused.push_back(i);
+            keys.emplace_back(p->n, jobs[i].op, ots);
+            limbs.push_back((uint64_t)jobs[i].batch * jobs[i].levels);
+            sizes.push_back(p->N);
         } else {
             direct.push_back(i);
         }
     }
-    std::vector<Chunk> chunks;
-    for (auto& g : groups) {
-        const auto& idx = g.second;
-        for (size_t k = 0; k < idx.size(); k += ntt::FUSED_MAX_JOBS) {
-            Chunk c;
-            c.n = std::get<0>(g.first);
-            c.fwd = std::get<1>(g.first) == NTT_OP_FORWARD;
-            c.ots = std::get<2>(g.first);
-            for (size_t m = k; m < idx.size() && m < k + ntt::FUSED_MAX_JOBS; ++m) {
-                c.jobs.push_back(idx[m]);
-                c.limbs += jobs[idx[m]].batch * jobs[idx[m]].levels;
-            }
-            if (c.limbs > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
-            c.work = (double)c.limbs * (double)(1u << c.n);
-            chunks.push_back(std::move(c));
-        }
+    std::vector<ntt::host::Chunk> chunks = ntt::host::make_chunks(keys, limbs, sizes, ntt::FUSED_MAX_JOBS);
+    for (ntt::host::Chunk& c : chunks) {
+        if (c.limbs > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
+        for (uint32_t& j : c.jobs) j = fused[j];          // indices into the submission
     }
-    std::sort(chunks.begin(), chunks.end(), [](const Chunk& x, const Chunk& y) { return x.work > y.work; });
 
     // one work area per fused launch, back to back; grown after the device drains
     size_t words = 0;
-    for (const Chunk& c : chunks) words += ntt::fused_work_words(c.limbs);
+    for (const ntt::host::Chunk& c : chunks) words += ntt::fused_work_words(c.limbs);
     if (words > b->work_words) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_status(e);
@@ -165,23 +146,21 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         b->work_words = words;
     }
 
-    // fork onto the internal streams, longest launches first on the least loaded stream
+    // fork onto the internal streams
     const cudaStream_t caller = (cudaStream_t)stream;
     const int used = (int)std::min<size_t>(kStreams, chunks.size() + direct.size());
     cudaError_t e = cudaEventRecord(b->fork, caller);
     for (int k = 0; k < used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->s[k], b->fork, 0);
     if (e != cudaSuccess) return cuda_status(e);
-    double load[kStreams] = {};
-    auto pick = [&](double w) {
-        int best = 0;
-        for (int k = 1; k < used; ++k)
-            if (load[k] < load[best]) best = k;
-        load[best] += w;
-        return best;
-    };
+    // longest first, each on the least loaded stream
+    std::vector<double> work;
+    for (const ntt::host::Chunk& c : chunks) work.push_back(c.work);
+    for (uint32_t i : direct) work.push_back((double)jobs[i].batch * jobs[i].levels * jobs[i].plan->N);
+    const std::vector<int> at = ntt::host::place_least_loaded(work, used);
     size_t off = 0;
     std::vector<ntt::JobCtx> jc;
-    for (const Chunk& c : chunks) {
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const ntt::host::Chunk& c = chunks[ci];
         jc.clear();
         for (uint32_t i : c.jobs) {
             const ntt_plan* p = jobs[i].plan;
@@ -189,16 +168,18 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
                                      jobs[i].levels, p->d_primes, p->d_tw, p->tw_len, p->d_ota_f, p->d_otb_f,
                                      p->d_ota_i, p->d_otb_i});
         }
-        const int k = pick(c.work);
-        const ntt::JobsCtx ctx{jc.data(), (uint32_t)jc.size(), c.n, c.ots, b->d_status, b->d_work + off,
+        const int k = at[ci];
+        const uint32_t n = std::get<0>(c.key), ots = std::get<2>(c.key);
+        const bool fwd = std::get<1>(c.key) == NTT_OP_FORWARD;
+        const ntt::JobsCtx ctx{jc.data(), (uint32_t)jc.size(), n, ots, b->d_status, b->d_work + off,
                                (uint32_t)c.limbs, b->s[k]};
         off += ntt::fused_work_words(c.limbs);
-        e = ntt::launch_fused_jobs(ctx, c.fwd);
+        e = ntt::launch_fused_jobs(ctx, fwd);
         if (e != cudaSuccess) break;
     }
     for (size_t m = 0; m < direct.size() && e == cudaSuccess; ++m) {
         const ntt_job& j = jobs[direct[m]];
-        const int k = pick((double)j.batch * j.levels * j.plan->N);
+        const int k = at[chunks.size() + m];
         const ntt::LaunchCtx c = j.plan->ctx(j.data, j.batch * j.levels, j.levels, b->s[k]);
         e = ntt::launch_transform(c, j.op == NTT_OP_FORWARD);
     }

@@ -24,6 +24,7 @@
 
 #include <cuda_runtime.h>
 
+#include "host_logic.h"
 #include "plan.h"
 
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
@@ -57,49 +58,7 @@ struct Slot {
     struct ntt_server* owner = nullptr;
 };
 
-// First-fit allocator over [0, size) with coalescing free ranges.
-class Arena {
-public:
-    void reset(size_t size)
-    {
-        free_.clear();
-        if (size) free_[0] = size;
-    }
-    bool alloc(size_t bytes, size_t* off)
-    {
-        bytes = (bytes + 255) & ~(size_t)255;
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes, at = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[at] = rest;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes)
-    {
-        bytes = (bytes + 255) & ~(size_t)255;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-
-private:
-    std::map<size_t, size_t> free_;
-};
+using Arena = ntt::host::Arena;
 
 }  // namespace
 
