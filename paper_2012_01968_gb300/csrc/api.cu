@@ -175,7 +175,7 @@ ntt_status ntt_mul_negacyclic(const ntt_plan* p, uint64_t* a, uint64_t* b, uint6
         jb.data = reinterpret_cast<ntt::u64*>(b);
         const ntt::JobCtx jobs[2] = {ja, jb};
         const uint32_t ots = p->twiddle_mode == NTT_TWIDDLE_OT ? p->ot_stages : 0;
-        const ntt::JobsCtx jc{jobs, 2u, p->n, ots, p->d_status, p->d_work, p->work_limbs, s};
+        const ntt::JobsCtx jc{jobs, 2u, p->n, ots, p->d_status, p->d_work, p->work_limbs, s, 0u};
         e = ntt::launch_fused_jobs(jc, true);
     } else {
         const ntt::LaunchCtx ca = p->ctx(a, (uint32_t)limbs, p->L, s);
@@ -288,6 +288,33 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
     const cudaError_t so = cudaStreamSynchronize(p->h_out);
     if (se == cudaSuccess) se = so;
     return to_status(e != cudaSuccess ? e : se);
+}
+
+// Test hook (not part of the public interface): the forward transform with
+// the first-pass queue of the fused kernel marked exhausted, so that no limb
+// is ever published and every producer's bounded wait for one runs out after
+// max_polls polls.  The kernel then sets STATUS_DEP_TIMEOUT in the plan's
+// status word, leaves the data untouched and resets its work area.
+ntt_status ntt_internal_test_stalled_forward(const ntt_plan* p, uint64_t* data, uint32_t batch, uint32_t max_polls)
+{
+    if (!p || !data || batch == 0 || max_polls == 0) return NTT_ERR_INVALID_ARG;
+    if (p->passes != 2 || p->kernel != NTT_KERNEL_FUSED) return NTT_ERR_INVALID_ARG;
+    if (!aligned16(data)) return NTT_ERR_MISALIGNED;
+    const uint64_t limbs = (uint64_t)batch * p->L;
+    if (limbs > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
+    if (p->work_limbs < limbs) {
+        cudaError_t e = ntt_internal_grow_work(const_cast<ntt_plan*>(p), (uint32_t)limbs);
+        if (e != cudaSuccess) return to_status(e);
+    }
+    const uint32_t taken = 0x40000000u;          // above any A-ticket count: no A tile is ever claimed
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_work, &taken, sizeof(taken), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return to_status(e);
+    ntt::LaunchCtx c = p->ctx(data, (uint32_t)limbs, p->L, nullptr);
+    c.max_polls = max_polls;
+    e = ntt::launch_transform(c, true);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return to_status(e);
 }
 
 const char* ntt_status_string(ntt_status s)

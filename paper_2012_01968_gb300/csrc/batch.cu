@@ -172,7 +172,7 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         const uint32_t n = std::get<0>(c.key), ots = std::get<2>(c.key);
         const bool fwd = std::get<1>(c.key) == NTT_OP_FORWARD;
         const ntt::JobsCtx ctx{jc.data(), (uint32_t)jc.size(), n, ots, b->d_status, b->d_work + off,
-                               (uint32_t)c.limbs, b->s[k]};
+                               (uint32_t)c.limbs, b->s[k], 0u};
         off += ntt::fused_work_words(c.limbs);
         e = ntt::launch_fused_jobs(ctx, fwd);
         if (e != cudaSuccess) break;

@@ -124,7 +124,7 @@ cudaError_t launch_fused_dir(const JobsCtx& c)
     a.njobs = c.njobs;
     a.limbs = (u32)limbs;
     a.a_window = fused_window_limbs(sizeof(u64) << (P1 + P2));
-    a.max_polls = 1u << 22;
+    a.max_polls = c.max_polls ? c.max_polls : 1u << 22;
     kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(a);
     return cudaGetLastError();
 }
@@ -156,7 +156,7 @@ cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
         }
     }
     const JobCtx job{c.data, c.limbs, c.L, c.primes, c.tw, c.tw_len, c.ota_f, c.otb_f, c.ota_i, c.otb_i};
-    const JobsCtx jc{&job, 1u, c.n, c.ots, c.status, c.work, c.work_limbs, c.stream};
+    const JobsCtx jc{&job, 1u, c.n, c.ots, c.status, c.work, c.work_limbs, c.stream, c.max_polls};
     return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(jc, fwd);
 }
 

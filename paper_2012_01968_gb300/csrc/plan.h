@@ -66,6 +66,7 @@ struct LaunchCtx {
     u32* work;               // fused kernel's work area (zero between launches)
     u32 work_limbs;          // limbs the work area covers (fused_work_words(work_limbs) words)
     cudaStream_t stream;
+    u32 max_polls;           // bound of the fused kernel's waits (0: the default)
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
@@ -97,6 +98,7 @@ struct JobsCtx {
     u32* work;               // zero, fused_work_words(work_limbs) words
     u32 work_limbs;          // >= the jobs' limbs
     cudaStream_t stream;
+    u32 max_polls;           // bound of every wait (0: the default)
 };
 cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
 cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a, const u64* b,
@@ -172,6 +174,7 @@ struct ntt_plan {
         c.work = d_work;
         c.work_limbs = work_limbs;
         c.stream = s;
+        c.max_polls = 0;
         return c;
     }
 

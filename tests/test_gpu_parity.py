@@ -357,3 +357,28 @@ def test_radix2_organisation(orc, n):
         assert (info.kernel, info.twiddle_mode) == (G.NTT_KERNEL_RADIX2, G.NTT_TWIDDLE_TABLE)
     with pytest.raises(G.NttError):
         G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_RADIX2)
+
+
+def test_bench_launch_configuration(orc):
+    """The bench's configuration at full size: two plans on two streams with
+    independent C2 polynomials in flight together, forward then inverse each;
+    every forward output against the oracle."""
+    w = I.workload_c2()
+    datas = [I.batch_uniform(w.seed + 10 * k, 1, w.primes, w.N) for k in range(4)]
+    with G.Plan(w.N, w.primes) as p0, G.Plan(w.N, w.primes) as p1:
+        plans = [p0, p1]
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        bufs = [dev(d) for d in datas]
+        fwd = [torch.empty_like(b) for b in bufs]
+        torch.cuda.synchronize()
+        for k, b in enumerate(bufs):
+            s = streams[k % 2]
+            with torch.cuda.stream(s):
+                plans[k % 2].forward(b, 1, s)
+                fwd[k].copy_(b)
+                plans[k % 2].inverse(b, 1, s)
+        torch.cuda.synchronize()
+        for k, d in enumerate(datas):
+            assert np.array_equal(host(fwd[k]), oracle_fwd(orc, d, w.primes))
+            assert np.array_equal(host(bufs[k]), d)
+        assert p0.device_status() == 0 and p1.device_status() == 0
