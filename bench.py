@@ -243,6 +243,12 @@ def run_reference(args, metric, unit, w):
     print(json.dumps(line), flush=True)
 
 
+def _ok(G, st, what):
+    """Raise on a failed library call (the timing loops call the C ABI directly)."""
+    if st:
+        raise RuntimeError(f"{what}: {G.ntt_status_string(st)} ({G.ntt_last_cuda_error()})")
+
+
 def per_limb_c2(G, torch, w, host, steps):
     """The plain per-limb path on the C2 polynomial: one single-prime plan per
     limb and one launch per limb and direction (45 x 2 launches per step)."""
@@ -256,8 +262,8 @@ def per_limb_c2(G, torch, w, host, steps):
 
         def step():
             for l in range(L):
-                lib.ntt_forward(plans[l].handle, bufs[l].data_ptr(), 1, s.cuda_stream)
-                lib.ntt_inverse(plans[l].handle, bufs[l].data_ptr(), 1, s.cuda_stream)
+                _ok(G, lib.ntt_forward(plans[l].handle, bufs[l].data_ptr(), 1, s.cuda_stream), "per-limb forward")
+                _ok(G, lib.ntt_inverse(plans[l].handle, bufs[l].data_ptr(), 1, s.cuda_stream), "per-limb inverse")
 
         for _ in range(3):
             step()
@@ -326,8 +332,8 @@ def batched_c4(G, torch, reps):
 
         def singles():
             for h, buf, bt, lv, op in spec:
-                (lib.ntt_forward_levels if op == G.NTT_OP_FORWARD else lib.ntt_inverse_levels)(
-                    h, buf.data_ptr(), bt, lv, s.cuda_stream)
+                _ok(G, (lib.ntt_forward_levels if op == G.NTT_OP_FORWARD else lib.ntt_inverse_levels)(
+                    h, buf.data_ptr(), bt, lv, s.cuda_stream), "single call")
         out["per_job_calls"] = timed(singles)
         return out
     finally:
@@ -429,12 +435,12 @@ def paper_ablation(G, torch, reps=40):
             with G.Plan(N, chain, mode, ots, kern) as p:
                 ptr = [pool[i * words:(i + 1) * words].data_ptr() for i in range(nbuf)]
                 for i in range(5):
-                    lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream)
+                    _ok(G, lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream), name)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(s)
                 for i in range(reps):
-                    lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream)
+                    _ok(G, lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream), name)
                 e1.record(s)
                 torch.cuda.synchronize()
                 row[name] = e0.elapsed_time(e1) * 1e3 / reps
@@ -443,6 +449,57 @@ def paper_ablation(G, torch, reps=40):
         out[f"logN{n}"] = row
         del pool
     return out
+
+
+def large_ring_c3(G, torch, reps=50):
+    """The large ring: N = 2^17, L = 60, one ciphertext (batch 2), forward
+    then inverse per step on one stream; and the negacyclic product of two
+    polynomials (two forwards in one launch, element-wise product, inverse)."""
+    w = I.workload_c3()
+    N, primes, L = w.N, w.primes, len(w.primes)
+    host = I.batch_uniform(w.seed, 2, primes, N)
+    src = torch.from_numpy(host.view(np.int64).copy()).cuda()
+    words = src.numel()
+    nbuf = max(2, -(-2 * L2_BYTES // (words * 8)) + 1)
+    bufs = [src.clone() for _ in range(nbuf)]
+    s = torch.cuda.Stream()
+    lib = G.lib()
+    with G.Plan(N, primes) as p:
+        def timed(fn, k):
+            with torch.cuda.stream(s):
+                for i in range(3):
+                    fn(i)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for i in range(k):
+                    fn(i)
+                e1.record(s)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / k
+
+        def step(i):
+            b = bufs[i % nbuf].data_ptr()
+            _ok(G, lib.ntt_forward(p.handle, b, 2, s.cuda_stream), "C3 forward")
+            _ok(G, lib.ntt_inverse(p.handle, b, 2, s.cuda_stream), "C3 inverse")
+        ms = timed(step, reps)
+        if not all(torch.equal(b, src) for b in bufs):
+            raise RuntimeError("C3 round trip mismatch")
+        c = torch.empty(L * N, dtype=torch.int64, device="cuda")
+
+        def product(i):
+            b = bufs[i % nbuf].view(-1)     # its two polynomials a = b[:LN], b = b[LN:] (left transformed)
+            st = lib.ntt_mul_negacyclic(p.handle, b[:L * N].data_ptr(), b[L * N:].data_ptr(), c.data_ptr(), 1,
+                                        s.cuda_stream)
+            _ok(G, st, "ntt_mul_negacyclic")
+        ms_mul = timed(product, reps)
+        if p.device_status() != 0:
+            raise RuntimeError("C3 device status reports a failed bounded wait")
+    return {"workload": "N=2^17, L=60, batch 2 (one ciphertext), forward + inverse, one stream",
+            "value": 2 * 2 * L / (ms / 1e3), "unit": "limb-NTT/s", "ms_per_step": ms,
+            "alg_bytes_per_step": 2 * 2 * 16 * L * N,
+            "negacyclic_product_us": ms_mul * 1e3,
+            "negacyclic_product": "c = a * b mod (X^N + 1), 60 limbs: 2 forwards in one launch, product, inverse"}
 
 
 def config_dict(w, args, ws):
@@ -556,9 +613,9 @@ def main():
         ev[0].record(s0)
         for i in range(Kp):
             b = bufs[i % nbuf].data_ptr()
-            lib.ntt_forward(handles[0], b, 1, s0.cuda_stream)
+            _ok(G, lib.ntt_forward(handles[0], b, 1, s0.cuda_stream), "forward")
             ev[2 * i + 1].record(s0)
-            lib.ntt_inverse(handles[0], b, 1, s0.cuda_stream)
+            _ok(G, lib.ntt_inverse(handles[0], b, 1, s0.cuda_stream), "inverse")
             ev[2 * i + 2].record(s0)
     torch.cuda.synchronize()
     fwd_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Kp)]
@@ -596,6 +653,9 @@ def main():
     if ws == 1 and not args.no_batch_compare:
         per_limb = per_limb_c2(G, torch, w, host, 100)
         batched = batched_c4(G, torch, 10)
+    large = None
+    if ws == 1 and not args.no_batch_compare:
+        large = large_ring_c3(G, torch)
     ablation = None
     if ws == 1 and not args.no_ablation:
         ablation = paper_ablation(G, torch)
@@ -634,6 +694,7 @@ def main():
         "batched_uneven_c4": batched,
         "served_c5": served,
         "paper_ablation": ablation,
+        "large_ring_c3": large,
         "gpu_launches": K * 2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes)),
         "clocks": clocks,
         "cpu_baseline": cpu,
