@@ -169,6 +169,19 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+# Integer-multiply roofline of the butterfly.  Per SM and clock the FMA-heavy
+# pipe retires 64 lanes of IMAD, 32 of IMAD.WIDE and 16 of IMAD.HI (measured
+# with a register-only micro-benchmark on this GPU); Shoup's lazy product
+# (arith.cuh) issues 3 IMAD.WIDE, 2 IMAD.HI and 4 IMAD per butterfly, so a
+# butterfly occupies 3/32 + 2/16 + 4/64 SM-clocks of the pipe.
+SMS, SM_MHZ_MAX = 152, 2070.0
+BFLY_PER_SM_CLK = 1.0 / (3 / 32 + 2 / 16 + 4 / 64)
+
+
+def alu_peak_gbfly(sm_mhz=SM_MHZ_MAX):
+    return SMS * BFLY_PER_SM_CLK * sm_mhz * 1e6 / 1e9
+
+
 def measured_peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -628,6 +641,8 @@ def main():
     dom_name, dom_ms = ("ntt_forward", fwd_avg) if fwd_avg >= inv_avg else ("ntt_inverse", inv_avg)
     alg_bytes = 2 * poly_bytes                       # one read + one write per transform
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    bfly_per_launch = L * (N // 2) * (N.bit_length() - 1)         # (N/2) log2 N butterflies per limb
+    bfly_achieved = bfly_per_launch / (dom_ms / 1e3) / 1e9
     step_bytes = 2 * alg_bytes
     frac_step = (step_bytes * K / (total_ms / 1e3) / 1e9) / peak
 
@@ -677,7 +692,18 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": config_dict(w, args, ws),
         "hbm_roofline_frac_step": frac_step,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "alu", "achieved": bfly_achieved, "peak": alu_peak_gbfly(),
+                     "unit": "G butterfly/s", "frac": bfly_achieved / alu_peak_gbfly(),
+                     "traffic": profile_traffic(),
+                     "kernel": f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})",
+                     "units_per_launch": f"{bfly_per_launch} butterflies (45 limbs x (N/2) log2 N)",
+                     "avg_launch_us": dom_ms * 1e3,
+                     "peak_source": "152 SMs x 2070 MHz x 3.56 butterflies per SM-clock (FMA-heavy pipe: "
+                                    "3 IMAD.WIDE + 2 IMAD.HI + 4 IMAD per butterfly at 32/16/64 lanes per clock)",
+                     "peak_measured": G.ntt_measure_butterfly_rate(),
+                     "peak_measured_source": "ntt_measure_butterfly_rate: register-only butterfly loop, live",
+                     "timed_region_frac": bfly_per_launch * 2 * K / (total_ms / 1e3) / 1e9 / alu_peak_gbfly()},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profile_traffic(),
                      "kernel": f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})",
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,

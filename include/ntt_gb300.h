@@ -336,6 +336,16 @@ ntt_status ntt_server_wait(ntt_server* server, uint64_t ticket, uint64_t timeout
 /* Timestamps of a request (for latency statistics). */
 ntt_status ntt_server_request_times(ntt_server* server, uint64_t ticket, ntt_request_times* times);
 
+/*
+ * Measurement helper for the roofline of the transform kernels (not part of
+ * the transform path; the paper has no counterpart): times a register-only
+ * loop of the forward butterfly (Shoup's lazy product, the range reduction
+ * every other stage) on the current device and writes the butterflies per
+ * second in units of 1e9.  Allocates and frees a small device buffer and
+ * synchronises the device.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_CUDA.
+ */
+ntt_status ntt_measure_butterfly_rate(double* gbfly_per_s);
+
 /* Plan facts, for callers and tests. */
 typedef struct ntt_plan_info {
     uint32_t N, L;

@@ -144,6 +144,8 @@ def _lib():
             L.ntt_server_wait.argtypes = [_vp, _u64, _u64]
             L.ntt_server_request_times.restype = S
             L.ntt_server_request_times.argtypes = [_vp, _u64, ctypes.POINTER(RequestTimes)]
+            L.ntt_measure_butterfly_rate.restype = S
+            L.ntt_measure_butterfly_rate.argtypes = [ctypes.POINTER(ctypes.c_double)]
             L.ntt_plan_query.restype = S
             L.ntt_plan_query.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
             L.ntt_plan_device_status.restype = S
@@ -312,6 +314,13 @@ def ntt_batch_submit(batch: int, jobs, stream=None) -> None:
 def ntt_batch_device_status(batch: int) -> int:
     v = _u32()
     _check(_lib().ntt_batch_device_status(batch, ctypes.byref(v)), "ntt_batch_device_status")
+    return v.value
+
+
+def ntt_measure_butterfly_rate() -> float:
+    """Butterflies per second (1e9) of a register-only loop of the transform's butterfly."""
+    v = ctypes.c_double()
+    _check(_lib().ntt_measure_butterfly_rate(ctypes.byref(v)), "ntt_measure_butterfly_rate")
     return v.value
 
 

@@ -382,3 +382,11 @@ def test_bench_launch_configuration(orc):
             assert np.array_equal(host(fwd[k]), oracle_fwd(orc, d, w.primes))
             assert np.array_equal(host(bufs[k]), d)
         assert p0.device_status() == 0 and p1.device_status() == 0
+
+
+def test_butterfly_rate_measurement():
+    """The roofline helper: a register-only butterfly loop runs at a rate of
+    the order of the multiply-pipe bound (152 SMs x 2.07 GHz x 3.56/clock)."""
+    r = G.ntt_measure_butterfly_rate()
+    derived = 152 * 2.07 * 3.556                   # G butterflies per second
+    assert 0.3 * derived < r < 1.5 * derived, r
