@@ -326,7 +326,9 @@ void ntt_server_destroy(ntt_server* server);
 
 /* Queue a request; *ticket identifies it.  Errors: NTT_ERR_INVALID_ARG (bad
  * field, or a request larger than the budget or the arena), NTT_ERR_MISALIGNED,
- * NTT_ERR_BUSY (max_queue requests already waiting: admission refused). */
+ * NTT_ERR_BUSY (max_queue requests already waiting: admission refused),
+ * NTT_ERR_CUDA (a copy or launch of the server failed earlier; the server
+ * takes no more requests). */
 ntt_status ntt_server_submit(ntt_server* server, const ntt_request* request, uint64_t* ticket);
 
 /* Wait up to timeout_ns for a request: its status (NTT_OK, or the error of

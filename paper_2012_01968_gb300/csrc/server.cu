@@ -276,6 +276,10 @@ ntt_status ntt_server_submit(ntt_server* srv, const ntt_request* req, uint64_t* 
     {
         std::lock_guard<std::mutex> g(srv->mu);
         if (srv->stop) return NTT_ERR_INVALID_ARG;
+        if (srv->fatal != cudaSuccess) {                 // a copy or launch of the server failed
+            ntt_internal_set_cuda_error(srv->fatal);
+            return NTT_ERR_CUDA;
+        }
         if (srv->pending.size() >= srv->opts.max_queue) return NTT_ERR_BUSY;
         r->ticket = srv->next_ticket++;
         r->t_submit = now_ns();

@@ -1,6 +1,5 @@
 """C ABI: the library loads, exports every declared symbol, and validates
 arguments on the host (no GPU needed for any of these)."""
-import ctypes
 import os
 import subprocess
 
