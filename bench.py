@@ -515,6 +515,61 @@ def large_ring_c3(G, torch, reps=50):
             "negacyclic_product": "c = a * b mod (X^N + 1), 60 limbs: 2 forwards in one launch, product, inverse"}
 
 
+def twiddle_modes_c2(G, torch, w, bufs, nbuf, reps=200):
+    """C2 per-launch times under each twiddle supply (table, OT of the last
+    one or two stages): one stream, CUDA events around the loop."""
+    out = {}
+    lib = G.lib()
+    s = torch.cuda.Stream()
+    for name, mode, ots in (("table", G.NTT_TWIDDLE_TABLE, 0), ("ot1", G.NTT_TWIDDLE_OT, 1),
+                            ("ot2", G.NTT_TWIDDLE_OT, 2)):
+        with G.Plan(w.N, w.primes, mode, ots) as p:
+            for fwd in (True, False):
+                fn = lib.ntt_forward if fwd else lib.ntt_inverse
+                for i in range(5):
+                    _ok(G, fn(p.handle, bufs[i % nbuf].data_ptr(), 1, s.cuda_stream), name)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                for i in range(reps):
+                    _ok(G, fn(p.handle, bufs[i % nbuf].data_ptr(), 1, s.cuda_stream), name)
+                e1.record(s)
+                torch.cuda.synchronize()
+                out[f"{name}_{'forward' if fwd else 'inverse'}_us"] = e0.elapsed_time(e1) * 1e3 / reps
+            # each buffer went through as many inverses as forwards: unchanged
+    torch.cuda.synchronize()
+    return out
+
+
+def single_limb_c1(G, torch, reps=500):
+    """C1: one limb of N = 2^12, forward then inverse, one stream: the launch
+    latency of the one-pass kernel."""
+    w = I.workload_c1()
+    host = I.batch_uniform(w.seed, 1, w.primes, w.N)
+    d = torch.from_numpy(host.view(np.int64).copy()).cuda()
+    ref = d.clone()
+    lib = G.lib()
+    s = torch.cuda.Stream()
+    with G.Plan(w.N, w.primes) as p:
+        def step():
+            _ok(G, lib.ntt_forward(p.handle, d.data_ptr(), 1, s.cuda_stream), "C1 forward")
+            _ok(G, lib.ntt_inverse(p.handle, d.data_ptr(), 1, s.cuda_stream), "C1 inverse")
+        for _ in range(10):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            step()
+        e1.record(s)
+        torch.cuda.synchronize()
+    if not torch.equal(d, ref):
+        raise RuntimeError("C1 round trip mismatch")
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    return {"workload": "N=2^12, L=1, forward + inverse, one stream", "us_per_step": us,
+            "value": 2 / (us / 1e6), "unit": "limb-NTT/s"}
+
+
 def config_dict(w, args, ws):
     return {"workload": "c2_n65536_l45_fwd_inv", "N": w.N, "L": len(w.primes), "polys_per_step": 1,
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
@@ -668,9 +723,11 @@ def main():
     if ws == 1 and not args.no_batch_compare:
         per_limb = per_limb_c2(G, torch, w, host, 100)
         batched = batched_c4(G, torch, 10)
-    large = None
+    large = modes = c1 = None
     if ws == 1 and not args.no_batch_compare:
         large = large_ring_c3(G, torch)
+        modes = twiddle_modes_c2(G, torch, w, bufs, nbuf)
+        c1 = single_limb_c1(G, torch)
     ablation = None
     if ws == 1 and not args.no_ablation:
         ablation = paper_ablation(G, torch)
@@ -721,6 +778,8 @@ def main():
         "served_c5": served,
         "paper_ablation": ablation,
         "large_ring_c3": large,
+        "twiddle_modes_c2": modes,
+        "single_limb_c1": c1,
         "gpu_launches": K * 2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes)),
         "clocks": clocks,
         "cpu_baseline": cpu,
