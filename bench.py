@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-batch-compare", action="store_true",
                     help="skip the per-limb C2 path and the uneven 96-job batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--no-peak-measure", action="store_true",
+                    help="skip the live butterfly-rate measurement (for profiling runs)")
     ap.add_argument("--no-ablation", action="store_true", help="skip the N sweep of kernel organisations")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--launch-steps", type=int, default=500,
@@ -757,7 +759,7 @@ def main():
                      "avg_launch_us": dom_ms * 1e3,
                      "peak_source": "152 SMs x 2070 MHz x 3.56 butterflies per SM-clock (FMA-heavy pipe: "
                                     "3 IMAD.WIDE + 2 IMAD.HI + 4 IMAD per butterfly at 32/16/64 lanes per clock)",
-                     "peak_measured": G.ntt_measure_butterfly_rate(),
+                     "peak_measured": None if args.no_peak_measure else G.ntt_measure_butterfly_rate(),
                      "peak_measured_source": "ntt_measure_butterfly_rate: register-only butterfly loop, live",
                      "timed_region_frac": bfly_per_launch * 2 * K / (total_ms / 1e3) / 1e9 / alu_peak_gbfly()},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
