@@ -390,3 +390,28 @@ def test_butterfly_rate_measurement():
     r = G.ntt_measure_butterfly_rate()
     derived = 152 * 2.07 * 3.556                   # G butterflies per second
     assert 0.3 * derived < r < 1.5 * derived, r
+
+
+@pytest.mark.parametrize("shape", ["c2", "c3"])
+def test_monomial_product_is_signed_shift_full_size(shape):
+    """At full size, a * X^k mod (X^N + 1) is a rotation of a by k with the
+    wrapped coefficients negated: a property of the product that needs no
+    oracle, checked through the forward, product and inverse kernels."""
+    w = I.workload_c2() if shape == "c2" else I.workload_c3()
+    N, primes = w.N, w.primes
+    L = len(primes)
+    a = I.batch_uniform(w.seed + 40, 1, primes, N)
+    rng = np.random.default_rng(41)
+    q = np.array(primes, dtype=np.uint64)[:, None]
+    with G.Plan(N, primes) as p:
+        for k in (0, 1, int(rng.integers(2, N - 1)), N - 1):
+            x = np.zeros((1, L, N), np.uint64)
+            x[:, :, k] = 1
+            want = np.roll(a[0], k, axis=1)
+            want[:, :k] = np.where(want[:, :k] == 0, 0, q - want[:, :k])     # -a mod q for the wrapped part
+            da, dx = dev(a), dev(x)
+            dc = torch.empty_like(da)
+            G.ntt_mul_negacyclic(p.handle, da, dx, dc, 1)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(dc)[0], want), f"k={k}"
+        assert p.device_status() == 0

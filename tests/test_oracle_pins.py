@@ -15,7 +15,7 @@ def test_oracle_pin(orc, pin):
     pin(orc)
 
 
-def test_survey_cross_check_values(orc):
+def test_psi_of_first_primes_against_sympy(orc):
     """psi for the first prime of each chain, recomputed live with sympy."""
     sympy = pytest.importorskip("sympy")
     import ntt_inputs as I
