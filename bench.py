@@ -543,6 +543,76 @@ def twiddle_modes_c2(G, torch, w, bufs, nbuf, reps=200):
     return out
 
 
+def word_size(G, torch, N, primes64, seed, reps=100):
+    """Sec. IV's word-size question: one modulus built from primes below 2^60
+    in 64-bit words, or from 28-bit primes in 32-bit words (about twice as
+    many limbs, at least as many bits), forward + inverse per step on one
+    stream.  Both with table twiddles and one launch per pass; the 64-bit
+    side also with its default (fused) kernel."""
+    import math
+    bits64 = sum(math.log2(q) for q in primes64)
+    cand = I.prime_chain(4 * len(primes64), 2 * N, below=1 << 28)
+    L32, acc = 0, 0.0
+    while acc < bits64:
+        acc += math.log2(cand[L32])
+        L32 += 1
+    p32 = cand[:L32]
+    lib = G.lib()
+    s = torch.cuda.Stream()
+
+    def timed(step):
+        for i in range(3):
+            step(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for i in range(reps):
+            step(i)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    out = {"workload": f"N=2^{N.bit_length() - 1}, modulus {bits64:.0f} bits, forward + inverse, one stream",
+           "limbs_64": len(primes64), "limbs_32": L32, "bits_32": acc}
+    h64 = I.batch_uniform(seed, 1, primes64, N)
+    src64 = torch.from_numpy(h64.view(np.int64).copy()).cuda()
+    nb64 = max(2, -(-2 * L2_BYTES // (src64.numel() * 8)) + 1)
+    b64 = [src64.clone() for _ in range(nb64)]
+    for name, kern in (("u64_per_pass_us", G.NTT_KERNEL_PER_PASS), ("u64_fused_us", G.NTT_KERNEL_AUTO)):
+        mode = G.NTT_TWIDDLE_TABLE if kern == G.NTT_KERNEL_PER_PASS else G.NTT_TWIDDLE_AUTO
+        with G.Plan(N, primes64, mode, 0, kern) as p:
+            def step(i):
+                b = b64[i % nb64].data_ptr()
+                _ok(G, lib.ntt_forward(p.handle, b, 1, s.cuda_stream), "u64 forward")
+                _ok(G, lib.ntt_inverse(p.handle, b, 1, s.cuda_stream), "u64 inverse")
+            out[name] = timed(step)
+    if not all(torch.equal(b, src64) for b in b64):
+        raise RuntimeError("64-bit word-size round trip mismatch")
+    h32 = I.batch_uniform(seed, 1, p32, N)
+    src32 = torch.from_numpy(h32.astype(np.uint32).view(np.int32).copy()).cuda()
+    nb32 = max(2, -(-2 * L2_BYTES // (src32.numel() * 4)) + 1)
+    b32 = [src32.clone() for _ in range(nb32)]
+    with G.Plan32(N, p32) as p:
+        def step32(i):
+            b = b32[i % nb32].data_ptr()
+            _ok(G, lib.ntt_forward32(p.handle, b, 1, s.cuda_stream), "u32 forward")
+            _ok(G, lib.ntt_inverse32(p.handle, b, 1, s.cuda_stream), "u32 inverse")
+        out["u32_per_pass_us"] = timed(step32)
+    if not all(torch.equal(b, src32) for b in b32):
+        raise RuntimeError("32-bit word-size round trip mismatch")
+    out["u32_vs_u64_per_pass"] = out["u64_per_pass_us"] / out["u32_per_pass_us"]
+    out["u32_vs_u64_fused"] = out["u64_fused_us"] / out["u32_per_pass_us"]
+    return out
+
+
+def word_sizes(G, torch):
+    """The word-size comparison on the C2 ring (N = 2^16, 45 x 60-bit primes)
+    and on the paper's own case (N = 2^17, Q about 2^1200: 20 x 60-bit primes)."""
+    w = I.workload_c2()
+    return {"c2_n65536": word_size(G, torch, w.N, w.primes, w.seed),
+            "paper_n131072_q1200": word_size(G, torch, 1 << 17, I.chain_for(1 << 17, 20), 7)}
+
+
 def single_limb_c1(G, torch, reps=500):
     """C1: one limb of N = 2^12, forward then inverse, one stream: the launch
     latency of the one-pass kernel."""
@@ -725,11 +795,12 @@ def main():
     if ws == 1 and not args.no_batch_compare:
         per_limb = per_limb_c2(G, torch, w, host, 100)
         batched = batched_c4(G, torch, 10)
-    large = modes = c1 = None
+    large = modes = c1 = words = None
     if ws == 1 and not args.no_batch_compare:
         large = large_ring_c3(G, torch)
         modes = twiddle_modes_c2(G, torch, w, bufs, nbuf)
         c1 = single_limb_c1(G, torch)
+        words = word_sizes(G, torch)
     ablation = None
     if ws == 1 and not args.no_ablation:
         ablation = paper_ablation(G, torch)
@@ -782,6 +853,7 @@ def main():
         "large_ring_c3": large,
         "twiddle_modes_c2": modes,
         "single_limb_c1": c1,
+        "word_size": words,
         "gpu_launches": K * 2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes)),
         "clocks": clocks,
         "cpu_baseline": cpu,

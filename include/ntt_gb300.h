@@ -339,6 +339,41 @@ ntt_status ntt_server_wait(ntt_server* server, uint64_t ticket, uint64_t timeout
 ntt_status ntt_server_request_times(ntt_server* server, uint64_t ticket, ntt_request_times* times);
 
 /*
+ * 32-bit word transforms (Sec. IV, "32b vs. 64b word size": the same modulus
+ * built from twice as many primes of half the width).  A separate plan type
+ * over primes q < 2^28 with q = 1 mod 2N, residues held in uint32_t.  The
+ * transform is the same negacyclic NTT as ntt_forward / ntt_inverse (same psi
+ * rule: psi = g^{(q-1)/2N} for the smallest generator g of Z_q^*), with table
+ * twiddles and one launch per pass.
+ */
+typedef struct ntt_plan32 ntt_plan32;
+
+/*
+ * Create a 32-bit plan.  N as for ntt_plan_create; primes: host array of L
+ * primes with q = 1 mod 2N and q < 2^28 (copied); 1 <= L <= 4096.  Device
+ * tables of 8 * N * L bytes, created on the current CUDA device.  Errors:
+ * NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME, NTT_ERR_OOM, NTT_ERR_CUDA; *out is
+ * left untouched on error.
+ */
+ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L);
+
+/* Free a 32-bit plan.  NULL is allowed.  Work that uses it must have finished. */
+void ntt_plan32_destroy(ntt_plan32* plan);
+
+/*
+ * In-place forward / inverse transform of `batch` polynomials of 32-bit
+ * residues at device address `data` (layout [batch][L][N], 16-byte aligned,
+ * caller-owned).  Orders and scaling as ntt_forward / ntt_inverse.  Errors:
+ * NTT_ERR_INVALID_ARG (NULL, batch == 0, batch * L >= 2^32),
+ * NTT_ERR_MISALIGNED, NTT_ERR_CUDA (launch failure).
+ */
+ntt_status ntt_forward32(const ntt_plan32* plan, uint32_t* data, uint32_t batch, void* stream);
+ntt_status ntt_inverse32(const ntt_plan32* plan, uint32_t* data, uint32_t batch, void* stream);
+
+/* psi for prime l (0 <= l < L) of a 32-bit plan, into *psi. */
+ntt_status ntt_plan32_psi(const ntt_plan32* plan, uint32_t l, uint32_t* psi);
+
+/*
  * Measurement helper for the roofline of the transform kernels (not part of
  * the transform path; the paper has no counterpart): times a register-only
  * loop of the forward butterfly (Shoup's lazy product, the range reduction

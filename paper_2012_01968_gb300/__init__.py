@@ -152,6 +152,15 @@ def _lib():
             L.ntt_plan_device_status.argtypes = [_vp, ctypes.POINTER(_u32)]
             L.ntt_plan_psi.restype = S
             L.ntt_plan_psi.argtypes = [_vp, _u32, _u64p]
+            L.ntt_plan32_create.restype = S
+            L.ntt_plan32_create.argtypes = [ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32), _u32]
+            L.ntt_plan32_destroy.restype = None
+            L.ntt_plan32_destroy.argtypes = [_vp]
+            for f in ("ntt_forward32", "ntt_inverse32"):
+                getattr(L, f).restype = S
+                getattr(L, f).argtypes = [_vp, _vp, _u32, _vp]
+            L.ntt_plan32_psi.restype = S
+            L.ntt_plan32_psi.argtypes = [_vp, _u32, ctypes.POINTER(_u32)]
             L.ntt_status_string.restype = ctypes.c_char_p
             L.ntt_status_string.argtypes = [S]
             L.ntt_last_cuda_error.restype = ctypes.c_char_p
@@ -342,6 +351,40 @@ def ntt_plan_psi(plan: int, l: int) -> int:
     return int(v.value)
 
 
+def ntt_plan32_create_status(N: int, primes):
+    """Create a 32-bit plan; returns (status, handle) without raising."""
+    primes = [int(p) for p in primes]
+    arr = (_u32 * max(1, len(primes)))(*primes)
+    out = _vp()
+    st = _lib().ntt_plan32_create(ctypes.byref(out), N, arr if primes else None, len(primes))
+    return st, (int(out.value) if out.value else 0)
+
+
+def ntt_plan32_create(N: int, primes) -> int:
+    """Create a 32-bit plan (primes q < 2^28); returns the handle.  Raises NttError."""
+    st, h = ntt_plan32_create_status(N, primes)
+    _check(st, "ntt_plan32_create")
+    return h
+
+
+def ntt_plan32_destroy(plan: int) -> None:
+    _lib().ntt_plan32_destroy(plan)
+
+
+def ntt_forward32(plan: int, data, batch: int, stream=None) -> None:
+    _check(_lib().ntt_forward32(plan, _addr(data), batch, _stream(stream, data)), "ntt_forward32")
+
+
+def ntt_inverse32(plan: int, data, batch: int, stream=None) -> None:
+    _check(_lib().ntt_inverse32(plan, _addr(data), batch, _stream(stream, data)), "ntt_inverse32")
+
+
+def ntt_plan32_psi(plan: int, l: int) -> int:
+    v = _u32()
+    _check(_lib().ntt_plan32_psi(plan, l, ctypes.byref(v)), "ntt_plan32_psi")
+    return int(v.value)
+
+
 def ntt_status_string(status: int) -> str:
     return _lib().ntt_status_string(status).decode()
 
@@ -375,6 +418,39 @@ class Plan:
     def close(self):
         if self.handle:
             ntt_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan32:
+    """RAII wrapper over a 32-bit plan handle (residues in int32/uint32 tensors)."""
+
+    def __init__(self, N: int, primes):
+        self.N = N
+        self.primes = [int(p) for p in primes]
+        self.L = len(self.primes)
+        self.handle = ntt_plan32_create(N, self.primes)
+
+    def forward(self, data, batch: int = 1, stream=None):
+        ntt_forward32(self.handle, data, batch, stream)
+
+    def inverse(self, data, batch: int = 1, stream=None):
+        ntt_inverse32(self.handle, data, batch, stream)
+
+    def close(self):
+        if self.handle:
+            ntt_plan32_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

@@ -199,6 +199,92 @@ __device__ __forceinline__ void gs_bfly_scaled(u64& x, u64& y, const Tw wn, cons
     y = shoup_lazy(d, wn.w, wn.wp, q);
 }
 
+// ---------------------------------------------------------------------------
+// 32-bit words.  Primes q < 2^28, so every value below 16q fits a word and the
+// range bookkeeping above applies unchanged.  Shoup's product takes the exact
+// quotient estimate qhat = hi32(y w'), w' = floor(w 2^32 / q): for y < 2^32,
+// floor(y w / q) - qhat <= 1, so r = lo32(y w - qhat q) lies in [0, 2q), within
+// the [0, 4q) the butterflies allow.
+// ---------------------------------------------------------------------------
+struct __align__(8) Tw32 {     // a twiddle and its 32-bit Shoup companion
+    u32 w, wp;
+};
+
+__device__ __forceinline__ u32 shoup_lazy(u32 y, u32 w, u32 wp, u32 q)
+{
+    const u32 qhat = __umulhi(y, wp);
+    return y * w - qhat * q;      // exact value < 2q
+}
+
+__device__ __forceinline__ u32 csub(u32 x, u32 c) { return x >= c ? x - c : x; }
+
+template <int X>
+__device__ __forceinline__ u32 canon(u32 x, u32 q, u32)
+{
+    static_assert(X >= 1 && X <= 16, "range");
+    if (X > 8) x = csub(x, q << 3);
+    if (X > 4) x = csub(x, q << 2);
+    if (X > 2) x = csub(x, q << 1);
+    if (X > 1) x = csub(x, q);
+    return x;
+}
+
+template <int X>
+__device__ __forceinline__ void ct_bfly(u32& x, u32& y, const u32 w, const u32 wp, const u32 q, const u32 q4,
+                                        const u32)
+{
+    u32 a = x;
+    if (ct_reduces(X)) a = csub(a, q4 << 1);
+    const u32 t = shoup_lazy(y, w, wp, q);
+    x = a + t;
+    y = a + q4 - t;
+}
+
+template <int X>
+__device__ __forceinline__ void ct_bfly_ot(u32& x, u32& y, const Tw32 f1, const Tw32 f2, const u32 q,
+                                           const u32 q4, const u32)
+{
+    u32 a = x;
+    if (ct_reduces(X)) a = csub(a, q4 << 1);
+    const u32 t = shoup_lazy(shoup_lazy(y, f1.w, f1.wp, q), f2.w, f2.wp, q);
+    x = a + t;
+    y = a + q4 - t;
+}
+
+template <int X, bool NEG>
+__device__ __forceinline__ void gs_bfly(u32& x, u32& y, const u32 w, const u32 wp, const u32 q, const u32)
+{
+    static_assert(X <= 8, "GS inputs must stay below 8q");
+    const u32 Xq = (u32)X * q;
+    const u32 d = NEG ? (y + Xq - x) : (x + Xq - y);
+    u32 s = x + y;
+    if (gs_reduces(X)) s = csub(s, q << 3);
+    x = s;
+    y = shoup_lazy(d, w, wp, q);
+}
+
+template <int X, bool NEG>
+__device__ __forceinline__ void gs_bfly_ot(u32& x, u32& y, const Tw32 f1, const Tw32 f2, const u32 q, const u32)
+{
+    static_assert(X <= 8, "GS inputs must stay below 8q");
+    const u32 Xq = (u32)X * q;
+    const u32 d = NEG ? (y + Xq - x) : (x + Xq - y);
+    u32 s = x + y;
+    if (gs_reduces(X)) s = csub(s, q << 3);
+    x = s;
+    y = shoup_lazy(shoup_lazy(d, f1.w, f1.wp, q), f2.w, f2.wp, q);
+}
+
+template <int X, bool NEG>
+__device__ __forceinline__ void gs_bfly_scaled(u32& x, u32& y, const Tw32 wn, const Tw32 ninv, const u32 q)
+{
+    static_assert(X <= 8, "GS inputs must stay below 8q");
+    const u32 Xq = (u32)X * q;
+    const u32 d = NEG ? (y + Xq - x) : (x + Xq - y);
+    x = shoup_lazy(x + y, ninv.w, ninv.wp, q);
+    y = shoup_lazy(d, wn.w, wn.wp, q);
+}
+
 // Barrett product of two residues a, b < q (data times data, no companion;
 // Barrett, CRYPTO 1986).  k = bit length of q, mu = floor(2^{2k} / q) < 2^{k+1}:
 //   t = floor(ab / 2^{k-1}),  qhat = floor(t mu / 2^{k+1}),  r = ab - qhat q

@@ -14,13 +14,40 @@ struct __align__(16) PrimeDev {
     u32 k;           // bit length of q
 };
 
+// Per-prime constants of a 32-bit plan (primes q < 2^28).
+struct __align__(16) PrimeDev32 {
+    u32 q;
+    u32 mbar;        // unused by the 32-bit kernels (kept for a common shape)
+    Tw32 ninv;       // N^{-1} mod q and its Shoup companion
+    Tw32 w1ninv;     // Psi[1] * N^{-1} mod q (the last inverse stage, applied to y - x)
+    u32 k;           // bit length of q
+};
+
+// Word-size traits of the pass kernels: the data word, the twiddle pair and
+// the per-prime constants.
+template <class W>
+struct WordTypes;
+template <>
+struct WordTypes<u64> {
+    using Tw = ntt::Tw;
+    using Prime = PrimeDev;
+};
+template <>
+struct WordTypes<u32> {
+    using Tw = Tw32;
+    using Prime = PrimeDev32;
+};
+
 // Arguments of one pass launch (all limbs of one polynomial batch).
-struct PassArgs {
-    u64* data;               // [limbs][N], limb-contiguous
-    const PrimeDev* primes;  // [L]
-    const Tw* tw;            // [L][tw_len] forward table Psi[i] = psi^{brv(i)}
-    const Tw* ota;           // [L][2^P] OT A factors for this pass and direction
-    const Tw* otb;           // [L][P << s0] OT B factors for this pass and direction
+template <class W = u64>
+struct PassArgsT {
+    using TwT = typename WordTypes<W>::Tw;
+    using PrimeT = typename WordTypes<W>::Prime;
+    W* data;                 // [limbs][N], limb-contiguous
+    const PrimeT* primes;    // [L]
+    const TwT* tw;           // [L][tw_len] forward table Psi[i] = psi^{brv(i)}
+    const TwT* ota;          // [L][2^P] OT A factors for this pass and direction
+    const TwT* otb;          // [L][P << s0] OT B factors for this pass and direction
     const u32* prime_map;    // optional [limbs] -> prime index (else limb % L)
     u32 tw_len;              // entries per prime in tw
     u32 n;                   // log2 N
@@ -29,5 +56,6 @@ struct PassArgs {
     u32 L;                   // primes per polynomial
     u32 limb_offset;         // first limb of this launch
 };
+using PassArgs = PassArgsT<u64>;
 
 }  // namespace ntt

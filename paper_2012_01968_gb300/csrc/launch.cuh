@@ -12,12 +12,24 @@ namespace ntt {
 
 constexpr u32 kMaxGridY = 65535;
 
+// What one pass launch needs, for either word size.
+template <class W>
+struct PassLaunch {
+    W* data;
+    u32 limbs, L, n;
+    const typename WordTypes<W>::Prime* primes;
+    const typename WordTypes<W>::Tw* tw;
+    u32 tw_len;
+    cudaStream_t stream;
+};
+
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
-          bool TW_SMEM>
-cudaError_t launch_pass(const LaunchCtx& c, u32 s0, const Tw* ota, const Tw* otb)
+          bool TW_SMEM, class W>
+cudaError_t launch_pass_w(const PassLaunch<W>& c, u32 s0, const typename WordTypes<W>::Tw* ota,
+                          const typename WordTypes<W>::Tw* otb)
 {
-    auto kern = ntt_pass_kernel<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM>;
-    constexpr size_t smem = pass_smem_bytes<P, LOGC, KMAX, TW_SMEM, OTS>();
+    auto kern = ntt_pass_kernel<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, W>;
+    constexpr size_t smem = pass_smem_bytes<P, LOGC, KMAX, TW_SMEM, OTS, W>();
     constexpr int T = pass_threads(P, LOGC, KMAX);
     if (smem > 48 * 1024) {
         static std::once_flag once;
@@ -28,7 +40,7 @@ cudaError_t launch_pass(const LaunchCtx& c, u32 s0, const Tw* ota, const Tw* otb
         if (attr_err != cudaSuccess) return attr_err;
     }
     const u32 tiles = (1u << c.n) >> (P + LOGC);
-    PassArgs a;
+    PassArgsT<W> a;
     a.data = c.data;
     a.primes = c.primes;
     a.tw = c.tw;
@@ -46,6 +58,14 @@ cudaError_t launch_pass(const LaunchCtx& c, u32 s0, const Tw* ota, const Tw* otb
         kern<<<dim3(tiles, cnt), T, smem, c.stream>>>(a);
     }
     return cudaGetLastError();
+}
+
+template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
+          bool TW_SMEM>
+cudaError_t launch_pass(const LaunchCtx& c, u32 s0, const Tw* ota, const Tw* otb)
+{
+    const PassLaunch<u64> pl{c.data, c.limbs, c.L, c.n, c.primes, c.tw, c.tw_len, c.stream};
+    return launch_pass_w<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, u64>(pl, s0, ota, otb);
 }
 
 // Single pass over all n stages (n <= 12): one CTA per limb.
@@ -75,6 +95,37 @@ cudaError_t launch_two_pass_ots(const LaunchCtx& c, bool fwd)
     constexpr int X1 = gs_range_after(1, P2);
     return launch_pass<P1, LOGC_C, KMAX_C, false, false, X1, true, true, 0, true>(c, 0, nullptr, nullptr);
 }
+
+// 32-bit words (table twiddles, one launch per pass).  The column pass takes
+// 32 columns per tile so that each row segment is a full 128-byte line.
+template <int N_LOG>
+cudaError_t launch_single_w32(const PassLaunch<u32>& c, bool fwd)
+{
+    if (fwd)
+        return launch_pass_w<N_LOG, 0, KMAX_ALL, true, true, 1, true, true, 0, false, u32>(c, 0, nullptr, nullptr);
+    return launch_pass_w<N_LOG, 0, KMAX_ALL, true, false, 1, true, true, 0, false, u32>(c, 0, nullptr, nullptr);
+}
+
+template <int P1, int P2, int LOGC_R, int KMAX_R>
+cudaError_t launch_two_pass_w32(const PassLaunch<u32>& c, bool fwd)
+{
+    constexpr int LOGC_C = 5;
+    cudaError_t e;
+    if (fwd) {
+        e = launch_pass_w<P1, LOGC_C, KMAX_R, false, true, 1, false, true, 0, true, u32>(c, 0, nullptr, nullptr);
+        if (e != cudaSuccess) return e;
+        constexpr int X2 = ct_range_after(1, P1);
+        return launch_pass_w<P2, LOGC_R, KMAX_R, true, true, X2, true, false, 0, false, u32>(c, P1, nullptr, nullptr);
+    }
+    e = launch_pass_w<P2, LOGC_R, KMAX_R, true, false, 1, false, false, 0, false, u32>(c, P1, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    constexpr int X1 = gs_range_after(1, P2);
+    return launch_pass_w<P1, LOGC_C, KMAX_R, false, false, X1, true, true, 0, true, u32>(c, 0, nullptr, nullptr);
+}
+
+// 32-bit launchers by size (k_w32_single.cu: n <= 12, k_w32_two.cu: 13 <= n <= 17)
+cudaError_t launch_w32_single(const PassLaunch<u32>& c, bool fwd);
+cudaError_t launch_w32_two(const PassLaunch<u32>& c, bool fwd);
 
 // host helpers for the fused launch (fused_host.cu)
 u32 fused_window_limbs(size_t limb_bytes);

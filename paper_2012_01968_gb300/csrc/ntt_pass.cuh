@@ -53,6 +53,16 @@ __host__ __device__ constexpr int gs_range_max(int X, int stages)
 // strided per-thread accesses of every round conflict-free.
 __device__ __forceinline__ u32 swz(u32 w) { return w ^ (((w >> 4) & 7u) << 1); }
 
+// The same for 32-bit words: pair index XOR (line index mod 8), line = 32
+// words (128 bytes), so that a warp reading word pairs at a stride of 16 words
+// still covers every bank pair once per 16 lanes.
+template <class W>
+__device__ __forceinline__ u32 swzw(u32 w)
+{
+    if constexpr (sizeof(W) == 8) return swz(w);
+    else return w ^ (((w >> 5) & 7u) << 1);
+}
+
 // Twiddle slots.  Within stage s the butterfly with index j = (u << sl) |
 // (hi << k) | pre (u: sub-transform bits, hi: bits of the round digit fixed
 // per thread, pre: the butterfly's group inside the thread's radix-2^KR
@@ -68,21 +78,53 @@ __host__ __device__ constexpr unsigned tw_slot(unsigned j, int sl, int K0, int k
 
 // Everything one item (one thread's 2^KR elements of one sub-transform in one
 // round) needs besides its data.
-struct ItemCtx {
-    const Tw* tw;        // twiddle table base for this prime (smem or global)
-    const Tw* ota;       // OT A factors for this prime (smem)
-    const Tw* otb;       // OT B factors for this prime (global)
-    u64 q, q4;
+template <class W = u64>
+struct ItemCtxT {
+    using TwT = typename WordTypes<W>::Tw;
+    const TwT* tw;       // twiddle table base for this prime (smem or global)
+    const TwT* ota;      // OT A factors for this prime (smem)
+    const TwT* otb;      // OT B factors for this prime (global)
+    W q, q4;
     u32 mbar;
     u32 u;               // upper index bits (which 2^{n-s0} block)
     u32 hi;              // bits of v above the round digit
     u32 s0;              // first stage of the pass
-    Tw ninv, w1ninv;
+    TwT ninv, w1ninv;
+};
+using ItemCtx = ItemCtxT<u64>;
+
+// two consecutive words as one vector (16 bytes for 64-bit words, 8 for 32-bit)
+__device__ __forceinline__ void load_pair(const u64* p, u64& a, u64& b)
+{
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void load_pair(const u32* p, u32& a, u32& b)
+{
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void store_pair(u64* p, u64 a, u64 b)
+{
+    *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a, b);
+}
+__device__ __forceinline__ void store_pair(u32* p, u32 a, u32 b) { *reinterpret_cast<uint2*>(p) = make_uint2(a, b); }
+template <class W>
+struct PairVec;
+template <>
+struct PairVec<u64> {
+    using T = ulonglong2;
+};
+template <>
+struct PairVec<u32> {
+    using T = uint2;
 };
 
 // ---------------------------------------------------------------- forward --
-template <int P, int KR, int K0, int k, int X, int OTS, bool TWG, int E>
-__device__ __forceinline__ void fwd_stages(u64 (&x)[E], const ItemCtx& c)
+template <int P, int KR, int K0, int k, int X, int OTS, bool TWG, int E, class W>
+__device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
 {
     if constexpr (k < KR) {
         constexpr int half = E >> (k + 1);
@@ -92,14 +134,14 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[E], const ItemCtx& c)
         for (int pre = 0; pre < (1 << k); ++pre) {
             const u32 jlo = ((u32)pre << K0) | c.hi;      // twiddle slot, see tw_slot
             if constexpr (ot) {
-                const Tw f1 = c.otb[((u32)sl << c.s0) + c.u];
-                const Tw f2 = c.ota[(1u << sl) + jlo];
+                const auto f1 = c.otb[((u32)sl << c.s0) + c.u];
+                const auto f2 = c.ota[(1u << sl) + jlo];
 #pragma unroll
                 for (int i = 0; i < half; ++i)
                     ct_bfly_ot<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q, c.q4, c.mbar);
             } else {
                 const u32 idx = TWG ? (1u << (c.s0 + sl)) + (c.u << sl) + jlo : (1u << sl) + jlo;
-                const Tw t = c.tw[idx];
+                const auto t = c.tw[idx];
 #pragma unroll
                 for (int i = 0; i < half; ++i)
                     ct_bfly<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.q4, c.mbar);
@@ -112,8 +154,8 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[E], const ItemCtx& c)
 // ---------------------------------------------------------------- inverse --
 // Stages run from KR-1 down to 0.  HAS_S0: this round holds global stage 0
 // (K0 == 0 and s0 == 0), whose butterfly also applies N^{-1}.
-template <int P, int KR, int K0, int k, int X, int OTS, bool HAS_S0, bool TWG, int E>
-__device__ __forceinline__ void inv_stages(u64 (&x)[E], const ItemCtx& c)
+template <int P, int KR, int K0, int k, int X, int OTS, bool HAS_S0, bool TWG, int E, class W>
+__device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c)
 {
     if constexpr (k >= 0) {
         constexpr int half = E >> (k + 1);
@@ -130,8 +172,8 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[E], const ItemCtx& c)
             for (int pre = 0; pre < (1 << k); ++pre) {
                 const u32 jlo = ((u32)pre << K0) | c.hi;  // twiddle slot, see tw_slot
                 if constexpr (ot) {
-                    const Tw f1 = c.otb[((u32)sl << c.s0) + c.u];
-                    const Tw f2 = c.ota[(1u << sl) + jlo];
+                    const auto f1 = c.otb[((u32)sl << c.s0) + c.u];
+                    const auto f2 = c.ota[(1u << sl) + jlo];
 #pragma unroll
                     for (int i = 0; i < half; ++i)
                         gs_bfly_ot<X, false>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q, c.mbar);
@@ -139,7 +181,7 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[E], const ItemCtx& c)
                     // Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j]
                     const u32 j = TWG ? (c.u << sl) + jlo : jlo;
                     const u32 idx = TWG ? (2u << (c.s0 + sl)) - 1u - j : (2u << sl) - 1u - j;
-                    const Tw t = c.tw[idx];
+                    const auto t = c.tw[idx];
 #pragma unroll
                     for (int i = 0; i < half; ++i)
                         gs_bfly<X, true>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.mbar);
@@ -154,8 +196,8 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[E], const ItemCtx& c)
 // One round: every item of the tile reads its 2^KR elements from shared
 // memory, runs KR stages in registers and writes them back.
 template <int P, int LOGC, int KMAX, int r, bool ROWS, bool FWD, int XR, int OTS,
-          bool HAS_S0, int CANON, bool TWG, int NT>
-__device__ __forceinline__ void run_round(u64* sm, ItemCtx c, const u32 u_base, const u32 tid)
+          bool HAS_S0, int CANON, bool TWG, int NT, class W>
+__device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base, const u32 tid)
 {
     constexpr int KR = rsize(P, KMAX, r);
     constexpr int K0 = rstart(P, KMAX, r);
@@ -179,21 +221,19 @@ __device__ __forceinline__ void run_round(u64* sm, ItemCtx c, const u32 u_base, 
         c.hi = hi;
         if constexpr (ROWS) c.u = u_base + cc;
         const u32 vbase = (hi << (P - K0)) | lo;
-        u64 x[E];
+        W x[E];
         if constexpr (PAIRS) {
 #pragma unroll
             for (int i = 0; i < E; i += 2) {
                 const u32 w = cc * R + vbase + (u32)i;
-                const ulonglong2 p = *reinterpret_cast<const ulonglong2*>(sm + swz(w));
-                x[i] = p.x;
-                x[i + 1] = p.y;
+                load_pair(sm + swzw<W>(w), x[i], x[i + 1]);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const u32 v = vbase | ((u32)i << NLO);
                 const u32 w = ROWS ? cc * R + v : v * C + cc;
-                x[i] = sm[swz(w)];
+                x[i] = sm[swzw<W>(w)];
             }
         }
         if constexpr (FWD)
@@ -208,14 +248,14 @@ __device__ __forceinline__ void run_round(u64* sm, ItemCtx c, const u32 u_base, 
 #pragma unroll
             for (int i = 0; i < E; i += 2) {
                 const u32 w = cc * R + vbase + (u32)i;
-                *reinterpret_cast<ulonglong2*>(sm + swz(w)) = make_ulonglong2(x[i], x[i + 1]);
+                store_pair(sm + swzw<W>(w), x[i], x[i + 1]);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const u32 v = vbase | ((u32)i << NLO);
                 const u32 w = ROWS ? cc * R + v : v * C + cc;
-                sm[swz(w)] = x[i];
+                sm[swzw<W>(w)] = x[i];
             }
         }
     }
@@ -249,15 +289,17 @@ __device__ __forceinline__ void round_barrier()
 // `mid` runs (in every thread) after the first round executed, before the
 // barrier that follows it.
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
-          bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false>
-__device__ __forceinline__ void compute_tile(u64* sm, const PrimeDev& pr, const Tw* tw, const Tw* ota,
-                                             const Tw* otb, const u32 u_base, const u32 s0, const u32 tid,
-                                             Hook mid = Hook())
+          bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false, class W = u64>
+__device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>::Prime& pr,
+                                             const typename WordTypes<W>::Tw* tw,
+                                             const typename WordTypes<W>::Tw* ota,
+                                             const typename WordTypes<W>::Tw* otb, const u32 u_base, const u32 s0,
+                                             const u32 tid, Hook mid = Hook())
 {
     constexpr int NR = nrounds(P, KMAX);
     static_assert(NR <= 4, "at most four rounds per pass");
     static_assert(FWD ? ct_range_max(XIN, P) <= 16 : gs_range_max(XIN, P) <= 8, "lazy range");
-    ItemCtx c;
+    ItemCtxT<W> c;
     c.q = pr.q;
     c.q4 = pr.q << 2;
     c.mbar = pr.mbar;
@@ -329,31 +371,63 @@ __device__ __forceinline__ void compute_tile(u64* sm, const PrimeDev& pr, const 
 //   OTS                 : the last OTS stages of the pass use on-the-fly twiddles
 //   TW_SMEM             : stage the pass's twiddles Psi[1 .. 2^P) in shared
 //                         memory (only when s0 == 0, where they are all it needs)
-template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0,
-          int OTS, bool TW_SMEM>
-__global__ void __launch_bounds__(pass_threads(P, LOGC, KMAX))
-ntt_pass_kernel(const PassArgs a)
+// 16-byte global <-> shared moves of a tile: one vector holds 16 / sizeof(W)
+// words and lands in shared memory as word pairs (the swizzle keeps pairs).
+template <class W>
+__device__ __forceinline__ void vec_to_smem(W* sm, u32 w, const uint4 v)
 {
+    if constexpr (sizeof(W) == 8) {
+        store_pair(sm + swz(w), ((u64)v.y << 32) | v.x, ((u64)v.w << 32) | v.z);
+    } else {
+        store_pair(sm + swzw<W>(w), (W)v.x, (W)v.y);
+        store_pair(sm + swzw<W>(w + 2), (W)v.z, (W)v.w);
+    }
+}
+template <class W>
+__device__ __forceinline__ uint4 vec_from_smem(const W* sm, u32 w)
+{
+    W a, b, c, d;
+    if constexpr (sizeof(W) == 8) {
+        load_pair(sm + swz(w), a, b);
+        return make_uint4((u32)a, (u32)(a >> 32), (u32)b, (u32)(b >> 32));
+    } else {
+        load_pair(sm + swzw<W>(w), a, b);
+        load_pair(sm + swzw<W>(w + 2), c, d);
+        return make_uint4(a, b, c, d);
+    }
+}
+
+template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0,
+          int OTS, bool TW_SMEM, class W = u64>
+__global__ void __launch_bounds__(pass_threads(P, LOGC, KMAX))
+ntt_pass_kernel(const PassArgsT<W> a)
+{
+    using TwT = typename WordTypes<W>::Tw;
+    using PrimeT = typename WordTypes<W>::Prime;
     constexpr int R = 1 << P, C = 1 << LOGC;
     constexpr int T = pass_threads(P, LOGC, KMAX);
     constexpr int NR = nrounds(P, KMAX);
     constexpr int TILE = R * C;
+    // words per 16-byte vector; tiles below 16 bytes move word by word
+    constexpr int VW = TILE * (int)sizeof(W) >= 16 ? 16 / (int)sizeof(W) : 1;
     static_assert(NR <= 4, "at most four rounds per pass");
     static_assert(FWD ? ct_range_max(XIN, P) <= 16 : gs_range_max(XIN, P) <= 8, "lazy range");
     static_assert(!TW_SMEM || HAS_S0, "twiddle staging needs s0 == 0");
+    static_assert(ROWS || C % VW == 0, "column tiles hold whole vectors");
 
-    extern __shared__ __align__(16) u64 smem[];
-    u64* sm = smem;
-    Tw* sm_tw = reinterpret_cast<Tw*>(smem + TILE);               // 2^P entries
-    Tw* sm_ota = sm_tw + (TW_SMEM ? R : 0);                        // 2^P entries
+    extern __shared__ __align__(16) u64 smem_pass[];
+    W* sm = reinterpret_cast<W*>(smem_pass);
+    // the tile is a multiple of 16 bytes or is at most 8 bytes; round up for the tables
+    TwT* sm_tw = reinterpret_cast<TwT*>(smem_pass + (TILE * sizeof(W) + 15) / 16 * 2);   // 2^P entries
+    TwT* sm_ota = sm_tw + (TW_SMEM ? R : 0);                                            // 2^P entries
 
     const u32 tid = threadIdx.x;
     const u32 tile = blockIdx.x;
     const u32 limb = blockIdx.y + a.limb_offset;
     const u32 pi = a.prime_map ? a.prime_map[limb] : limb % a.L;
-    const PrimeDev pr = a.primes[pi];
+    const PrimeT pr = a.primes[pi];
     const u32 nb = a.n - a.s0;                       // bits of u's block size
-    u64* base = a.data + (size_t)limb * ((size_t)1 << a.n);
+    W* base = a.data + (size_t)limb * ((size_t)1 << a.n);
 
     // tile origin
     u32 u_base, l0;
@@ -367,28 +441,27 @@ ntt_pass_kernel(const PassArgs a)
     }
 
     if constexpr (TW_SMEM) {
-        const Tw* g = a.tw + (size_t)pi * a.tw_len;
+        const TwT* g = a.tw + (size_t)pi * a.tw_len;
         for (u32 i = tid; i < (u32)R; i += T) sm_tw[i] = g[i];
     }
     if constexpr (OTS > 0) {
-        const Tw* g = a.ota + (size_t)pi * R;
+        const TwT* g = a.ota + (size_t)pi * R;
         for (u32 i = tid; i < (u32)R; i += T) sm_ota[i] = g[i];
     }
 
-    // global -> shared (16-byte vectors)
-    if constexpr (ROWS) {
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(base + ((size_t)u_base << P));
-        for (u32 i = tid; i < TILE / 2; i += T) {
-            const ulonglong2 v = src[i];
-            *reinterpret_cast<ulonglong2*>(sm + swz(2 * i)) = v;
-        }
+    // global -> shared
+    if constexpr (VW == 1) {
+        const W* src = base + ((size_t)u_base << P);
+        for (u32 i = tid; i < (u32)TILE; i += T) sm[swzw<W>(i)] = src[i];
+    } else if constexpr (ROWS) {
+        const uint4* src = reinterpret_cast<const uint4*>(base + ((size_t)u_base << P));
+        for (u32 i = tid; i < TILE / VW; i += T) vec_to_smem(sm, VW * i, src[i]);
     } else {
-        constexpr int VPR = C / 2;                    // vectors per row
-        const u64* blk = base + ((size_t)u_base << nb) + l0;
-        for (u32 i = tid; i < TILE / 2; i += T) {
+        constexpr int VPR = C / VW;                   // vectors per row
+        const W* blk = base + ((size_t)u_base << nb) + l0;
+        for (u32 i = tid; i < TILE / VW; i += T) {
             const u32 v = i / VPR, cv = i % VPR;
-            const ulonglong2 val = *reinterpret_cast<const ulonglong2*>(blk + ((size_t)v << a.b) + 2 * cv);
-            *reinterpret_cast<ulonglong2*>(sm + swz(v * C + 2 * cv)) = val;
+            vec_to_smem(sm, v * C + VW * cv, *reinterpret_cast<const uint4*>(blk + ((size_t)v << a.b) + VW * cv));
         }
     }
     __syncthreads();
@@ -399,26 +472,28 @@ ntt_pass_kernel(const PassArgs a)
     __syncthreads();
 
     // shared -> global
-    if constexpr (ROWS) {
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(base + ((size_t)u_base << P));
-        for (u32 i = tid; i < TILE / 2; i += T)
-            dst[i] = *reinterpret_cast<const ulonglong2*>(sm + swz(2 * i));
+    if constexpr (VW == 1) {
+        W* dst = base + ((size_t)u_base << P);
+        for (u32 i = tid; i < (u32)TILE; i += T) dst[i] = sm[swzw<W>(i)];
+    } else if constexpr (ROWS) {
+        uint4* dst = reinterpret_cast<uint4*>(base + ((size_t)u_base << P));
+        for (u32 i = tid; i < TILE / VW; i += T) dst[i] = vec_from_smem(sm, VW * i);
     } else {
-        constexpr int VPR = C / 2;
-        u64* blk = base + ((size_t)u_base << nb) + l0;
-        for (u32 i = tid; i < TILE / 2; i += T) {
+        constexpr int VPR = C / VW;
+        W* blk = base + ((size_t)u_base << nb) + l0;
+        for (u32 i = tid; i < TILE / VW; i += T) {
             const u32 v = i / VPR, cv = i % VPR;
-            *reinterpret_cast<ulonglong2*>(blk + ((size_t)v << a.b) + 2 * cv) =
-                *reinterpret_cast<const ulonglong2*>(sm + swz(v * C + 2 * cv));
+            *reinterpret_cast<uint4*>(blk + ((size_t)v << a.b) + VW * cv) = vec_from_smem(sm, v * C + VW * cv);
         }
     }
 }
 
-template <int P, int LOGC, int KMAX, bool TW_SMEM, int OTS>
+template <int P, int LOGC, int KMAX, bool TW_SMEM, int OTS, class W = u64>
 __host__ __device__ constexpr size_t pass_smem_bytes()
 {
-    return (size_t)(1 << (P + LOGC)) * 8 + (TW_SMEM ? (size_t)(1 << P) * 16 : 0) +
-           (OTS > 0 ? (size_t)(1 << P) * 16 : 0);
+    constexpr size_t tw = sizeof(typename WordTypes<W>::Tw);
+    return ((size_t)(1 << (P + LOGC)) * sizeof(W) + 15) / 16 * 16 + (TW_SMEM ? (size_t)(1 << P) * tw : 0) +
+           (OTS > 0 ? (size_t)(1 << P) * tw : 0);
 }
 
 }  // namespace ntt

@@ -1,0 +1,149 @@
+// 32-bit word plans (Sec. IV, "32b vs. 64b word size"): primes q < 2^28,
+// residues in 32-bit words, table twiddles, one launch per pass.
+//
+// Tables per prime q, in the slot order of the 64-bit kernels (the pass split
+// and the per-thread radix are the same):
+//   tw[i] = (Psi[i], floor(Psi[i] 2^32 / q)),  Psi[i] = psi^{brv(i)},  i < N.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "launch.cuh"
+#include "numtheory.h"
+
+namespace nt = ntt::nt;
+using ntt::PrimeDev32;
+using ntt::Tw32;
+
+extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
+
+struct ntt_plan32 {
+    uint32_t N = 0, n = 0, L = 0, p1 = 0;
+    int device = 0;
+    std::vector<uint32_t> primes, psis;
+    PrimeDev32* d_primes = nullptr;
+    Tw32* d_tw = nullptr;
+};
+
+namespace {
+
+Tw32 make_tw32(uint64_t w, uint64_t q) { return Tw32{(uint32_t)w, (uint32_t)((w << 32) / q)}; }
+
+void free_plan32(ntt_plan32* p)
+{
+    if (!p) return;
+    cudaFree(p->d_primes);
+    cudaFree(p->d_tw);
+    delete p;
+}
+
+ntt_status to_status32(cudaError_t e)
+{
+    if (e == cudaSuccess) return NTT_OK;
+    ntt_internal_set_cuda_error(e);
+    return e == cudaErrorMemoryAllocation ? NTT_ERR_OOM : NTT_ERR_CUDA;
+}
+
+ntt_status transform32(const ntt_plan32* p, uint32_t* data, uint32_t batch, void* stream, bool fwd)
+{
+    if (!p || !data || batch == 0) return NTT_ERR_INVALID_ARG;
+    if (((uintptr_t)data & 15u) != 0) return NTT_ERR_MISALIGNED;
+    const uint64_t limbs = (uint64_t)batch * p->L;
+    if (limbs > 0xFFFFFFFFull) return NTT_ERR_INVALID_ARG;
+    const ntt::PassLaunch<ntt::u32> c{data, (uint32_t)limbs, p->L, p->n, p->d_primes, p->d_tw, p->N,
+                                      (cudaStream_t)stream};
+    const cudaError_t e = p->n <= (uint32_t)ntt::SINGLE_PASS_MAX ? ntt::launch_w32_single(c, fwd)
+                                                                 : ntt::launch_w32_two(c, fwd);
+    return to_status32(e);
+}
+
+}  // namespace
+
+extern "C" ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L)
+{
+    if (!out || !primes || L == 0 || L > 4096) return NTT_ERR_INVALID_ARG;
+    if (N < 2 || N > (1u << 17) || (N & (N - 1))) return NTT_ERR_INVALID_ARG;
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint64_t q = primes[l];
+        if (q >= (1ull << 28)) return NTT_ERR_BAD_PRIME;       // 16 q must fit a word
+        if ((q - 1) % (2ull * N) != 0 || q < 2) return NTT_ERR_BAD_PRIME;
+        if (!nt::is_prime(q)) return NTT_ERR_BAD_PRIME;
+    }
+    ntt_plan32* p = new (std::nothrow) ntt_plan32();
+    if (!p) return NTT_ERR_OOM;
+    p->N = N;
+    p->n = (uint32_t)__builtin_ctz(N);
+    p->L = L;
+    p->p1 = (uint32_t)ntt::split_p1((int)p->n);
+    cudaError_t ce = cudaGetDevice(&p->device);
+    if (ce != cudaSuccess) {
+        free_plan32(p);
+        return to_status32(ce);
+    }
+    std::vector<Tw32> tw;
+    std::vector<PrimeDev32> pd;
+    try {
+        p->primes.assign(primes, primes + L);
+        p->psis.resize(L);
+        tw.resize((size_t)L * N);
+        pd.resize(L);
+    } catch (...) {
+        free_plan32(p);
+        return NTT_ERR_OOM;
+    }
+    const uint32_t n = p->n;
+    std::vector<uint64_t> pw(N);
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint64_t q = primes[l];
+        const uint64_t psi = nt::powmod(nt::smallest_generator(q), (q - 1) / (2ull * N), q);
+        p->psis[l] = (uint32_t)psi;
+        pw[0] = 1;
+        for (uint32_t e = 1; e < N; ++e) pw[e] = pw[e - 1] * psi % q;     // q < 2^28: no overflow
+        Tw32* t = tw.data() + (size_t)l * N;
+        t[0] = make_tw32(1, q);
+        for (uint32_t s = 0; s < n; ++s) {
+            const ntt::StageSlot g = ntt::stage_slot_params((int)n, (int)p->p1, (int)s);
+            for (uint32_t j = 0; j < (1u << s); ++j)
+                t[(1u << s) + ntt::tw_slot(j, g.sl, g.K0, g.k)] = make_tw32(pw[nt::brv((1u << s) + j, n)], q);
+        }
+        PrimeDev32& d = pd[l];
+        d.q = (uint32_t)q;
+        d.mbar = 0;
+        d.k = (uint32_t)nt::bitlen(q);
+        const uint64_t ninv = nt::powmod(N % q, q - 2, q);
+        d.ninv = make_tw32(ninv, q);
+        d.w1ninv = make_tw32(pw[nt::brv(1, n)] * ninv % q, q);     // Psi[1] N^{-1}
+    }
+    ce = cudaMalloc(&p->d_primes, pd.size() * sizeof(PrimeDev32));
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_primes, pd.data(), pd.size() * sizeof(PrimeDev32), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_tw, tw.size() * sizeof(Tw32));
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(Tw32), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        free_plan32(p);
+        cudaGetLastError();
+        return to_status32(ce);
+    }
+    *out = p;
+    return NTT_OK;
+}
+
+extern "C" void ntt_plan32_destroy(ntt_plan32* plan) { free_plan32(plan); }
+
+extern "C" ntt_status ntt_forward32(const ntt_plan32* p, uint32_t* data, uint32_t batch, void* stream)
+{
+    return transform32(p, data, batch, stream, true);
+}
+
+extern "C" ntt_status ntt_inverse32(const ntt_plan32* p, uint32_t* data, uint32_t batch, void* stream)
+{
+    return transform32(p, data, batch, stream, false);
+}
+
+extern "C" ntt_status ntt_plan32_psi(const ntt_plan32* p, uint32_t l, uint32_t* psi)
+{
+    if (!p || !psi || l >= p->L) return NTT_ERR_INVALID_ARG;
+    *psi = p->psis[l];
+    return NTT_OK;
+}

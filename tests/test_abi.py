@@ -65,6 +65,31 @@ def test_plan_create_rejects(lib, N, primes, kw, want):
     assert h == 0
 
 
+SMALL = I.small_ntt_primes(1 << 12, 2, start=1 << 27)      # 28-bit primes = 1 mod 2^13
+
+
+@pytest.mark.parametrize("N,primes,want", [
+    (0, SMALL[:1], G.NTT_ERR_INVALID_ARG),
+    (3, SMALL[:1], G.NTT_ERR_INVALID_ARG),
+    (1 << 18, SMALL[:1], G.NTT_ERR_INVALID_ARG),
+    (1 << 12, [], G.NTT_ERR_INVALID_ARG),
+    (1 << 12, [1 << 28 | 1], G.NTT_ERR_BAD_PRIME),                       # not below 2^28
+    (1 << 12, BIG[:1], G.NTT_ERR_BAD_PRIME),                             # a 60-bit prime
+    (1 << 12, [3 * 8192 + 1], G.NTT_ERR_BAD_PRIME),                      # 1 mod 2N, composite (7 * 3511)
+    (1 << 13, SMALL[1:2], G.NTT_ERR_BAD_PRIME),                          # 8193 mod 2^14
+    (2, [2], G.NTT_ERR_BAD_PRIME),                                       # 2 is not 1 mod 4
+])
+def test_plan32_create_rejects(lib, N, primes, want):
+    st, h = G.ntt_plan32_create_status(N, primes)
+    assert st == want
+    assert h == 0
+
+
+def test_plan32_primes_are_28_bit():
+    assert all((1 << 27) <= q < (1 << 28) and q % (1 << 13) == 1 and I.is_prime(q) for q in SMALL)
+    assert SMALL[1] % (1 << 14) != 1
+
+
 def test_null_arguments_rejected(lib):
     assert lib.ntt_forward(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_inverse(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
@@ -73,6 +98,11 @@ def test_null_arguments_rejected(lib):
     assert lib.ntt_plan_query(None, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_plan_create(None, 16, None, 1, None) == G.NTT_ERR_INVALID_ARG
     lib.ntt_plan_destroy(None)
+    assert lib.ntt_forward32(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_inverse32(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_plan32_psi(None, 0, None) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_plan32_create(None, 16, None, 1) == G.NTT_ERR_INVALID_ARG
+    lib.ntt_plan32_destroy(None)
 
 
 def test_no_oracle_in_product_path():
