@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-peak-measure", action="store_true",
                     help="skip the live butterfly-rate measurement (for profiling runs)")
     ap.add_argument("--no-ablation", action="store_true", help="skip the N sweep of kernel organisations")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="plans with the fixed default options instead of the autotuner's choice")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--launch-steps", type=int, default=500,
                     help="steps of the single-stream pass that times each launch")
@@ -258,6 +260,25 @@ def run_reference(args, metric, unit, w):
     print(json.dumps(line), flush=True)
 
 
+KERNEL_NAMES = {0: "auto", 1: "fused", 2: "per_pass", 3: "radix2"}
+
+
+def opts_summary(o):
+    return {"kernel": KERNEL_NAMES[int(o.kernel)],
+            "twiddle": "table" if o.twiddle_mode == 1 else f"ot{o.ot_stages}" if o.twiddle_mode == 2 else "auto",
+            "geometry": int(o.geometry)}
+
+
+def autotune(G, N, primes, batch, reps=10):
+    """The library's autotuner for (N, primes, batch): the chosen options and
+    a short report (the five fastest candidates, forward + inverse µs)."""
+    best, entries = G.ntt_autotune(N, primes, batch, reps=reps)
+    ranked = sorted((e for e in entries if e.status == 0), key=lambda e: e.forward_us + e.inverse_us)
+    rep = {"chosen": opts_summary(best), "candidates": len(entries),
+           "fastest_us": [dict(opts_summary(e.opts), us=round(e.forward_us + e.inverse_us, 2)) for e in ranked[:5]]}
+    return best, rep
+
+
 def _ok(G, st, what):
     """Raise on a failed library call (the timing loops call the C ABI directly)."""
     if st:
@@ -299,13 +320,15 @@ def per_limb_c2(G, torch, w, host, steps):
             p.close()
 
 
-def batched_c4(G, torch, reps):
+def batched_c4(G, torch, reps, tuned=None):
     """The uneven 96-job workload (N in 2^14..2^17, L in [1, 60], mixed
     directions): one ntt_batch_submit, its CUDA-graph replay, and the same
-    jobs as 96 single calls on one stream."""
+    jobs as 96 single calls on one stream.  `tuned` maps log2 N to plan
+    options (the autotuner's); None: the default options."""
     w = I.workload_c4()
     chain = I.chain_2_18_60()
-    plans = {n: G.Plan(1 << n, chain) for n in range(14, 18)}
+    plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain))
+             for n in range(14, 18)}
     lib = G.lib()
     try:
         gen = torch.Generator(device="cuda")
@@ -356,14 +379,15 @@ def batched_c4(G, torch, reps):
             p.close()
 
 
-def serve_c5(G, torch, count, budget_gb=64, ring_gb=80):
+def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None):
     """The serving workload: `count` requests (N in 2^15..2^17, L in [4, 60],
     mixed directions) on device-resident data, admitted by an HBM budget.
     A capacity run (every request submitted at once), then Poisson arrivals at
     50 / 80 / 95% of that capacity; latency = submission to completion."""
     import collections
     chain = I.chain_2_18_60()
-    plans = {n: G.Plan(1 << n, chain) for n in (15, 16, 17)}
+    plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain))
+             for n in (15, 16, 17)}
     word = 8
     ring_words = (ring_gb << 30) // word
     ring = torch.empty(ring_words, dtype=torch.int64, device="cuda")
@@ -466,7 +490,7 @@ def paper_ablation(G, torch, reps=40):
     return out
 
 
-def large_ring_c3(G, torch, reps=50):
+def large_ring_c3(G, torch, reps=50, opts=None):
     """The large ring: N = 2^17, L = 60, one ciphertext (batch 2), forward
     then inverse per step on one stream; and the negacyclic product of two
     polynomials (two forwards in one launch, element-wise product, inverse)."""
@@ -479,7 +503,7 @@ def large_ring_c3(G, torch, reps=50):
     bufs = [src.clone() for _ in range(nbuf)]
     s = torch.cuda.Stream()
     lib = G.lib()
-    with G.Plan(N, primes) as p:
+    with (G.Plan.from_opts(N, primes, opts) if opts is not None else G.Plan(N, primes)) as p:
         def timed(fn, k):
             with torch.cuda.stream(s):
                 for i in range(3):
@@ -684,7 +708,12 @@ def main():
     S = max(1, args.streams)
     # one plan (tables + work area) per stream: steps on different streams are
     # independent polynomials and may overlap on the device
-    plans = [G.Plan(N, primes, *mode, kern) for _ in range(S)]
+    c2_tune = None
+    if not args.no_tune and args.twiddle == "auto" and args.kernel == "auto":
+        best, c2_tune = autotune(G, N, primes, 1, reps=20)
+        plans = [G.Plan.from_opts(N, primes, best) for _ in range(S)]
+    else:
+        plans = [G.Plan(N, primes, *mode, kern) for _ in range(S)]
     plan = plans[0]
     info = plan.info()
     poly_bytes = N * L * 8
@@ -792,12 +821,25 @@ def main():
                "d2h_bytes_per_step": poly_bytes, "steps": E}
 
     per_limb = batched = None
+    chain = I.chain_2_18_60()
+    tuned = {}
+    if ws == 1 and not (args.no_batch_compare and args.no_serve) and not args.no_tune:
+        # the uneven-batch and serving sizes, tuned at 60 limbs x a few polynomials per launch
+        tuned = {n: autotune(G, 1 << n, chain, 6) for n in range(14, 18)}
     if ws == 1 and not args.no_batch_compare:
         per_limb = per_limb_c2(G, torch, w, host, 100)
         batched = batched_c4(G, torch, 10)
+        if tuned:
+            batched["autotuned"] = batched_c4(G, torch, 10, {n: t[0] for n, t in tuned.items()})
+            batched["autotune"] = {f"N=2^{n}": t[1] for n, t in tuned.items()}
     large = modes = c1 = words = None
     if ws == 1 and not args.no_batch_compare:
+        w3 = I.workload_c3()
         large = large_ring_c3(G, torch)
+        if not args.no_tune:
+            o3, r3 = autotune(G, w3.N, w3.primes, 2)
+            large["autotuned"] = large_ring_c3(G, torch, opts=o3)
+            large["autotune"] = r3
         modes = twiddle_modes_c2(G, torch, w, bufs, nbuf)
         c1 = single_limb_c1(G, torch)
         words = word_sizes(G, torch)
@@ -807,6 +849,9 @@ def main():
     served = None
     if ws == 1 and not args.no_serve:
         served = serve_c5(G, torch, args.serve_requests)
+        if tuned:
+            served["autotuned"] = serve_c5(G, torch, args.serve_requests,
+                                           tuned={n: t[0] for n, t in tuned.items()})
 
     if rank != 0:
         if dist is not None:
@@ -816,6 +861,10 @@ def main():
     if ws == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_time(primes, N, 10.0)
         cpu = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
+    # the committed DRAM counters are for the fused kernel with OT1 in geometry 0
+    profiled = (info.kernel == G.NTT_KERNEL_FUSED and info.twiddle_mode == G.NTT_TWIDDLE_OT
+                and info.ot_stages == 1 and info.geometry == 0)
+    traffic = profile_traffic() if profiled else None
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -824,7 +873,7 @@ def main():
         "hbm_roofline_frac_step": frac_step,
         "roofline": {"bound": "alu", "achieved": bfly_achieved, "peak": alu_peak_gbfly(),
                      "unit": "G butterfly/s", "frac": bfly_achieved / alu_peak_gbfly(),
-                     "traffic": profile_traffic(),
+                     "traffic": traffic,
                      "kernel": f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})",
                      "units_per_launch": f"{bfly_per_launch} butterflies (45 limbs x (N/2) log2 N)",
                      "avg_launch_us": dom_ms * 1e3,
@@ -834,7 +883,7 @@ def main():
                      "peak_measured_source": "ntt_measure_butterfly_rate: register-only butterfly loop, live",
                      "timed_region_frac": bfly_per_launch * 2 * K / (total_ms / 1e3) / 1e9 / alu_peak_gbfly()},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profile_traffic(),
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})",
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
                      "launch_timing": f"CUDA events around each of {Kp} forward and inverse launches on one stream",
@@ -844,7 +893,10 @@ def main():
                              "single_stream_per_transform": single_ms * 1e3 / 2},
         "plan": {"twiddle_mode": int(info.twiddle_mode), "ot_stages": int(info.ot_stages),
                  "passes": int(info.passes), "pass1_log2": int(info.pass1_log2),
-                 "kernel": "fused" if info.kernel == G.NTT_KERNEL_FUSED else "per_pass"},
+                 "row_tile_log2": int(info.row_tile_log2), "geometry": int(info.geometry),
+                 "kernel": KERNEL_NAMES[int(info.kernel)],
+                 "chosen_by": "ntt_autotune" if c2_tune else "fixed options"},
+        "autotune_c2": c2_tune,
         "e2e": e2e,
         "per_limb_path": per_limb,
         "batched_uneven_c4": batched,

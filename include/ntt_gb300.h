@@ -85,11 +85,23 @@ enum {
     NTT_KERNEL_RADIX2 = 3
 };
 
+/* Pass geometries of the two-pass sizes (N >= 2^13, FUSED and PER_PASS):
+ * the radix split N = 2^p1 x 2^(n-p1) and the height of the second pass's row
+ * tiles (Sec. VI-C: the decomposition and the per-CTA tile are tuning
+ * parameters).  0 is the default split p1 = floor(n/2); 1 halves the row tile;
+ * 2 moves one stage to the other pass (ntt_plan_info reports the result). */
+enum {
+    NTT_GEOMETRY_DEFAULT = 0,
+    NTT_GEOMETRY_SMALL_ROW_TILE = 1,
+    NTT_GEOMETRY_ALT_SPLIT = 2
+};
+
 typedef struct ntt_plan_opts {
     uint32_t twiddle_mode;    /* NTT_TWIDDLE_*; AUTO: OT (ot_stages, default 1) for N >= 2^13, TABLE below */
     uint32_t ot_stages;       /* OT: final stages built on the fly, 1 or 2 (0 = 1) */
     uint32_t kernel;          /* NTT_KERNEL_* */
-    uint32_t reserved[5];     /* must be zero */
+    uint32_t geometry;        /* NTT_GEOMETRY_*; must be 0 for N <= 2^12 and for RADIX2 */
+    uint32_t reserved[4];     /* must be zero */
 } ntt_plan_opts;
 
 /*
@@ -338,6 +350,39 @@ ntt_status ntt_server_wait(ntt_server* server, uint64_t ticket, uint64_t timeout
 /* Timestamps of a request (for latency statistics). */
 ntt_status ntt_server_request_times(ntt_server* server, uint64_t ticket, ntt_request_times* times);
 
+/* One configuration tried by ntt_autotune, and its measured times. */
+typedef struct ntt_tune_entry {
+    ntt_plan_opts opts;       /* the configuration, as plan options */
+    double forward_us;        /* mean device time of one ntt_forward call */
+    double inverse_us;        /* mean device time of one ntt_inverse call */
+    ntt_status status;        /* NTT_OK, or why the configuration was not timed */
+    uint32_t reserved;
+} ntt_tune_entry;
+
+/*
+ * Autotuner: the radix split and row tile (NTT_GEOMETRY_*), the kernel
+ * organisation (FUSED, PER_PASS, RADIX2) and the twiddle supply (TABLE, OT of
+ * the last 1 or 2 stages), the tuning parameters of Sec. VI-C and VII, are
+ * picked by measurement on the current device.  Every compiled configuration
+ * for N-point transforms of `batch` polynomials over primes[0..L-1] is timed:
+ * `reps` calls (0: 20) of each direction after two warm-up calls, CUDA events
+ * on an internal stream, inputs rotating over buffers that together exceed
+ * twice the L2 (at most 1 GiB).  The fastest by forward + inverse time goes to
+ * *best.
+ *   entries / max_entries / count : optional; when entries is non-NULL, up to
+ *     max_entries results are written in candidate order and *count (if
+ *     non-NULL) receives the number of candidates.
+ * The choice is cached per (device, N, L, batch, primes): a call with
+ * entries == NULL returns the cached choice without timing when there is one
+ * (then *count, if given, is 0).  A call with entries always times again and
+ * refreshes the cache.  Allocates and frees device memory and plans, and
+ * synchronises the device.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME,
+ * NTT_ERR_OOM, NTT_ERR_CUDA; NTT_ERR_DEVICE when no configuration could be
+ * timed.
+ */
+ntt_status ntt_autotune(uint32_t N, const uint64_t* primes, uint32_t L, uint32_t batch, uint32_t reps,
+                        ntt_plan_opts* best, ntt_tune_entry* entries, uint32_t max_entries, uint32_t* count);
+
 /*
  * 32-bit word transforms (Sec. IV, "32b vs. 64b word size": the same modulus
  * built from twice as many primes of half the width).  A separate plan type
@@ -394,6 +439,8 @@ typedef struct ntt_plan_info {
     uint32_t device;          /* CUDA device ordinal */
     uint32_t kernel;          /* NTT_KERNEL_FUSED, NTT_KERNEL_PER_PASS or NTT_KERNEL_RADIX2 */
     uint64_t device_bytes;    /* device memory held by the plan (tables) */
+    uint32_t geometry;        /* NTT_GEOMETRY_* */
+    uint32_t row_tile_log2;   /* rows per tile of the second pass (two-pass sizes), log2 */
 } ntt_plan_info;
 
 ntt_status ntt_plan_query(const ntt_plan* plan, ntt_plan_info* info);

@@ -41,6 +41,10 @@ NTT_KERNEL_FUSED = 1
 NTT_KERNEL_PER_PASS = 2
 NTT_KERNEL_RADIX2 = 3
 
+NTT_GEOMETRY_DEFAULT = 0
+NTT_GEOMETRY_SMALL_ROW_TILE = 1
+NTT_GEOMETRY_ALT_SPLIT = 2
+
 NTT_OP_FORWARD = 1
 NTT_OP_INVERSE = 2
 
@@ -51,13 +55,20 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("kernel", _u32), ("reserved", _u32 * 5)]
+    _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("kernel", _u32), ("geometry", _u32),
+                ("reserved", _u32 * 4)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("opts", PlanOpts), ("forward_us", ctypes.c_double), ("inverse_us", ctypes.c_double),
+                ("status", ctypes.c_int), ("reserved", _u32)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("N", _u32), ("L", _u32), ("log2_N", _u32), ("passes", _u32),
                 ("pass1_log2", _u32), ("twiddle_mode", _u32), ("ot_stages", _u32),
-                ("device", _u32), ("kernel", _u32), ("device_bytes", _u64)]
+                ("device", _u32), ("kernel", _u32), ("device_bytes", _u64), ("geometry", _u32),
+                ("row_tile_log2", _u32)]
 
 
 class Job(ctypes.Structure):
@@ -152,6 +163,9 @@ def _lib():
             L.ntt_plan_device_status.argtypes = [_vp, ctypes.POINTER(_u32)]
             L.ntt_plan_psi.restype = S
             L.ntt_plan_psi.argtypes = [_vp, _u32, _u64p]
+            L.ntt_autotune.restype = S
+            L.ntt_autotune.argtypes = [_u32, _u64p, _u32, _u32, _u32, ctypes.POINTER(PlanOpts),
+                                       ctypes.POINTER(TuneEntry), _u32, ctypes.POINTER(_u32)]
             L.ntt_plan32_create.restype = S
             L.ntt_plan32_create.argtypes = [ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32), _u32]
             L.ntt_plan32_destroy.restype = None
@@ -213,11 +227,11 @@ def _check(st: int, where: str):
 # C ABI, same names
 # --------------------------------------------------------------------------
 def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
-                    kernel: int = NTT_KERNEL_AUTO) -> int:
+                    kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT) -> int:
     """Create a plan; returns the opaque handle (an int).  Raises NttError."""
     primes = [int(p) for p in primes]
     arr = (_u64 * len(primes))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry)
     out = _vp()
     _check(_lib().ntt_plan_create(ctypes.byref(out), N, arr, len(primes), ctypes.byref(opts)),
            "ntt_plan_create")
@@ -225,11 +239,11 @@ def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_sta
 
 
 def ntt_plan_create_status(N: int, primes, twiddle_mode: int = 0, ot_stages: int = 0, reserved=None,
-                           kernel: int = 0):
+                           kernel: int = 0, geometry: int = 0):
     """Like ntt_plan_create but returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
     arr = (_u64 * max(1, len(primes)))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry)
     if reserved:
         for i, v in enumerate(reserved):
             opts.reserved[i] = v
@@ -351,6 +365,22 @@ def ntt_plan_psi(plan: int, l: int) -> int:
     return int(v.value)
 
 
+def ntt_autotune(N: int, primes, batch: int = 1, reps: int = 0, entries: bool = True):
+    """Time every compiled configuration on the current device; returns
+    (best PlanOpts, [TuneEntry, ...]).  With entries=False the cached choice is
+    returned when there is one (and the list is empty)."""
+    primes = [int(p) for p in primes]
+    arr = (_u64 * max(1, len(primes)))(*primes)
+    best = PlanOpts()
+    cap = 64
+    buf = (TuneEntry * cap)() if entries else None
+    cnt = _u32()
+    _check(_lib().ntt_autotune(N, arr, len(primes), batch, reps, ctypes.byref(best), buf, cap if entries else 0,
+                               ctypes.byref(cnt)), "ntt_autotune")
+    out = [buf[i] for i in range(min(cnt.value, cap))] if entries else []
+    return best, out
+
+
 def ntt_plan32_create_status(N: int, primes):
     """Create a 32-bit plan; returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
@@ -397,11 +427,16 @@ class Plan:
     """RAII wrapper over a plan handle."""
 
     def __init__(self, N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
-                 kernel: int = NTT_KERNEL_AUTO):
+                 kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT):
         self.N = N
         self.primes = [int(p) for p in primes]
         self.L = len(self.primes)
-        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel)
+        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel, geometry)
+
+    @classmethod
+    def from_opts(cls, N: int, primes, opts: PlanOpts):
+        """A plan with the options an autotuner run returned."""
+        return cls(N, primes, opts.twiddle_mode, opts.ot_stages, opts.kernel, opts.geometry)
 
     def forward(self, data, batch: int = 1, stream=None):
         ntt_forward(self.handle, data, batch, stream)

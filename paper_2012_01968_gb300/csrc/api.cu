@@ -175,7 +175,7 @@ ntt_status ntt_mul_negacyclic(const ntt_plan* p, uint64_t* a, uint64_t* b, uint6
         jb.data = reinterpret_cast<ntt::u64*>(b);
         const ntt::JobCtx jobs[2] = {ja, jb};
         const uint32_t ots = p->twiddle_mode == NTT_TWIDDLE_OT ? p->ot_stages : 0;
-        const ntt::JobsCtx jc{jobs, 2u, p->n, ots, p->d_status, p->d_work, p->work_limbs, s, 0u};
+        const ntt::JobsCtx jc{jobs, 2u, p->n, ots, p->d_status, p->d_work, p->work_limbs, s, 0u, p->geom};
         e = ntt::launch_fused_jobs(jc, true);
     } else {
         const ntt::LaunchCtx ca = p->ctx(a, (uint32_t)limbs, p->L, s);

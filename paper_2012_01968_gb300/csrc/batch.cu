@@ -109,7 +109,7 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
     }
     if (ntt::host::any_overlap(ranges)) return NTT_ERR_INVALID_ARG;
 
-    // group the fused jobs by (size, direction, OT stages); the rest run alone
+    // group the fused jobs by (size and geometry, direction, OT stages); the rest run alone
     std::vector<uint32_t> fused, direct;
     std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> keys;
     std::vector<uint64_t> limbs, sizes;
@@ -118,7 +118,7 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED) {
             const uint32_t ots = p->twiddle_mode == NTT_TWIDDLE_OT ? p->ot_stages : 0;
             fused.push_back(i);
-            keys.emplace_back(p->n, jobs[i].op, ots);
+            keys.emplace_back(p->n | (p->geom << 8), jobs[i].op, ots);
             limbs.push_back((uint64_t)jobs[i].batch * jobs[i].levels);
             sizes.push_back(p->N);
         } else {
@@ -169,10 +169,10 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
                                      p->d_ota_i, p->d_otb_i});
         }
         const int k = at[ci];
-        const uint32_t n = std::get<0>(c.key), ots = std::get<2>(c.key);
+        const uint32_t n = std::get<0>(c.key) & 0xFFu, geom = std::get<0>(c.key) >> 8, ots = std::get<2>(c.key);
         const bool fwd = std::get<1>(c.key) == NTT_OP_FORWARD;
         const ntt::JobsCtx ctx{jc.data(), (uint32_t)jc.size(), n, ots, b->d_status, b->d_work + off,
-                               (uint32_t)c.limbs, b->s[k], 0u};
+                               (uint32_t)c.limbs, b->s[k], 0u, geom};
         off += ntt::fused_work_words(c.limbs);
         e = ntt::launch_fused_jobs(ctx, fwd);
         if (e != cudaSuccess) break;

@@ -156,5 +156,44 @@ private:
     std::map<size_t, size_t> free_;
 };
 
+// Configurations the autotuner times for N = 2^n, as plan option codes
+// (kernel 1 FUSED, 2 PER_PASS, 3 RADIX2; twiddle 1 TABLE, 2 OT with ot_stages
+// 1 or 2; geometry 0 .. geometries-1).  Two-pass sizes (n >= 13): every
+// geometry x {FUSED, PER_PASS} x {TABLE, OT1, OT2}, then RADIX2 with table
+// twiddles.  One-pass sizes: the one-pass kernel (kernel 0 = AUTO) and RADIX2.
+struct TuneCandidate {
+    uint32_t kernel, twiddle_mode, ot_stages, geometry;
+};
+inline std::vector<TuneCandidate> tune_candidates(uint32_t n, uint32_t geometries, uint32_t single_pass_max)
+{
+    std::vector<TuneCandidate> out;
+    if (n <= single_pass_max) {
+        out.push_back(TuneCandidate{0, 1, 0, 0});
+        out.push_back(TuneCandidate{3, 1, 0, 0});
+        return out;
+    }
+    for (uint32_t g = 0; g < geometries; ++g)
+        for (uint32_t k = 1; k <= 2; ++k) {
+            out.push_back(TuneCandidate{k, 1, 0, g});
+            out.push_back(TuneCandidate{k, 2, 1, g});
+            out.push_back(TuneCandidate{k, 2, 2, g});
+        }
+    out.push_back(TuneCandidate{3, 1, 0, 0});
+    return out;
+}
+
+// Index of the fastest timed candidate by forward + inverse time (ties: the
+// earlier one), or -1 when none was timed (ok[i] false for all).
+inline int tune_pick(const std::vector<double>& fwd_us, const std::vector<double>& inv_us,
+                     const std::vector<bool>& ok)
+{
+    int best = -1;
+    for (size_t i = 0; i < fwd_us.size(); ++i) {
+        if (!ok[i]) continue;
+        if (best < 0 || fwd_us[i] + inv_us[i] < fwd_us[(size_t)best] + inv_us[(size_t)best]) best = (int)i;
+    }
+    return best;
+}
+
 }  // namespace host
 }  // namespace ntt

@@ -207,7 +207,7 @@ cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
         }
     }
     const JobCtx job{c.data, c.limbs, c.L, c.primes, c.tw, c.tw_len, c.ota_f, c.otb_f, c.ota_i, c.otb_i};
-    const JobsCtx jc{&job, 1u, c.n, c.ots, c.status, c.work, c.work_limbs, c.stream, c.max_polls};
+    const JobsCtx jc{&job, 1u, c.n, c.ots, c.status, c.work, c.work_limbs, c.stream, c.max_polls, c.geom};
     return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(jc, fwd);
 }
 

@@ -167,9 +167,12 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
         if (r) return NTT_ERR_INVALID_ARG;
     if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
     if (o.kernel > NTT_KERNEL_RADIX2) return NTT_ERR_INVALID_ARG;
+    if (o.geometry >= (uint32_t)ntt::kGeometries) return NTT_ERR_INVALID_ARG;
     const uint32_t n = (uint32_t)__builtin_ctz(N);
-    const uint32_t p1 = (uint32_t)ntt::split_p1((int)n);
     const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
+    if (o.geometry && (!two_pass || o.kernel == NTT_KERNEL_RADIX2)) return NTT_ERR_INVALID_ARG;
+    const uint32_t p1 = two_pass ? (uint32_t)ntt::geometry_of((int)n, (int)o.geometry).p1
+                                 : (uint32_t)ntt::split_p1((int)n);
     // AUTO: OT on the last stage for two-pass sizes (measured faster than the
     // table there, and half the last stage's twiddle traffic), table below
     const bool radix2 = o.kernel == NTT_KERNEL_RADIX2;
@@ -201,6 +204,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     p->twiddle_mode = mode;
     p->ot_stages = ots;
     p->kernel = radix2 ? NTT_KERNEL_RADIX2 : o.kernel == NTT_KERNEL_PER_PASS ? NTT_KERNEL_PER_PASS : NTT_KERNEL_FUSED;
+    p->geom = o.geometry;
     cudaError_t ce = cudaGetDevice(&p->device);
     if (ce != cudaSuccess) {
         ntt_internal_set_cuda_error(ce);
@@ -279,6 +283,8 @@ extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
     info->device = (uint32_t)p->device;
     info->kernel = p->kernel;
     info->device_bytes = p->device_bytes;
+    info->geometry = p->geom;
+    info->row_tile_log2 = p->passes == 2 ? (uint32_t)ntt::geometry_of((int)p->n, (int)p->geom).logc_r : 0;
     return NTT_OK;
 }
 

@@ -17,6 +17,26 @@ namespace ntt {
 constexpr int SINGLE_PASS_MAX = 12;
 inline int split_p1(int n) { return n <= SINGLE_PASS_MAX ? n : n - (n + 1) / 2; }
 
+// Geometries of the two-pass sizes (13 <= n <= 17): the pass split p1 (stages
+// of the first, column-like pass) and the row tile height 2^logc_r of the
+// second pass.  Index 0 is the default (p1 = split_p1(n)); 1 halves the row
+// tile; 2 moves one stage to the other pass.  Each is compiled (k_nXX.cu,
+// k_nXX_g1.cu, k_nXX_g2.cu) and picked per plan, by hand or by the autotuner.
+// Limits: a column tile is 16 columns x 2^p1 rows (one TMA box, 2^p1 <= 256),
+// a row tile at most 4096 words.
+constexpr int kGeometries = 3;
+struct Geometry {
+    int p1, logc_r;
+};
+constexpr Geometry kGeometryTable[5][kGeometries] = {
+    {{6, 5}, {6, 4}, {7, 6}},    // n = 13
+    {{7, 5}, {7, 4}, {6, 4}},    // n = 14
+    {{7, 4}, {7, 3}, {8, 5}},    // n = 15
+    {{8, 4}, {8, 3}, {7, 3}},    // n = 16
+    {{8, 3}, {8, 2}, {7, 2}},    // n = 17
+};
+constexpr Geometry geometry_of(int n, int g) { return kGeometryTable[n - 13][g]; }
+
 // Round geometry of the pass that holds stage s (per-thread radix 2^KMAX), used
 // to lay out the twiddle table in the slot order the kernels read.
 #ifndef NTT_KMAX
@@ -67,6 +87,7 @@ struct LaunchCtx {
     u32 work_limbs;          // limbs the work area covers (fused_work_words(work_limbs) words)
     cudaStream_t stream;
     u32 max_polls;           // bound of the fused kernel's waits (0: the default)
+    u32 geom;                // geometry index (two-pass sizes; see kGeometryTable)
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
@@ -99,6 +120,7 @@ struct JobsCtx {
     u32 work_limbs;          // >= the jobs' limbs
     cudaStream_t stream;
     u32 max_polls;           // bound of every wait (0: the default)
+    u32 geom = 0;            // geometry index shared by the jobs
 };
 cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
 cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a, const u64* b,
@@ -135,6 +157,7 @@ struct ntt_plan {
     ntt::Tw* d_otb_i = nullptr;
     uint64_t device_bytes = 0;
     uint32_t kernel = 0;                  // NTT_KERNEL_*
+    uint32_t geom = 0;                    // geometry index (two-pass sizes)
     uint32_t* d_status = nullptr;         // device status word (kernel error bits)
     uint32_t* d_work = nullptr;           // fused kernel's work area: fused_work_words(work_limbs) words
     uint32_t work_limbs = 0;
@@ -175,6 +198,7 @@ struct ntt_plan {
         c.work_limbs = work_limbs;
         c.stream = s;
         c.max_polls = 0;
+        c.geom = geom;
         return c;
     }
 

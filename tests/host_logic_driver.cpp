@@ -78,6 +78,23 @@ int main()
             std::vector<std::pair<uintptr_t, uintptr_t>> r(n);
             for (auto& x : r) std::cin >> x.first >> x.second;
             std::printf("%d\n", any_overlap(r) ? 1 : 0);
+        } else if (cmd == "tune") {
+            uint32_t n, geometries, single_max;
+            std::cin >> n >> geometries >> single_max;
+            for (const auto& c : tune_candidates(n, geometries, single_max))
+                std::printf("%u %u %u %u ; ", c.kernel, c.twiddle_mode, c.ot_stages, c.geometry);
+            std::printf("\n");
+        } else if (cmd == "pick") {
+            int m;
+            std::cin >> m;
+            std::vector<double> f(m), v(m);
+            std::vector<bool> ok(m);
+            for (int i = 0; i < m; ++i) {
+                int o;
+                std::cin >> f[i] >> v[i] >> o;
+                ok[i] = o != 0;
+            }
+            std::printf("%d\n", tune_pick(f, v, ok));
         }
     }
     return 0;

@@ -324,17 +324,25 @@ def logc_rows(p2):
     return min(5, 12 - p2)
 
 
-def transform(a, q, psi, n, fwd, ots=0):
+# (p1, log2 rows per row tile) of the two-pass geometries 0, 1, 2 (n = 13 .. 17)
+GEOMETRIES = {13: [(6, 5), (6, 4), (7, 6)], 14: [(7, 5), (7, 4), (6, 4)], 15: [(7, 4), (7, 3), (8, 5)],
+              16: [(8, 4), (8, 3), (7, 3)], 17: [(8, 3), (8, 2), (7, 2)]}
+
+
+def transform(a, q, psi, n, fwd, ots=0, geometry=0):
     """Whole transform as the library dispatches it (one limb)."""
     data = [int(v) for v in a]
     p1, p2 = split(n)
+    if p2 and geometry:
+        p1, LRg = GEOMETRIES[n][geometry]
+        p2 = n - p1
     if p2 == 0:
         T = PrimeTables(q, psi, n, n, 0)
         run_pass(data, T, P=n, LOGC=0, KMAX=4, ROWS=True, FWD=fwd, XIN=1, FINAL=True, HAS_S0=True,
                  OTS=0, TW_SMEM=False, s0=0)
         return data
     T = PrimeTables(q, psi, n, p1, ots)
-    LR = logc_rows(p2)
+    LR = LRg if geometry else logc_rows(p2)
     if fwd:
         run_pass(data, T, P=p1, LOGC=4, KMAX=4, ROWS=False, FWD=True, XIN=1, FINAL=False, HAS_S0=True,
                  OTS=0, TW_SMEM=True, s0=0)

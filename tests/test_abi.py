@@ -1,5 +1,6 @@
 """C ABI: the library loads, exports every declared symbol, and validates
 arguments on the host (no GPU needed for any of these)."""
+import ctypes
 import os
 import subprocess
 
@@ -58,6 +59,9 @@ BIG = I.prime_chain(3, 1 << 18)
     (1 << 16, BIG[:1], {"twiddle_mode": G.NTT_TWIDDLE_OT, "ot_stages": 3}, G.NTT_ERR_INVALID_ARG),
     (1 << 16, BIG[:1], {"twiddle_mode": G.NTT_TWIDDLE_TABLE, "ot_stages": 1}, G.NTT_ERR_INVALID_ARG),
     (1 << 12, BIG[:1], {"reserved": [1]}, G.NTT_ERR_INVALID_ARG),
+    (1 << 16, BIG[:1], {"geometry": 3}, G.NTT_ERR_INVALID_ARG),                # no such geometry
+    (1 << 12, BIG[:1], {"geometry": 1}, G.NTT_ERR_INVALID_ARG),                # one-pass size
+    (1 << 16, BIG[:1], {"geometry": 2, "kernel": G.NTT_KERNEL_RADIX2}, G.NTT_ERR_INVALID_ARG),
 ])
 def test_plan_create_rejects(lib, N, primes, kw, want):
     st, h = G.ntt_plan_create_status(N, primes, **kw)
@@ -102,6 +106,12 @@ def test_null_arguments_rejected(lib):
     assert lib.ntt_inverse32(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_plan32_psi(None, 0, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_plan32_create(None, 16, None, 1) == G.NTT_ERR_INVALID_ARG
+    best = G.PlanOpts()
+    assert lib.ntt_autotune(16, None, 1, 1, 1, ctypes.byref(best), None, 0, None) == G.NTT_ERR_INVALID_ARG
+    arr = (ctypes.c_uint64 * 1)(BIG[0])
+    assert lib.ntt_autotune(16, arr, 1, 0, 1, ctypes.byref(best), None, 0, None) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_autotune(3, arr, 1, 1, 1, ctypes.byref(best), None, 0, None) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_autotune(16, arr, 1, 1, 1, None, None, 0, None) == G.NTT_ERR_INVALID_ARG
     lib.ntt_plan32_destroy(None)
 
 

@@ -181,3 +181,36 @@ def test_arena_release_coalesces(run):
     cmd = [f"a {b}" for b in sizes] + [f"r {reps[i][1]} {sizes[i]}" for i in order]
     line = run(f"arena {cap} {len(cmd)} " + " ".join(cmd) + "\n")[0]
     assert [int(x) for x in line.split("|")[1].split()] == [1, 0, cap]
+
+
+# -- autotuner candidates and choice ------------------------------------------------
+def test_tune_candidates_cover_the_space(run):
+    for n in range(1, 18):
+        line = run(f"tune {n} 3 12\n")[0]
+        cands = [tuple(int(x) for x in c.split()) for c in line.split(";") if c.strip()]
+        assert len(set(cands)) == len(cands)                         # no duplicates
+        if n <= 12:
+            assert cands == [(0, 1, 0, 0), (3, 1, 0, 0)]             # one-pass kernel, radix-2
+            continue
+        want = {(k, t, o, g) for g in range(3) for k in (1, 2) for t, o in ((1, 0), (2, 1), (2, 2))}
+        want.add((3, 1, 0, 0))                                       # radix-2: table, default geometry
+        assert set(cands) == want
+
+
+def test_tune_pick_is_the_argmin(run):
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        m = int(rng.integers(1, 20))
+        f = rng.uniform(1, 100, m).round(3)
+        v = rng.uniform(1, 100, m).round(3)
+        ok = rng.random(m) < 0.8
+        if rng.random() < 0.2:
+            f[:] = 5.0
+            v[:] = 5.0                                               # all tied: the first timed one
+        text = f"pick {m} " + " ".join(f"{a} {b} {int(o)}" for a, b, o in zip(f, v, ok)) + "\n"
+        got = int(run(text)[0])
+        if not ok.any():
+            assert got == -1
+            continue
+        tot = np.where(ok, f + v, np.inf)
+        assert got == int(np.argmin(tot))                            # argmin takes the first of ties

@@ -114,3 +114,28 @@ def test_round_accesses_bank_conflicts(P, LOGC, rows):
                     keys = [(a >> 1) % 8 for a in grp] if pairs else [a % 16 for a in grp]
                     worst = max(worst, max(keys.count(k) for k in set(keys)))
     assert worst <= 2, worst
+
+
+@pytest.mark.parametrize("n,geometry,ots", [(13, 1, 0), (13, 2, 1), (14, 1, 2), (14, 2, 0), (14, 2, 2)])
+def test_model_alternative_geometries(orc, n, geometry, ots):
+    """The autotuner's geometries (half the row tile; the other pass split):
+    the same transform, with the tables laid out for their split."""
+    N, q, a = _case(n, 300 + n + geometry)
+    psi = orc.psi(q, N)
+    got = KM.transform(a, q, psi, n, True, ots, geometry)
+    assert got == [int(v) for v in orc.ntt_radix2(a, q)]
+    assert KM.transform(got, q, psi, n, False, ots, geometry) == a
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+@pytest.mark.parametrize("geometry", [0, 1, 2])
+def test_geometry_limits(n, geometry):
+    """Each geometry fits the fused kernel: a column tile is one TMA box of 16
+    columns x 2^p1 rows (at most 256), a row tile at most 4096 words in whole
+    rows, and both passes tile the limb exactly."""
+    p1, lr = KM.GEOMETRIES[n][geometry]
+    p2 = n - p1
+    assert 1 << p1 <= 256 and (1 << p2) >= 16
+    assert (1 << (lr + p2)) <= 4096 and lr <= p1
+    UC, UR = (1 << p2) // 16, (1 << p1) >> lr
+    assert UC * 16 * (1 << p1) == 1 << n and UR * (1 << lr) * (1 << p2) == 1 << n
