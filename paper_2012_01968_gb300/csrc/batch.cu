@@ -51,9 +51,44 @@ void release(ntt_batch* b)
         if (b->join[k]) cudaEventDestroy(b->join[k]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
-    cudaFree(b->d_work);
+    if (b->d_work) {
+        cudaFreeAsync(b->d_work, nullptr);
+        cudaStreamSynchronize(nullptr);
+    }
     cudaFree(b->d_status);
     delete b;
+}
+
+// Make the work area hold `words` words, zero-filled, ordered on `caller`:
+// the caller's stream first waits for everything the batch's streams hold
+// (the old area's last users), then frees the old area and allocates the new
+// one stream-ordered, so no other stream or host thread is blocked.  Not
+// during graph capture (the area must outlive the captured graph).
+cudaError_t grow_work(ntt_batch* b, size_t words, cudaStream_t caller)
+{
+    if (words <= b->work_words) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(caller, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+    for (int k = 0; k < kStreams && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->join[k], b->s[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, b->join[k], 0);
+    }
+    if (e != cudaSuccess) return e;
+    if (b->d_work) {
+        e = cudaFreeAsync(b->d_work, caller);
+        b->d_work = nullptr;
+        b->work_words = 0;
+        if (e != cudaSuccess) return e;
+    }
+    void* mem = nullptr;
+    e = cudaMallocAsync(&mem, words * sizeof(uint32_t), caller);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(mem, 0, words * sizeof(uint32_t), caller);
+    b->d_work = static_cast<uint32_t*>(mem);
+    if (e == cudaSuccess) b->work_words = words;
+    return e;
 }
 
 }  // namespace
@@ -131,23 +166,16 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         for (uint32_t& j : c.jobs) j = fused[j];          // indices into the submission
     }
 
-    // one work area per fused launch, back to back; grown after the device drains
+    // one work area per fused launch, back to back; grown in stream order
+    const cudaStream_t caller = (cudaStream_t)stream;
     size_t words = 0;
     for (const ntt::host::Chunk& c : chunks) words += ntt::fused_work_words(c.limbs);
     if (words > b->work_words) {
-        cudaError_t e = cudaDeviceSynchronize();
+        cudaError_t e = grow_work(b, words, caller);
         if (e != cudaSuccess) return cuda_status(e);
-        cudaFree(b->d_work);
-        b->d_work = nullptr;
-        b->work_words = 0;
-        e = cudaMalloc(&b->d_work, words * sizeof(uint32_t));
-        if (e == cudaSuccess) e = cudaMemset(b->d_work, 0, words * sizeof(uint32_t));
-        if (e != cudaSuccess) return cuda_status(e);
-        b->work_words = words;
     }
 
     // fork onto the internal streams
-    const cudaStream_t caller = (cudaStream_t)stream;
     const int used = (int)std::min<size_t>(kStreams, chunks.size() + direct.size());
     cudaError_t e = cudaEventRecord(b->fork, caller);
     for (int k = 0; k < used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->s[k], b->fork, 0);
@@ -190,6 +218,15 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         cudaStreamWaitEvent(caller, b->join[k], 0);
     }
     return cuda_status(e);
+}
+
+// Library-internal: size the work area up front (the serving loop reserves
+// its batches' areas at creation, so that no submission grows one).
+ntt_status ntt_internal_batch_reserve(ntt_batch* b, uint64_t words, void* stream)
+{
+    if (!b) return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(b->mu);
+    return cuda_status(grow_work(b, (size_t)words, (cudaStream_t)stream));
 }
 
 ntt_status ntt_batch_device_status(ntt_batch* b, uint32_t* status)

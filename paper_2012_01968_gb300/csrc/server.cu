@@ -28,6 +28,7 @@
 #include "plan.h"
 
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
+extern "C" ntt_status ntt_internal_batch_reserve(ntt_batch* b, uint64_t words, void* stream);
 
 namespace {
 
@@ -218,6 +219,15 @@ ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess && ntt_batch_create(&s.batch) != NTT_OK) e = cudaErrorMemoryAllocation;
     }
+    // every slot's batch gets its fused-kernel work area now: one batch holds
+    // at most max_batch_jobs launches and, within the budget, at most
+    // budget / (8 * 2^13) limbs of fused sizes (capped at 2^24)
+    const uint64_t limb_bound = std::min<uint64_t>(srv->opts.hbm_budget_bytes / (8ull << 13), 1ull << 24);
+    const uint64_t words = 4ull * srv->opts.max_batch_jobs + 2ull * limb_bound;
+    for (Slot& s : srv->slots)
+        if (e == cudaSuccess && ntt_internal_batch_reserve(s.batch, words, s.stream) != NTT_OK)
+            e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         for (Slot& s : srv->slots) {
             if (s.batch) ntt_batch_destroy(s.batch);
