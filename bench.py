@@ -285,6 +285,39 @@ def _ok(G, st, what):
         raise RuntimeError(f"{what}: {G.ntt_status_string(st)} ({G.ntt_last_cuda_error()})")
 
 
+def host_link_rates(torch, hin, hout, reps=20):
+    """Pinned host <-> device copy rates of this machine's link (GB/s): one
+    direction at a time, and both at once on two streams, for the buffers
+    the end-to-end call moves."""
+    d = torch.empty_like(hin, device="cuda")
+    d2 = torch.empty_like(hin, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nbytes = hin.numel() * hin.element_size()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d.copy_(hin, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            hout.copy_(d2, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+    return {"h2d_gbs": nbytes / timed(h2d) / 1e9, "d2h_gbs": nbytes / timed(d2h) / 1e9,
+            "both_gbs": 2 * nbytes / timed(both) / 1e9}
+
+
 def per_limb_c2(G, torch, w, host, steps):
     """The plain per-limb path on the C2 polynomial: one single-prime plan per
     limb and one launch per limb and direction (45 x 2 launches per step)."""
@@ -819,6 +852,13 @@ def main():
             raise RuntimeError("e2e round trip mismatch")
         e2e = {"value": 2 * L * E / el, "unit": unit, "h2d_bytes_per_step": poly_bytes,
                "d2h_bytes_per_step": poly_bytes, "steps": E}
+        link = host_link_rates(torch, hin, hout)
+        # a step needs its input in and its result out: with both directions
+        # overlapped at best, the link alone takes max(in, out, both) per step
+        t_link = max(poly_bytes / link["h2d_gbs"], poly_bytes / link["d2h_gbs"],
+                     2 * poly_bytes / link["both_gbs"]) / 1e9
+        e2e["host_link"] = dict(link, step_floor_us=t_link * 1e6, value_bound=2 * L / t_link,
+                                frac_of_bound=(2 * L * E / el) / (2 * L / t_link))
 
     per_limb = batched = None
     chain = I.chain_2_18_60()
