@@ -101,8 +101,17 @@ typedef struct ntt_plan_opts {
     uint32_t ot_stages;       /* OT: final stages built on the fly, 1 or 2 (0 = 1) */
     uint32_t kernel;          /* NTT_KERNEL_* */
     uint32_t geometry;        /* NTT_GEOMETRY_*; must be 0 for N <= 2^12 and for RADIX2 */
-    uint32_t reserved[4];     /* must be zero */
+    uint32_t flags;           /* NTT_PLAN_* bits */
+    uint32_t reserved[3];     /* must be zero */
 } ntt_plan_opts;
+
+/* Keep the plan's twiddle table resident in L2 across calls: plan creation
+ * raises this CUDA context's persisting-L2 limit (cudaLimitPersistingL2CacheSize,
+ * a per-context runtime limit) to cover the table, up to the device maximum,
+ * and the plan's own calls (ntt_forward / ntt_inverse and their variants) carry
+ * an L2 access-policy window over it (hits persist, misses stream).  Batch and
+ * server launches, which mix plans, do not. */
+#define NTT_PLAN_L2_TWIDDLES 1u
 
 /*
  * Create a plan for N-point transforms over the L primes primes[0..L-1].

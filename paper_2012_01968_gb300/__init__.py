@@ -45,6 +45,8 @@ NTT_GEOMETRY_DEFAULT = 0
 NTT_GEOMETRY_SMALL_ROW_TILE = 1
 NTT_GEOMETRY_ALT_SPLIT = 2
 
+NTT_PLAN_L2_TWIDDLES = 1
+
 NTT_OP_FORWARD = 1
 NTT_OP_INVERSE = 2
 
@@ -56,7 +58,7 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("kernel", _u32), ("geometry", _u32),
-                ("reserved", _u32 * 4)]
+                ("flags", _u32), ("reserved", _u32 * 3)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -227,11 +229,11 @@ def _check(st: int, where: str):
 # C ABI, same names
 # --------------------------------------------------------------------------
 def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
-                    kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT) -> int:
+                    kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0) -> int:
     """Create a plan; returns the opaque handle (an int).  Raises NttError."""
     primes = [int(p) for p in primes]
     arr = (_u64 * len(primes))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags)
     out = _vp()
     _check(_lib().ntt_plan_create(ctypes.byref(out), N, arr, len(primes), ctypes.byref(opts)),
            "ntt_plan_create")
@@ -239,11 +241,11 @@ def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_sta
 
 
 def ntt_plan_create_status(N: int, primes, twiddle_mode: int = 0, ot_stages: int = 0, reserved=None,
-                           kernel: int = 0, geometry: int = 0):
+                           kernel: int = 0, geometry: int = 0, flags: int = 0):
     """Like ntt_plan_create but returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
     arr = (_u64 * max(1, len(primes)))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags)
     if reserved:
         for i, v in enumerate(reserved):
             opts.reserved[i] = v
@@ -427,16 +429,17 @@ class Plan:
     """RAII wrapper over a plan handle."""
 
     def __init__(self, N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
-                 kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT):
+                 kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0):
         self.N = N
         self.primes = [int(p) for p in primes]
         self.L = len(self.primes)
-        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel, geometry)
+        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel, geometry, flags)
 
     @classmethod
-    def from_opts(cls, N: int, primes, opts: PlanOpts):
-        """A plan with the options an autotuner run returned."""
-        return cls(N, primes, opts.twiddle_mode, opts.ot_stages, opts.kernel, opts.geometry)
+    def from_opts(cls, N: int, primes, opts: PlanOpts, flags: int | None = None):
+        """A plan with the options an autotuner run returned (flags: override)."""
+        return cls(N, primes, opts.twiddle_mode, opts.ot_stages, opts.kernel, opts.geometry,
+                   opts.flags if flags is None else flags)
 
     def forward(self, data, batch: int = 1, stream=None):
         ntt_forward(self.handle, data, batch, stream)

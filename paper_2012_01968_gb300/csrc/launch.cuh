@@ -12,6 +12,33 @@ namespace ntt {
 
 constexpr u32 kMaxGridY = 65535;
 
+// Launch `kern` with an optional L2 access-policy window (persisting hits on
+// [base, base + bytes), streaming misses); a plain launch when bytes == 0.
+template <class Kern, class Arg>
+cudaError_t launch_windowed(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const void* base,
+                            size_t bytes, float hit, const Arg& arg)
+{
+    if (bytes == 0) {
+        kern<<<grid, block, smem, s>>>(arg);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+    attr[0].val.accessPolicyWindow.num_bytes = bytes;
+    attr[0].val.accessPolicyWindow.hitRatio = hit;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 // What one pass launch needs, for either word size.
 template <class W>
 struct PassLaunch {
@@ -21,6 +48,9 @@ struct PassLaunch {
     const typename WordTypes<W>::Tw* tw;
     u32 tw_len;
     cudaStream_t stream;
+    const void* l2_base = nullptr;   // L2 access-policy window (l2_bytes 0: none)
+    size_t l2_bytes = 0;
+    float l2_hit = 0.f;
 };
 
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
@@ -55,16 +85,19 @@ cudaError_t launch_pass_w(const PassLaunch<W>& c, u32 s0, const typename WordTyp
     for (u32 off = 0; off < c.limbs; off += kMaxGridY) {
         const u32 cnt = c.limbs - off < kMaxGridY ? c.limbs - off : kMaxGridY;
         a.limb_offset = off;
-        kern<<<dim3(tiles, cnt), T, smem, c.stream>>>(a);
+        const cudaError_t e = launch_windowed(kern, dim3(tiles, cnt), dim3(T), smem, c.stream, c.l2_base,
+                                              c.l2_bytes, c.l2_hit, a);
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
           bool TW_SMEM>
 cudaError_t launch_pass(const LaunchCtx& c, u32 s0, const Tw* ota, const Tw* otb)
 {
-    const PassLaunch<u64> pl{c.data, c.limbs, c.L, c.n, c.primes, c.tw, c.tw_len, c.stream};
+    const PassLaunch<u64> pl{c.data,   c.limbs,    c.L,        c.n,        c.primes,
+                             c.tw,     c.tw_len,   c.stream,   c.l2_base,  c.l2_bytes, c.l2_hit};
     return launch_pass_w<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, u64>(pl, s0, ota, otb);
 }
 
@@ -176,8 +209,8 @@ cudaError_t launch_fused_dir(const JobsCtx& c)
     a.limbs = (u32)limbs;
     a.a_window = fused_window_limbs(sizeof(u64) << (P1 + P2));
     a.max_polls = c.max_polls ? c.max_polls : 1u << 22;
-    kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(a);
-    return cudaGetLastError();
+    return launch_windowed(kern, dim3(grid), dim3(F::THREADS), F::SMEM, c.stream, c.l2_base, c.l2_bytes, c.l2_hit,
+                           a);
 }
 
 template <int P1, int P2, int LOGC_R, int KMAX, int MAXJ>
@@ -207,7 +240,8 @@ cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
         }
     }
     const JobCtx job{c.data, c.limbs, c.L, c.primes, c.tw, c.tw_len, c.ota_f, c.otb_f, c.ota_i, c.otb_i};
-    const JobsCtx jc{&job, 1u, c.n, c.ots, c.status, c.work, c.work_limbs, c.stream, c.max_polls, c.geom};
+    const JobsCtx jc{&job,   1u,         c.n,      c.ots,        c.status,  c.work,   c.work_limbs,
+                     c.stream, c.max_polls, c.geom, c.l2_base, c.l2_bytes, c.l2_hit};
     return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(jc, fwd);
 }
 

@@ -153,6 +153,33 @@ void free_plan(ntt_plan* p)
     delete p;
 }
 
+// Persisting L2 for the twiddle table (NTT_PLAN_L2_TWIDDLES): raise this
+// context's persisting-L2 limit to cover the table (never lower it), up to the
+// device maximum, and keep the fraction of the window that fits.
+std::mutex g_l2_mu;
+cudaError_t reserve_l2(ntt_plan* p)
+{
+    const size_t bytes = (size_t)p->L * p->tw_len * sizeof(Tw);
+    int max_persist = 0, max_window = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, p->device);
+    if (e != cudaSuccess) return e;
+    if (max_persist <= 0 || max_window <= 0 || bytes > (size_t)max_window) {
+        p->l2_hit = 0.f;              // no window: the plan runs as without the flag
+        return cudaSuccess;
+    }
+    std::lock_guard<std::mutex> g(g_l2_mu);
+    size_t cur = 0;
+    e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    if (e != cudaSuccess) return e;
+    const size_t want = std::min(bytes, (size_t)max_persist);
+    if (cur < want) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    p->l2_hit = e == cudaSuccess ? (float)std::min(1.0, (double)cur / (double)bytes) : 0.f;
+    return e;
+}
+
 }  // namespace
 
 extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t* primes, uint32_t L,
@@ -165,6 +192,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     if (opts) o = *opts;
     for (uint32_t r : o.reserved)
         if (r) return NTT_ERR_INVALID_ARG;
+    if (o.flags & ~NTT_PLAN_L2_TWIDDLES) return NTT_ERR_INVALID_ARG;
     if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
     if (o.kernel > NTT_KERNEL_RADIX2) return NTT_ERR_INVALID_ARG;
     if (o.geometry >= (uint32_t)ntt::kGeometries) return NTT_ERR_INVALID_ARG;
@@ -205,6 +233,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     p->ot_stages = ots;
     p->kernel = radix2 ? NTT_KERNEL_RADIX2 : o.kernel == NTT_KERNEL_PER_PASS ? NTT_KERNEL_PER_PASS : NTT_KERNEL_FUSED;
     p->geom = o.geometry;
+    p->flags = o.flags;
     cudaError_t ce = cudaGetDevice(&p->device);
     if (ce != cudaSuccess) {
         ntt_internal_set_cuda_error(ce);
@@ -257,6 +286,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     if (ce == cudaSuccess) ce = upload(&p->d_otb_f, h.otb_f, p->device_bytes);
     if (ce == cudaSuccess) ce = upload(&p->d_ota_i, h.ota_i, p->device_bytes);
     if (ce == cudaSuccess) ce = upload(&p->d_otb_i, h.otb_i, p->device_bytes);
+    if (ce == cudaSuccess && (p->flags & NTT_PLAN_L2_TWIDDLES)) ce = reserve_l2(p);
     if (ce != cudaSuccess) {
         ntt_internal_set_cuda_error(ce);
         free_plan(p);

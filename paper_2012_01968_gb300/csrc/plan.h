@@ -88,6 +88,9 @@ struct LaunchCtx {
     cudaStream_t stream;
     u32 max_polls;           // bound of the fused kernel's waits (0: the default)
     u32 geom;                // geometry index (two-pass sizes; see kGeometryTable)
+    const void* l2_base;     // L2 access-policy window of the launches (l2_bytes 0: none)
+    size_t l2_bytes;
+    float l2_hit;            // fraction of the window that persists
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
@@ -121,6 +124,9 @@ struct JobsCtx {
     cudaStream_t stream;
     u32 max_polls;           // bound of every wait (0: the default)
     u32 geom = 0;            // geometry index shared by the jobs
+    const void* l2_base = nullptr;   // L2 access-policy window (l2_bytes 0: none)
+    size_t l2_bytes = 0;
+    float l2_hit = 0.f;
 };
 cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
 cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a, const u64* b,
@@ -158,6 +164,8 @@ struct ntt_plan {
     uint64_t device_bytes = 0;
     uint32_t kernel = 0;                  // NTT_KERNEL_*
     uint32_t geom = 0;                    // geometry index (two-pass sizes)
+    uint32_t flags = 0;                   // NTT_PLAN_* bits
+    float l2_hit = 0.f;                   // persisting fraction of the twiddle window
     uint32_t* d_status = nullptr;         // device status word (kernel error bits)
     uint32_t* d_work = nullptr;           // fused kernel's work area: fused_work_words(work_limbs) words
     uint32_t work_limbs = 0;
@@ -199,6 +207,10 @@ struct ntt_plan {
         c.stream = s;
         c.max_polls = 0;
         c.geom = geom;
+        const bool win = (flags & NTT_PLAN_L2_TWIDDLES) && l2_hit > 0.f;
+        c.l2_base = win ? (const void*)d_tw : nullptr;
+        c.l2_bytes = win ? (size_t)L * tw_len * sizeof(ntt::Tw) : 0;
+        c.l2_hit = l2_hit;
         return c;
     }
 

@@ -62,6 +62,7 @@ BIG = I.prime_chain(3, 1 << 18)
     (1 << 16, BIG[:1], {"geometry": 3}, G.NTT_ERR_INVALID_ARG),                # no such geometry
     (1 << 12, BIG[:1], {"geometry": 1}, G.NTT_ERR_INVALID_ARG),                # one-pass size
     (1 << 16, BIG[:1], {"geometry": 2, "kernel": G.NTT_KERNEL_RADIX2}, G.NTT_ERR_INVALID_ARG),
+    (1 << 16, BIG[:1], {"flags": 2}, G.NTT_ERR_INVALID_ARG),                   # unknown flag bit
 ])
 def test_plan_create_rejects(lib, N, primes, kw, want):
     st, h = G.ntt_plan_create_status(N, primes, **kw)

@@ -126,3 +126,17 @@ def test_autotune_reports_and_picks_the_fastest(orc, n, L, batch):
         assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
         p.inverse(d, batch)
         assert np.array_equal(host(d), data)
+
+
+@pytest.mark.parametrize("n,kernel", [(12, G.NTT_KERNEL_AUTO), (16, G.NTT_KERNEL_FUSED), (16, G.NTT_KERNEL_PER_PASS)])
+def test_l2_resident_twiddles_same_results(orc, n, kernel):
+    """NTT_PLAN_L2_TWIDDLES changes only the cache policy of the launches."""
+    N = 1 << n
+    primes = I.prime_chain(4, 2 * N)
+    data = I.batch_uniform(495 + n, 2, primes, N)
+    with G.Plan(N, primes, G.NTT_TWIDDLE_AUTO, 0, kernel, 0, G.NTT_PLAN_L2_TWIDDLES) as p:
+        d = dev(data)
+        p.forward(d, 2)
+        assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
+        p.inverse(d, 2)
+        assert np.array_equal(host(d), data)
