@@ -140,3 +140,38 @@ def test_l2_resident_twiddles_same_results(orc, n, kernel):
         assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
         p.inverse(d, 2)
         assert np.array_equal(host(d), data)
+
+
+def test_config3_full_size_with_tuned_choice(orc):
+    """The large ring (N = 2^17, 60 limbs, one ciphertext) with the
+    configuration the bench's autotuner picks there (fused, table, half the row
+    tile), against the oracle in full."""
+    w = I.workload_c3()
+    N, primes = w.N, w.primes
+    data = I.batch_uniform(w.seed, 2, primes, N)
+    with G.Plan(N, primes, G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_FUSED, G.NTT_GEOMETRY_SMALL_ROW_TILE) as p:
+        d = dev(data)
+        p.forward(d, 2)
+        assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
+        p.inverse(d, 2)
+        assert np.array_equal(host(d), data)
+        assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("geometry", [1, 2])
+def test_host_call_and_noalloc_with_geometry(orc, geometry):
+    """The host-buffer call (segments viewing the tables from a prime offset)
+    and the no-allocation call under the alternative geometries."""
+    N = 1 << 15
+    primes = I.prime_chain(7, 2 * N)
+    data = I.batch_uniform(497, 2, primes, N)
+    want = oracle_fwd(orc, data, primes)
+    with G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_FUSED, geometry) as p:
+        out = np.empty_like(data)
+        G.ntt_execute_host(p.handle, data, out, 2, G.NTT_OP_FORWARD)
+        assert np.array_equal(out, want)
+        d = dev(data)
+        G.ntt_transform_noalloc(p.handle, d, 2, len(primes), G.NTT_OP_FORWARD)
+        assert np.array_equal(host(d), want)
+        G.ntt_transform_noalloc(p.handle, d, 2, len(primes), G.NTT_OP_INVERSE)
+        assert np.array_equal(host(d), data)
