@@ -260,7 +260,7 @@ def run_reference(args, metric, unit, w):
     print(json.dumps(line), flush=True)
 
 
-KERNEL_NAMES = {0: "auto", 1: "fused", 2: "per_pass", 3: "radix2"}
+KERNEL_NAMES = {0: "auto", 1: "fused", 2: "per_pass", 3: "radix2", 4: "high_radix"}
 
 
 def opts_summary(o):
@@ -482,11 +482,16 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None):
 def paper_ablation(G, torch, reps=40):
     """The structure of the paper's N sweep (21 limbs, forward transform,
     log N = 14..17) on this GPU: the radix-2 launch-per-stage organisation
-    the paper starts from, the launch-per-pass organisation (the paper's
-    two-kernel shared-memory design), and the one-launch fused kernel, each
-    with table and OT twiddles.  Buffers rotate over more than 2x L2."""
+    the paper starts from, its register-based high-radix step (radix 2^2 ..
+    2^5 per launch), the launch-per-pass organisation (the paper's two-kernel
+    shared-memory design), and the one-launch fused kernel, each with table
+    and OT twiddles.  Buffers rotate over more than 2x L2."""
     chain = I.prime_chain(21, 1 << 18)          # 21 largest primes < 2^60 = 1 mod 2^18
     configs = (("radix2", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_RADIX2),
+               ("high_radix4", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_HIGH_RADIX, 2),
+               ("high_radix8", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_HIGH_RADIX, 3),
+               ("high_radix16", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_HIGH_RADIX, 4),
+               ("high_radix32", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_HIGH_RADIX, 5),
                ("per_pass_table", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_PER_PASS),
                ("per_pass_ot1", G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_PER_PASS),
                ("fused_table", G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_FUSED),
@@ -503,8 +508,8 @@ def paper_ablation(G, torch, reps=40):
         pool = torch.empty(nbuf * words, dtype=torch.int64, device="cuda")
         pool.random_(0, 1 << 59, generator=gen)
         row = {}
-        for name, mode, ots, kern in configs:
-            with G.Plan(N, chain, mode, ots, kern) as p:
+        for name, mode, ots, kern, *radix in configs:
+            with G.Plan(N, chain, mode, ots, kern, radix_log2=radix[0] if radix else 0) as p:
                 ptr = [pool[i * words:(i + 1) * words].data_ptr() for i in range(nbuf)]
                 for i in range(5):
                     _ok(G, lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream), name)
@@ -517,6 +522,7 @@ def paper_ablation(G, torch, reps=40):
                 torch.cuda.synchronize()
                 row[name] = e0.elapsed_time(e1) * 1e3 / reps
         row["speedup_fused_ot1_vs_radix2"] = row["radix2"] / row["fused_ot1"]
+        row["speedup_high_radix16_vs_radix2"] = row["radix2"] / row["high_radix16"]
         row["speedup_per_pass_ot1_vs_radix2"] = row["radix2"] / row["per_pass_ot1"]
         out[f"logN{n}"] = row
         del pool

@@ -76,13 +76,16 @@ enum {
  * that runs both passes with per-limb dependency counters (FUSED, the
  * default), or one launch per pass (PER_PASS); for every size, RADIX2 is the
  * paper's starting point (Sec. VI): one launch per radix-2 stage with its
- * operands in global memory, table twiddles only, kept for comparison.
- * Results are identical. */
+ * operands in global memory, and HIGH_RADIX its register-based high-radix
+ * step (Sec. VI-B): one launch per radix_log2 stages, each thread running
+ * them on 2^radix_log2 operands in registers.  Both with table twiddles only,
+ * kept for comparison.  Results are identical. */
 enum {
     NTT_KERNEL_AUTO = 0,
     NTT_KERNEL_FUSED = 1,
     NTT_KERNEL_PER_PASS = 2,
-    NTT_KERNEL_RADIX2 = 3
+    NTT_KERNEL_RADIX2 = 3,
+    NTT_KERNEL_HIGH_RADIX = 4
 };
 
 /* Pass geometries of the two-pass sizes (N >= 2^13, FUSED and PER_PASS):
@@ -102,7 +105,8 @@ typedef struct ntt_plan_opts {
     uint32_t kernel;          /* NTT_KERNEL_* */
     uint32_t geometry;        /* NTT_GEOMETRY_*; must be 0 for N <= 2^12 and for RADIX2 */
     uint32_t flags;           /* NTT_PLAN_* bits */
-    uint32_t reserved[3];     /* must be zero */
+    uint32_t radix_log2;      /* HIGH_RADIX: stages per launch, 1..5 (0 = 4, radix 16); else 0 */
+    uint32_t reserved[2];     /* must be zero */
 } ntt_plan_opts;
 
 /* Keep the plan's twiddle table resident in L2 across calls: plan creation
@@ -370,7 +374,7 @@ typedef struct ntt_tune_entry {
 
 /*
  * Autotuner: the radix split and row tile (NTT_GEOMETRY_*), the kernel
- * organisation (FUSED, PER_PASS, RADIX2) and the twiddle supply (TABLE, OT of
+ * organisation (FUSED, PER_PASS, RADIX2, HIGH_RADIX) and the twiddle supply (TABLE, OT of
  * the last 1 or 2 stages), the tuning parameters of Sec. VI-C and VII, are
  * picked by measurement on the current device.  Every compiled configuration
  * for N-point transforms of `batch` polynomials over primes[0..L-1] is timed:
@@ -446,10 +450,12 @@ typedef struct ntt_plan_info {
     uint32_t twiddle_mode;    /* NTT_TWIDDLE_TABLE or NTT_TWIDDLE_OT */
     uint32_t ot_stages;       /* OT: final stages built on the fly */
     uint32_t device;          /* CUDA device ordinal */
-    uint32_t kernel;          /* NTT_KERNEL_FUSED, NTT_KERNEL_PER_PASS or NTT_KERNEL_RADIX2 */
+    uint32_t kernel;          /* NTT_KERNEL_FUSED, _PER_PASS, _RADIX2 or _HIGH_RADIX */
     uint64_t device_bytes;    /* device memory held by the plan (tables) */
     uint32_t geometry;        /* NTT_GEOMETRY_* */
     uint32_t row_tile_log2;   /* rows per tile of the second pass (two-pass sizes), log2 */
+    uint32_t radix_log2;      /* HIGH_RADIX: stages per launch; else 0 */
+    uint32_t reserved;
 } ntt_plan_info;
 
 ntt_status ntt_plan_query(const ntt_plan* plan, ntt_plan_info* info);

@@ -40,6 +40,7 @@ NTT_KERNEL_AUTO = 0
 NTT_KERNEL_FUSED = 1
 NTT_KERNEL_PER_PASS = 2
 NTT_KERNEL_RADIX2 = 3
+NTT_KERNEL_HIGH_RADIX = 4
 
 NTT_GEOMETRY_DEFAULT = 0
 NTT_GEOMETRY_SMALL_ROW_TILE = 1
@@ -58,7 +59,7 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("kernel", _u32), ("geometry", _u32),
-                ("flags", _u32), ("reserved", _u32 * 3)]
+                ("flags", _u32), ("radix_log2", _u32), ("reserved", _u32 * 2)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -70,7 +71,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("N", _u32), ("L", _u32), ("log2_N", _u32), ("passes", _u32),
                 ("pass1_log2", _u32), ("twiddle_mode", _u32), ("ot_stages", _u32),
                 ("device", _u32), ("kernel", _u32), ("device_bytes", _u64), ("geometry", _u32),
-                ("row_tile_log2", _u32)]
+                ("row_tile_log2", _u32), ("radix_log2", _u32), ("reserved", _u32)]
 
 
 class Job(ctypes.Structure):
@@ -229,11 +230,12 @@ def _check(st: int, where: str):
 # C ABI, same names
 # --------------------------------------------------------------------------
 def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
-                    kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0) -> int:
+                    kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0,
+                    radix_log2: int = 0) -> int:
     """Create a plan; returns the opaque handle (an int).  Raises NttError."""
     primes = [int(p) for p in primes]
     arr = (_u64 * len(primes))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2)
     out = _vp()
     _check(_lib().ntt_plan_create(ctypes.byref(out), N, arr, len(primes), ctypes.byref(opts)),
            "ntt_plan_create")
@@ -241,11 +243,11 @@ def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_sta
 
 
 def ntt_plan_create_status(N: int, primes, twiddle_mode: int = 0, ot_stages: int = 0, reserved=None,
-                           kernel: int = 0, geometry: int = 0, flags: int = 0):
+                           kernel: int = 0, geometry: int = 0, flags: int = 0, radix_log2: int = 0):
     """Like ntt_plan_create but returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
     arr = (_u64 * max(1, len(primes)))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2)
     if reserved:
         for i, v in enumerate(reserved):
             opts.reserved[i] = v
@@ -429,17 +431,18 @@ class Plan:
     """RAII wrapper over a plan handle."""
 
     def __init__(self, N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
-                 kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0):
+                 kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0,
+                 radix_log2: int = 0):
         self.N = N
         self.primes = [int(p) for p in primes]
         self.L = len(self.primes)
-        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel, geometry, flags)
+        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2)
 
     @classmethod
     def from_opts(cls, N: int, primes, opts: PlanOpts, flags: int | None = None):
         """A plan with the options an autotuner run returned (flags: override)."""
         return cls(N, primes, opts.twiddle_mode, opts.ot_stages, opts.kernel, opts.geometry,
-                   opts.flags if flags is None else flags)
+                   opts.flags if flags is None else flags, opts.radix_log2)
 
     def forward(self, data, batch: int = 1, stream=None):
         ntt_forward(self.handle, data, batch, stream)

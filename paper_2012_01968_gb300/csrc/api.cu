@@ -26,6 +26,7 @@ cudaError_t launch_transform(const LaunchCtx& c, bool fwd)
 {
     if (c.limbs == 0) return cudaSuccess;
     if (c.radix2) return launch_radix2(c, fwd);
+    if (c.high_radix) return launch_high_radix(c, fwd);
     if (c.n <= (u32)SINGLE_PASS_MAX) return launch_single(c, fwd);
     switch (c.n) {
     case 13: return launch_n13(c, fwd);

@@ -157,10 +157,11 @@ private:
 };
 
 // Configurations the autotuner times for N = 2^n, as plan option codes
-// (kernel 1 FUSED, 2 PER_PASS, 3 RADIX2; twiddle 1 TABLE, 2 OT with ot_stages
-// 1 or 2; geometry 0 .. geometries-1).  Two-pass sizes (n >= 13): every
-// geometry x {FUSED, PER_PASS} x {TABLE, OT1, OT2}, then RADIX2 with table
-// twiddles.  One-pass sizes: the one-pass kernel (kernel 0 = AUTO) and RADIX2.
+// (kernel 1 FUSED, 2 PER_PASS, 3 RADIX2, 4 HIGH_RADIX (radix 16); twiddle 1
+// TABLE, 2 OT with ot_stages 1 or 2; geometry 0 .. geometries-1).  Two-pass
+// sizes (n >= 13): every geometry x {FUSED, PER_PASS} x {TABLE, OT1, OT2},
+// then RADIX2 and HIGH_RADIX with table twiddles.  One-pass sizes: the
+// one-pass kernel (kernel 0 = AUTO), RADIX2 and HIGH_RADIX.
 struct TuneCandidate {
     uint32_t kernel, twiddle_mode, ot_stages, geometry;
 };
@@ -170,6 +171,7 @@ inline std::vector<TuneCandidate> tune_candidates(uint32_t n, uint32_t geometrie
     if (n <= single_pass_max) {
         out.push_back(TuneCandidate{0, 1, 0, 0});
         out.push_back(TuneCandidate{3, 1, 0, 0});
+        out.push_back(TuneCandidate{4, 1, 0, 0});
         return out;
     }
     for (uint32_t g = 0; g < geometries; ++g)
@@ -179,6 +181,7 @@ inline std::vector<TuneCandidate> tune_candidates(uint32_t n, uint32_t geometrie
             out.push_back(TuneCandidate{k, 2, 2, g});
         }
     out.push_back(TuneCandidate{3, 1, 0, 0});
+    out.push_back(TuneCandidate{4, 1, 0, 0});
     return out;
 }
 

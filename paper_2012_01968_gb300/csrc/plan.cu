@@ -75,7 +75,8 @@ void build_prime(const ntt_plan& p, uint32_t l, HostTables& h)
     for (uint32_t s = 0; (1u << s) < p.tw_len; ++s) {
         const ntt::StageSlot g = ntt::stage_slot_params(n, p.p1, s);
         for (uint32_t j = 0; j < (1u << s); ++j) {
-            const uint32_t slot = p.kernel == NTT_KERNEL_RADIX2 ? j : ntt::tw_slot(j, g.sl, g.K0, g.k);
+            const bool natural = p.kernel == NTT_KERNEL_RADIX2 || p.kernel == NTT_KERNEL_HIGH_RADIX;
+            const uint32_t slot = natural ? j : ntt::tw_slot(j, g.sl, g.K0, g.k);
             tw[(1u << s) + slot] = make_tw(fwd(nt::brv((1u << s) + j, n)), q);
         }
     }
@@ -194,16 +195,18 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
         if (r) return NTT_ERR_INVALID_ARG;
     if (o.flags & ~NTT_PLAN_L2_TWIDDLES) return NTT_ERR_INVALID_ARG;
     if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
-    if (o.kernel > NTT_KERNEL_RADIX2) return NTT_ERR_INVALID_ARG;
+    if (o.kernel > NTT_KERNEL_HIGH_RADIX) return NTT_ERR_INVALID_ARG;
+    const bool high_radix = o.kernel == NTT_KERNEL_HIGH_RADIX;
+    if (high_radix ? o.radix_log2 > 5 : o.radix_log2 != 0) return NTT_ERR_INVALID_ARG;
     if (o.geometry >= (uint32_t)ntt::kGeometries) return NTT_ERR_INVALID_ARG;
     const uint32_t n = (uint32_t)__builtin_ctz(N);
     const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
-    if (o.geometry && (!two_pass || o.kernel == NTT_KERNEL_RADIX2)) return NTT_ERR_INVALID_ARG;
+    if (o.geometry && (!two_pass || o.kernel == NTT_KERNEL_RADIX2 || high_radix)) return NTT_ERR_INVALID_ARG;
     const uint32_t p1 = two_pass ? (uint32_t)ntt::geometry_of((int)n, (int)o.geometry).p1
                                  : (uint32_t)ntt::split_p1((int)n);
     // AUTO: OT on the last stage for two-pass sizes (measured faster than the
     // table there, and half the last stage's twiddle traffic), table below
-    const bool radix2 = o.kernel == NTT_KERNEL_RADIX2;
+    const bool radix2 = o.kernel == NTT_KERNEL_RADIX2 || high_radix;   // global-memory organisations
     if (radix2 && o.twiddle_mode == NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;   // table twiddles only
     uint32_t mode = o.twiddle_mode;
     if (mode == NTT_TWIDDLE_AUTO) mode = two_pass && !radix2 ? NTT_TWIDDLE_OT : NTT_TWIDDLE_TABLE;
@@ -231,7 +234,11 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     p->passes = two_pass ? 2 : 1;
     p->twiddle_mode = mode;
     p->ot_stages = ots;
-    p->kernel = radix2 ? NTT_KERNEL_RADIX2 : o.kernel == NTT_KERNEL_PER_PASS ? NTT_KERNEL_PER_PASS : NTT_KERNEL_FUSED;
+    p->kernel = high_radix                         ? NTT_KERNEL_HIGH_RADIX
+                : radix2                           ? NTT_KERNEL_RADIX2
+                : o.kernel == NTT_KERNEL_PER_PASS ? NTT_KERNEL_PER_PASS
+                                                   : NTT_KERNEL_FUSED;
+    p->radix_log2 = high_radix ? (o.radix_log2 ? o.radix_log2 : 4u) : 0u;
     p->geom = o.geometry;
     p->flags = o.flags;
     cudaError_t ce = cudaGetDevice(&p->device);
@@ -315,6 +322,7 @@ extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
     info->device_bytes = p->device_bytes;
     info->geometry = p->geom;
     info->row_tile_log2 = p->passes == 2 ? (uint32_t)ntt::geometry_of((int)p->n, (int)p->geom).logc_r : 0;
+    info->radix_log2 = p->radix_log2;
     return NTT_OK;
 }
 

@@ -82,6 +82,7 @@ struct LaunchCtx {
     u32 ots;                 // OT stages (0 = table mode)
     u32 separate_passes;     // 1: one launch per pass instead of the fused kernel
     u32 radix2;              // 1: one launch per radix-2 stage (natural-order table)
+    u32 high_radix;          // k > 0: one launch per k stages in registers (natural-order table)
     u32* status;             // persistent device status word of the plan
     u32* work;               // fused kernel's work area (zero between launches)
     u32 work_limbs;          // limbs the work area covers (fused_work_words(work_limbs) words)
@@ -135,6 +136,7 @@ cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a,
 // per-n launchers (one translation unit each, compiled in parallel)
 cudaError_t launch_single(const LaunchCtx& c, bool fwd);
 cudaError_t launch_radix2(const LaunchCtx& c, bool fwd);
+cudaError_t launch_high_radix(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n13(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n14(const LaunchCtx& c, bool fwd);
 cudaError_t launch_n15(const LaunchCtx& c, bool fwd);
@@ -165,6 +167,7 @@ struct ntt_plan {
     uint32_t kernel = 0;                  // NTT_KERNEL_*
     uint32_t geom = 0;                    // geometry index (two-pass sizes)
     uint32_t flags = 0;                   // NTT_PLAN_* bits
+    uint32_t radix_log2 = 0;              // HIGH_RADIX: stages per launch
     float l2_hit = 0.f;                   // persisting fraction of the twiddle window
     uint32_t* d_status = nullptr;         // device status word (kernel error bits)
     uint32_t* d_work = nullptr;           // fused kernel's work area: fused_work_words(work_limbs) words
@@ -201,6 +204,7 @@ struct ntt_plan {
         c.ots = twiddle_mode == NTT_TWIDDLE_OT ? ot_stages : 0;
         c.separate_passes = kernel == NTT_KERNEL_PER_PASS ? 1u : 0u;
         c.radix2 = kernel == NTT_KERNEL_RADIX2 ? 1u : 0u;
+        c.high_radix = kernel == NTT_KERNEL_HIGH_RADIX ? radix_log2 : 0u;
         c.status = d_status;
         c.work = d_work;
         c.work_limbs = work_limbs;

@@ -362,3 +362,52 @@ def fused_geometry(n):
     lr = logc_rows(p2)
     UC, UR = (1 << p2) // 16, (1 << p1) >> lr
     return UC, UR
+
+
+def high_radix_transform(a, q, psi, n, k, fwd):
+    """The register-based high-radix organisation's index maps (one launch per
+    group of k stages; item = 2^k elements spaced t apart; natural-order table),
+    with exact modular butterflies."""
+    N = 1 << n
+    pw = [1] * N
+    for e in range(1, N):
+        pw[e] = pw[e - 1] * psi % q
+    tw = [pw[brv(i, n)] for i in range(N)]          # Psi[i] = psi^brv(i), natural order
+    ninv = pow(N, q - 2, q)
+    d = [int(v) for v in a]
+    groups = (n + k - 1) // k
+    order = range(groups) if fwd else range(groups - 1, -1, -1)
+    for g in order:
+        s0 = g * k
+        kk = min(k, n - s0)
+        nb = n - s0 - kk
+        for m in range(N >> kk):
+            b, j = m >> nb, m & ((1 << nb) - 1)
+            base = (b << (n - s0)) + j
+            idx = [base + (i << nb) for i in range(1 << kk)]
+            x = [d[i] for i in idx]
+            rs = range(kk) if fwd else range(kk - 1, -1, -1)
+            for r in rs:
+                h = 1 << (kk - 1 - r)
+                s = s0 + r
+                for grp in range(1 << r):
+                    for i in range(h):
+                        lo, hi = grp * 2 * h + i, grp * 2 * h + i + h
+                        if fwd:
+                            w = tw[(1 << s) + (b << r) + grp]
+                            v = x[hi] * w % q
+                            x[lo], x[hi] = (x[lo] + v) % q, (x[lo] - v) % q
+                        elif s == 0:
+                            # stage 0 with N^{-1} folded in: (x + y) / N and (y - x) Psi[1] / N
+                            u, v = x[lo], x[hi]
+                            x[lo] = (u + v) * ninv % q
+                            x[hi] = (v - u) * tw[1] % q * ninv % q
+                        else:
+                            jj = (b << r) + grp
+                            w = tw[(2 << s) - 1 - jj]      # -Psi^{-1}[2^s + jj]
+                            u, v = x[lo], x[hi]
+                            x[lo] = (u + v) % q
+                            x[hi] = (v - u) * w % q
+            for i, v in zip(idx, x):
+                d[i] = v
+    return d

@@ -63,6 +63,11 @@ BIG = I.prime_chain(3, 1 << 18)
     (1 << 12, BIG[:1], {"geometry": 1}, G.NTT_ERR_INVALID_ARG),                # one-pass size
     (1 << 16, BIG[:1], {"geometry": 2, "kernel": G.NTT_KERNEL_RADIX2}, G.NTT_ERR_INVALID_ARG),
     (1 << 16, BIG[:1], {"flags": 2}, G.NTT_ERR_INVALID_ARG),                   # unknown flag bit
+    (1 << 16, BIG[:1], {"kernel": 5}, G.NTT_ERR_INVALID_ARG),                  # no such organisation
+    (1 << 16, BIG[:1], {"kernel": G.NTT_KERNEL_HIGH_RADIX, "radix_log2": 6}, G.NTT_ERR_INVALID_ARG),
+    (1 << 16, BIG[:1], {"radix_log2": 4}, G.NTT_ERR_INVALID_ARG),              # radix only for HIGH_RADIX
+    (1 << 16, BIG[:1], {"kernel": G.NTT_KERNEL_HIGH_RADIX, "twiddle_mode": G.NTT_TWIDDLE_OT}, G.NTT_ERR_INVALID_ARG),
+    (1 << 16, BIG[:1], {"kernel": G.NTT_KERNEL_HIGH_RADIX, "geometry": 1}, G.NTT_ERR_INVALID_ARG),
 ])
 def test_plan_create_rejects(lib, N, primes, kw, want):
     st, h = G.ntt_plan_create_status(N, primes, **kw)

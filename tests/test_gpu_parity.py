@@ -359,6 +359,33 @@ def test_radix2_organisation(orc, n):
         G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_RADIX2)
 
 
+@pytest.mark.parametrize("n", list(range(1, 18)))
+def test_high_radix_organisation(orc, n):
+    """One launch per 2^k-point group of stages in registers (the paper's
+    register-based high radix), every radix 2^1 .. 2^5, including the short
+    last group when k does not divide log2 N."""
+    N = 1 << n
+    primes = I.prime_chain(3, 2 * N)
+    data = I.batch_uniform(180 + n, 2, primes, N)
+    y = I.batch_uniform(190 + n, 2, primes, N)
+    want_f, want_i = oracle_fwd(orc, data, primes), oracle_inv(orc, y, primes)
+    for k in (1, 2, 3, 4, 5):
+        with G.Plan(N, primes, G.NTT_TWIDDLE_AUTO, 0, G.NTT_KERNEL_HIGH_RADIX, radix_log2=k) as p:
+            info = p.info()
+            assert (info.kernel, info.radix_log2, info.twiddle_mode) == (G.NTT_KERNEL_HIGH_RADIX, k,
+                                                                           G.NTT_TWIDDLE_TABLE)
+            d = dev(data)
+            p.forward(d, 2)
+            assert np.array_equal(host(d), want_f), f"forward n={n} radix 2^{k}"
+            p.inverse(d, 2)
+            assert np.array_equal(host(d), data), f"roundtrip n={n} radix 2^{k}"
+            dy = dev(y)
+            p.inverse(dy, 2)
+            assert np.array_equal(host(dy), want_i), f"inverse n={n} radix 2^{k}"
+    with G.Plan(N, primes, G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_HIGH_RADIX) as p:
+        assert p.info().radix_log2 == 4                   # the default: radix 16
+
+
 def test_bench_launch_configuration(orc):
     """The bench's configuration at full size: two plans on two streams with
     independent C2 polynomials in flight together, forward then inverse each;

@@ -108,7 +108,7 @@ def test_autotune_reports_and_picks_the_fastest(orc, n, L, batch):
     N = 1 << n
     primes = I.prime_chain(L, 2 * N)
     best, entries = G.ntt_autotune(N, primes, batch, reps=3)
-    assert len(entries) == (2 if n <= 12 else 19)
+    assert len(entries) == (3 if n <= 12 else 20)
     assert all(e.status == G.NTT_OK and e.forward_us > 0 and e.inverse_us > 0 for e in entries)
     tot = [e.forward_us + e.inverse_us for e in entries]
     k = int(np.argmin(tot))

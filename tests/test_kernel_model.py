@@ -139,3 +139,15 @@ def test_geometry_limits(n, geometry):
     assert (1 << (lr + p2)) <= 4096 and lr <= p1
     UC, UR = (1 << p2) // 16, (1 << p1) >> lr
     assert UC * 16 * (1 << p1) == 1 << n and UR * (1 << lr) * (1 << p2) == 1 << n
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 7, 10])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_high_radix_index_maps(orc, n, k):
+    """The high-radix organisation's items and twiddle indices give the
+    oracle's transform for every radix, including a short last group."""
+    N, q, a = _case(n, 400 + n + k)
+    psi = orc.psi(q, N)
+    got = KM.high_radix_transform(a, q, psi, n, k, True)
+    assert got == [int(v) for v in orc.ntt_radix2(a, q)]
+    assert KM.high_radix_transform(got, q, psi, n, k, False) == a
