@@ -206,6 +206,22 @@ ntt_status ntt_execute_host(const ntt_plan* plan, const uint64_t* host_in, uint6
                             uint32_t batch, uint32_t ops, void* stream);
 
 /*
+ * Asynchronous form of ntt_execute_host: enqueues the same copies and
+ * transforms (in two segments) and returns without waiting; the work starts
+ * after everything enqueued earlier on `stream`, and `stream` is ordered after
+ * the last copy-out, so host_out holds the result once `stream` has reached
+ * this point (e.g. after cudaStreamSynchronize(stream)).  host_in and
+ * host_out must stay valid, and host_in unchanged, until then.  The plan has
+ * two staging buffers, used by alternate calls: calls issued on two
+ * alternating streams overlap (one call's copy-in runs while the previous
+ * call is transformed and copied out), while calls on one stream follow one
+ * another.  Errors as ntt_execute_host; on an error the plan's host streams
+ * are drained before returning.
+ */
+ntt_status ntt_execute_host_async(const ntt_plan* plan, const uint64_t* host_in, uint64_t* host_out,
+                                  uint32_t batch, uint32_t ops, void* stream);
+
+/*
  * No-allocation transform.  The paper has no counterpart: this is a library
  * interface for callers that may not allocate device memory while they run,
  * e.g. a serving loop whose device memory is fully reserved up front, code

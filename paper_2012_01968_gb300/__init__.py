@@ -136,8 +136,9 @@ def _lib():
             L.ntt_mul_negacyclic.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
             L.ntt_mul_pointwise.restype = S
             L.ntt_mul_pointwise.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
-            L.ntt_execute_host.restype = S
-            L.ntt_execute_host.argtypes = [_vp, _vp, _vp, _u32, _u32, _vp]
+            for f in ("ntt_execute_host", "ntt_execute_host_async"):
+                getattr(L, f).restype = S
+                getattr(L, f).argtypes = [_vp, _vp, _vp, _u32, _u32, _vp]
             L.ntt_transform_noalloc.restype = S
             L.ntt_transform_noalloc.argtypes = [_vp, _vp, _u32, _u32, _u32, _vp]
             L.ntt_batch_create.restype = S
@@ -290,16 +291,25 @@ def ntt_mul_negacyclic(plan: int, a, b, c, batch: int, stream=None) -> None:
            "ntt_mul_negacyclic")
 
 
+def _host_ptr(x) -> int:
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x)
+
+
 def ntt_execute_host(plan: int, host_in, host_out, batch: int, ops: int, stream=None) -> None:
     """host_in / host_out: numpy uint64 arrays or CPU torch tensors (pinned for speed)."""
-    def hp(x):
-        if hasattr(x, "ctypes"):
-            return x.ctypes.data
-        if hasattr(x, "data_ptr"):
-            return int(x.data_ptr())
-        return int(x)
-    _check(_lib().ntt_execute_host(plan, hp(host_in), hp(host_out), batch, ops, _stream(stream)),
+    _check(_lib().ntt_execute_host(plan, _host_ptr(host_in), _host_ptr(host_out), batch, ops, _stream(stream)),
            "ntt_execute_host")
+
+
+def ntt_execute_host_async(plan: int, host_in, host_out, batch: int, ops: int, stream=None) -> None:
+    """As ntt_execute_host without waiting: `stream` is ordered after the result
+    lands in host_out; keep both buffers alive (and host_in unchanged) until then."""
+    _check(_lib().ntt_execute_host_async(plan, _host_ptr(host_in), _host_ptr(host_out), batch, ops,
+                                         _stream(stream)), "ntt_execute_host_async")
 
 
 def ntt_transform_noalloc(plan: int, data, batch: int, levels: int, op: int, stream=None) -> None:

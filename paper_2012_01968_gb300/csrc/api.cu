@@ -191,8 +191,11 @@ ntt_status ntt_mul_negacyclic(const ntt_plan* p, uint64_t* a, uint64_t* b, uint6
     return to_status(e);
 }
 
-ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_t* host_out, uint32_t batch,
-                            uint32_t ops, void* stream)
+// Enqueue the host-buffer pipeline of ntt_execute_host / _async; the
+// caller's stream waits for the last copy-out.  `wait` drains the plan's host
+// streams before returning (the synchronous call).
+static ntt_status host_pipeline(const ntt_plan* cp, const uint64_t* host_in, uint64_t* host_out, uint32_t batch,
+                                uint32_t ops, void* stream, bool wait)
 {
     if (!cp || !host_in || !host_out || batch == 0) return NTT_ERR_INVALID_ARG;
     if (ops == 0 || (ops & ~(uint32_t)(NTT_OP_FORWARD | NTT_OP_INVERSE))) return NTT_ERR_INVALID_ARG;
@@ -209,9 +212,12 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
     // streams as soon as their copy has landed, and copied out on another
     // stream as soon as their transforms are done, so the two copy directions
     // and the transforms overlap.
+    // (an asynchronous call takes fewer, larger segments: its copies overlap
+    // the neighbouring calls' work, and larger launches run more efficiently)
     using Seg = ntt::host::Segment;
     constexpr uint32_t kSegments = ntt_plan::kHostSegments;
-    const std::vector<Seg> segs = ntt::host::split_segments(batch, L, kSegments);
+    const std::vector<Seg> segs =
+        ntt::host::split_segments(batch, L, wait ? kSegments : (uint32_t)ntt_plan::kHostSegmentsAsync);
     if (segs.size() > kSegments) return NTT_ERR_INVALID_ARG;      // cannot happen: one event pair per segment
     uint32_t seg_max = 0;
     for (const Seg& g : segs) seg_max = g.count > seg_max ? g.count : seg_max;
@@ -228,21 +234,35 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
     mk_stream(p->h_out);
     for (int k = 0; k < ntt_plan::kHostCompute; ++k) mk_stream(p->h_comp[k]);
     mk_event(p->hfork);
+    mk_event(p->h_join);
     for (uint32_t k = 0; k < kSegments; ++k) {
         mk_event(p->h_loaded[k]);
         mk_event(p->h_done[k]);
+        for (int b = 0; b < ntt_plan::kHostBuffers; ++b) mk_event(p->h_out_done[b][k]);
     }
     if (e != cudaSuccess) return to_status(e);
+    auto drain = [&]() {
+        cudaError_t se = cudaStreamSynchronize(p->h_in);
+        for (int k = 0; k < ntt_plan::kHostCompute; ++k) {
+            const cudaError_t sk = cudaStreamSynchronize(p->h_comp[k]);
+            if (se == cudaSuccess) se = sk;
+        }
+        const cudaError_t so = cudaStreamSynchronize(p->h_out);
+        return se == cudaSuccess ? so : se;
+    };
     if (p->stage_bytes < bytes || p->hwork_limbs < seg_max) {
-        // the call is synchronous, so nothing of this plan's host path is in flight
+        // earlier asynchronous calls may still use the staging: drain first
+        e = drain();
+        if (e != cudaSuccess) return to_status(e);
         cudaFree(p->d_stage);
         cudaFree(p->d_hwork);
         p->d_stage = nullptr;
         p->d_hwork = nullptr;
         p->stage_bytes = 0;
         p->hwork_limbs = 0;
+        for (int b = 0; b < ntt_plan::kHostBuffers; ++b) p->h_prev_segs[b] = 0;
         const size_t wwords = ntt::fused_work_words(seg_max) * ntt_plan::kHostCompute;
-        e = cudaMalloc(&p->d_stage, bytes);
+        e = cudaMalloc(&p->d_stage, bytes * ntt_plan::kHostBuffers);
         if (e == cudaSuccess) e = cudaMalloc(&p->d_hwork, wwords * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemset(p->d_hwork, 0, wwords * sizeof(uint32_t));
         if (e != cudaSuccess) {
@@ -253,12 +273,23 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
         p->hwork_limbs = seg_max;
     }
 
+    // this call's staging buffer (alternate calls use alternate buffers)
+    const uint32_t sb = p->h_next;
+    p->h_next = (sb + 1) % ntt_plan::kHostBuffers;
+    uint64_t* const stage = p->d_stage + (p->stage_bytes / sizeof(uint64_t)) * sb;
+
     // after the caller's earlier work on `stream`
     e = cudaEventRecord(p->hfork, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->h_in, p->hfork, 0);
     for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
         const size_t off = (size_t)segs[i].first * N, nbytes = (size_t)segs[i].count * N * sizeof(uint64_t);
-        e = cudaMemcpyAsync(p->d_stage + off, host_in + off, nbytes, cudaMemcpyHostToDevice, p->h_in);
+        // the staging range must have been copied out by the buffer's previous call
+        for (uint32_t j = 0; j < p->h_prev_segs[sb] && e == cudaSuccess; ++j) {
+            const uint32_t a0 = p->h_prev_first[sb][j], a1 = a0 + p->h_prev_count[sb][j];
+            if (a0 < segs[i].first + segs[i].count && segs[i].first < a1)
+                e = cudaStreamWaitEvent(p->h_in, p->h_out_done[sb][j], 0);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stage + off, host_in + off, nbytes, cudaMemcpyHostToDevice, p->h_in);
         if (e == cudaSuccess) e = cudaEventRecord(p->h_loaded[i], p->h_in);
     }
     for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
@@ -268,7 +299,7 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
         const size_t off = (size_t)sg.first * N;
         e = cudaStreamWaitEvent(s, p->h_loaded[i], 0);
         if (e != cudaSuccess) break;
-        ntt::LaunchCtx c = p->ctx_range(p->d_stage + off, sg.count, sg.lview, sg.prime0, s);
+        ntt::LaunchCtx c = p->ctx_range(stage + off, sg.count, sg.lview, sg.prime0, s);
         c.work = p->d_hwork + ntt::fused_work_words(p->hwork_limbs) * (size_t)k;
         c.work_limbs = p->hwork_limbs;
         if (ops & NTT_OP_FORWARD) e = ntt::launch_transform(c, true);
@@ -278,17 +309,35 @@ ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_
     for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {
         const size_t off = (size_t)segs[i].first * N, nbytes = (size_t)segs[i].count * N * sizeof(uint64_t);
         e = cudaStreamWaitEvent(p->h_out, p->h_done[i], 0);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out + off, p->d_stage + off, nbytes, cudaMemcpyDeviceToHost, p->h_out);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out + off, stage + off, nbytes, cudaMemcpyDeviceToHost, p->h_out);
+        if (e == cudaSuccess) e = cudaEventRecord(p->h_out_done[sb][i], p->h_out);
     }
+    if (e == cudaSuccess) {
+        for (size_t i = 0; i < segs.size(); ++i) {
+            p->h_prev_first[sb][i] = segs[i].first;
+            p->h_prev_count[sb][i] = segs[i].count;
+        }
+        p->h_prev_segs[sb] = (uint32_t)segs.size();
+        e = cudaEventRecord(p->h_join, p->h_out);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, p->h_join, 0);
+    }
+    if (!wait && e == cudaSuccess) return NTT_OK;
     // drain every stream, also after an error, before the staging can be reused
-    cudaError_t se = cudaStreamSynchronize(p->h_in);
-    for (int k = 0; k < ntt_plan::kHostCompute; ++k) {
-        const cudaError_t sk = cudaStreamSynchronize(p->h_comp[k]);
-        if (se == cudaSuccess) se = sk;
-    }
-    const cudaError_t so = cudaStreamSynchronize(p->h_out);
-    if (se == cudaSuccess) se = so;
+    const cudaError_t se = drain();
+    if (e != cudaSuccess) p->h_prev_segs[sb] = 0;
     return to_status(e != cudaSuccess ? e : se);
+}
+
+ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_t* host_out, uint32_t batch,
+                            uint32_t ops, void* stream)
+{
+    return host_pipeline(cp, host_in, host_out, batch, ops, stream, true);
+}
+
+ntt_status ntt_execute_host_async(const ntt_plan* cp, const uint64_t* host_in, uint64_t* host_out, uint32_t batch,
+                                  uint32_t ops, void* stream)
+{
+    return host_pipeline(cp, host_in, host_out, batch, ops, stream, false);
 }
 
 // Test hook (not part of the public interface): the forward transform with

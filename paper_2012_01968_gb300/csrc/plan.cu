@@ -145,9 +145,12 @@ void free_plan(ntt_plan* p)
     for (int k = 0; k < ntt_plan::kHostCompute; ++k)
         if (p->h_comp[k]) cudaStreamDestroy(p->h_comp[k]);
     if (p->hfork) cudaEventDestroy(p->hfork);
+    if (p->h_join) cudaEventDestroy(p->h_join);
     for (int k = 0; k < ntt_plan::kHostSegments; ++k) {
         if (p->h_loaded[k]) cudaEventDestroy(p->h_loaded[k]);
         if (p->h_done[k]) cudaEventDestroy(p->h_done[k]);
+        for (int b = 0; b < ntt_plan::kHostBuffers; ++b)
+            if (p->h_out_done[b][k]) cudaEventDestroy(p->h_out_done[b][k]);
     }
     cudaFree(p->d_status);
     cudaFree(p->d_work);

@@ -173,16 +173,26 @@ struct ntt_plan {
     uint32_t* d_work = nullptr;           // fused kernel's work area: fused_work_words(work_limbs) words
     uint32_t work_limbs = 0;
     std::mutex work_mu;
-    // staging for ntt_execute_host: device copy of the data; a copy-in
-    // stream, a copy-out stream and kHostCompute compute streams (with one
-    // work area each), ordered per segment by events
+    // staging for ntt_execute_host: device copies of the data, two buffers
+    // used by alternate calls; a copy-in stream, a copy-out stream and
+    // kHostCompute compute streams (with one work area each), ordered per
+    // segment by events
     static constexpr int kHostCompute = 2;
-    static constexpr int kHostSegments = 6;
+    static constexpr int kHostBuffers = 2;
+    static constexpr int kHostSegments = 6;       // segments of a synchronous call
+    static constexpr int kHostSegmentsAsync = 2;  // of an asynchronous call (calls overlap instead)
     std::mutex stage_mu;
-    uint64_t* d_stage = nullptr;
-    size_t stage_bytes = 0;
+    uint64_t* d_stage = nullptr;          // kHostBuffers x stage_bytes
+    size_t stage_bytes = 0;               // per buffer
+    uint32_t h_next = 0;                  // buffer of the next call
     cudaStream_t h_in = nullptr, h_out = nullptr, h_comp[kHostCompute] = {};
     cudaEvent_t hfork = nullptr, h_loaded[kHostSegments] = {}, h_done[kHostSegments] = {};
+    // copy-out of each segment of the latest call on each buffer, with its
+    // staging range [first, first + count) in limbs: a later call's copy-in of
+    // an overlapping range of the same buffer waits for it
+    cudaEvent_t h_out_done[kHostBuffers][kHostSegments] = {}, h_join = nullptr;
+    uint32_t h_prev_first[kHostBuffers][kHostSegments] = {}, h_prev_count[kHostBuffers][kHostSegments] = {};
+    uint32_t h_prev_segs[kHostBuffers] = {};
     uint32_t* d_hwork = nullptr;
     uint32_t hwork_limbs = 0;             // per compute stream
 

@@ -206,6 +206,34 @@ def test_execute_host_roundtrip(orc):
         assert np.array_equal(both, data)
 
 
+def test_execute_host_async_chains(orc):
+    """Asynchronous host-buffer calls overlap on one plan: several independent
+    calls in flight, then an in-place forward followed by an in-place inverse
+    on the same buffer; every result is the oracle's."""
+    w = I.workload_c2()
+    primes = w.primes[:7]
+    datas = [I.batch_uniform(w.seed + k, 2, primes, w.N) for k in range(3)]
+    s = torch.cuda.Stream()
+    with G.Plan(w.N, primes) as p:
+        ins = [torch.from_numpy(d.view(np.int64).copy()).pin_memory() for d in datas]
+        outs = [torch.empty_like(x).pin_memory() for x in ins]
+        alt = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for k, (x, y) in enumerate(zip(ins, outs)):
+            G.ntt_execute_host_async(p.handle, x, y, 2, G.NTT_OP_FORWARD, alt[k % 2])    # calls overlap
+        torch.cuda.synchronize()
+        for d, y in zip(datas, outs):
+            assert np.array_equal(y.numpy().view(np.uint64), oracle_fwd(orc, d, primes))
+        buf = ins[0]
+        G.ntt_execute_host_async(p.handle, buf, buf, 2, G.NTT_OP_FORWARD, s)
+        G.ntt_execute_host_async(p.handle, buf, buf, 2, G.NTT_OP_INVERSE, s)
+        s.synchronize()
+        assert np.array_equal(buf.numpy().view(np.uint64), datas[0])
+        # another batch size: other segments, each waiting on the overlapping ones of the previous call
+        G.ntt_execute_host_async(p.handle, ins[1][:1], outs[1][:1], 1, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE, s)
+        s.synchronize()
+        assert np.array_equal(outs[1][:1].numpy().view(np.uint64), datas[1][:1])
+
+
 def test_plan_query_and_psi(orc):
     w = I.workload_c2()
     with G.Plan(w.N, w.primes[:3], G.NTT_TWIDDLE_OT, 2) as p:
