@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-peak-measure", action="store_true",
                     help="skip the live butterfly-rate measurement (for profiling runs)")
     ap.add_argument("--no-ablation", action="store_true", help="skip the N sweep of kernel organisations")
+    ap.add_argument("--ablation-only", action="store_true",
+                    help="run only the kernel-organisation sweep and print it (for profiling its launches)")
+    ap.add_argument("--ablation-reps", type=int, default=40)
     ap.add_argument("--no-tune", action="store_true",
                     help="plans with the fixed default options instead of the autotuner's choice")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -479,7 +482,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None):
         del ring
 
 
-def paper_ablation(G, torch, reps=40):
+def paper_ablation(G, torch, reps=40, sizes=(14, 15, 16, 17)):
     """The structure of the paper's N sweep (21 limbs, forward transform,
     log N = 14..17) on this GPU: the radix-2 launch-per-stage organisation
     the paper starts from, its register-based high-radix step (radix 2^2 ..
@@ -501,7 +504,7 @@ def paper_ablation(G, torch, reps=40):
     gen = torch.Generator(device="cuda")
     gen.manual_seed(21)
     out = {"limbs": 21, "unit": "us per forward transform of all 21 limbs (one stream, events)"}
-    for n in (14, 15, 16, 17):
+    for n in sizes:
         N = 1 << n
         words = 21 * N
         nbuf = max(2, -(-2 * L2_BYTES // (words * 8)) + 1)
@@ -511,7 +514,7 @@ def paper_ablation(G, torch, reps=40):
         for name, mode, ots, kern, *radix in configs:
             with G.Plan(N, chain, mode, ots, kern, radix_log2=radix[0] if radix else 0) as p:
                 ptr = [pool[i * words:(i + 1) * words].data_ptr() for i in range(nbuf)]
-                for i in range(5):
+                for i in range(min(5, reps)):
                     _ok(G, lib.ntt_forward(p.handle, ptr[i % nbuf], 1, s.cuda_stream), name)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -739,6 +742,12 @@ def main():
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
     G.lib()
+    if args.ablation_only:
+        if rank == 0:
+            print(json.dumps({"paper_ablation": paper_ablation(G, torch, args.ablation_reps, (16, 17))}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     N, primes, L = w.N, w.primes, len(w.primes)
     mode = {"auto": (G.NTT_TWIDDLE_AUTO, 0), "table": (G.NTT_TWIDDLE_TABLE, 0),
