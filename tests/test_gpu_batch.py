@@ -31,11 +31,20 @@ def _job_data(w, job, chain):
     return I.batch_uniform(w.seed, 1, chain[:job.L], job.N, first_poly=job.poly)
 
 
-def test_uneven_batch_c4_against_oracle(orc, chain):
+# the configurations the autotuner picks for these sizes on GB300 (fused kernel,
+# table twiddles; geometry per size), as the bench's tuned C4 / C5 legs use them
+TUNED_C4 = {14: (G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_FUSED, 1), 15: (G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_FUSED, 2),
+            16: (G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_FUSED, 0), 17: (G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_FUSED, 1)}
+
+
+@pytest.mark.parametrize("options", ["default", "tuned"])
+def test_uneven_batch_c4_against_oracle(orc, chain, options):
     """The 96-job uneven workload (N in 2^14..2^17, L in [1, 60], mixed
-    directions) in one submission, every job against the oracle."""
+    directions) in one submission, every job against the oracle; with the
+    default plan options and with the tuned ones."""
     w = I.workload_c4()
-    plans = {n: G.Plan(1 << n, chain) for n in range(14, 18)}
+    plans = {n: (G.Plan(1 << n, chain, *TUNED_C4[n]) if options == "tuned" else G.Plan(1 << n, chain))
+             for n in range(14, 18)}
     try:
         datas = [_job_data(w, j, chain) for j in w.jobs]
         devs = [dev(d) for d in datas]
