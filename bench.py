@@ -19,6 +19,7 @@ Multi-GPU (torchrun): every rank transforms its own polynomials on its own GPU
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -435,6 +436,16 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None):
     limbs_total = sum(r.L for r in base)
     try:
         def run(rate):
+            # the load generator must not pause: no Python garbage collection
+            # while requests arrive (a collection would release a burst late)
+            gc.collect()
+            gc.disable()
+            try:
+                return run_load(rate)
+            finally:
+                gc.enable()
+
+        def run_load(rate):
             with G.Server(budget_gb << 30, max_batch_jobs=32, slots=3) as srv:
                 inflight = collections.deque()          # (ticket, start, end) in ring order
                 tickets = []
