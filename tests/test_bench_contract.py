@@ -1,0 +1,60 @@
+"""bench.py's output contract: one JSON line with the keys and types the
+measurement needs, for the reference arm (the oracle, CPU) and for the GPU
+arm (a short run)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(args, timeout):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, capture_output=True,
+                         text=True, timeout=timeout)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout[-2000:]
+    return json.loads(lines[0])
+
+
+def _common(d):
+    for k, t in (("metric", str), ("value", float), ("unit", str), ("n_gpus", int), ("steps", int),
+                 ("warmup", int), ("ms_per_step", float), ("higher_is_better", bool), ("scaling", str),
+                 ("dtype", str), ("data", str), ("config", dict)):
+        assert isinstance(d[k], t), k
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["scaling"] == "weak"
+    assert d["config"]["workload"] == "c2_n65536_l45_fwd_inv"
+    assert "vs_baseline" in d and d["vs_baseline"] is None
+
+
+def test_reference_arm_line():
+    d = _run(["--impl", "reference", "--steps", "1", "--warmup", "0"], 600)
+    _common(d)
+    assert d["impl"] == "reference"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = _run(["--steps", "40", "--warmup", "3", "--no-cpu-baseline", "--no-batch-compare", "--no-serve",
+              "--no-ablation", "--no-peak-measure", "--e2e-steps", "4", "--launch-steps", "5"], 900)
+    _common(d)
+    r = d["roofline"]
+    assert r["bound"] == "alu" and r["achieved"] > 0 and r["peak"] > 0
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
+    h = d["roofline_hbm"]
+    assert h["bound"] == "hbm" and h["unit"] == "GB/s" and 0 < h["frac"] < 1
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 45 * 65536 * 8
+    per = 1 if d["plan"]["kernel"] == "fused" else d["plan"]["passes"]
+    assert d["gpu_launches"] == 2 * per * d["steps"]
+    assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
