@@ -624,8 +624,8 @@ def word_size(G, torch, N, primes64, seed, reps=100):
     """Sec. IV's word-size question: one modulus built from primes below 2^60
     in 64-bit words, or from 28-bit primes in 32-bit words (about twice as
     many limbs, at least as many bits), forward + inverse per step on one
-    stream.  Both with table twiddles and one launch per pass; the 64-bit
-    side also with its default (fused) kernel."""
+    stream.  Each word size with one launch per pass (table twiddles) and with
+    the fused kernel (the 64-bit default, OT1; the 32-bit one, table)."""
     import math
     bits64 = sum(math.log2(q) for q in primes64)
     cand = I.prime_chain(4 * len(primes64), 2 * N, below=1 << 28)
@@ -669,16 +669,19 @@ def word_size(G, torch, N, primes64, seed, reps=100):
     src32 = torch.from_numpy(h32.astype(np.uint32).view(np.int32).copy()).cuda()
     nb32 = max(2, -(-2 * L2_BYTES // (src32.numel() * 4)) + 1)
     b32 = [src32.clone() for _ in range(nb32)]
-    with G.Plan32(N, p32) as p:
-        def step32(i):
-            b = b32[i % nb32].data_ptr()
-            _ok(G, lib.ntt_forward32(p.handle, b, 1, s.cuda_stream), "u32 forward")
-            _ok(G, lib.ntt_inverse32(p.handle, b, 1, s.cuda_stream), "u32 inverse")
-        out["u32_per_pass_us"] = timed(step32)
+    for name, kern in (("u32_per_pass_us", G.NTT_KERNEL_PER_PASS), ("u32_fused_us", G.NTT_KERNEL_FUSED)):
+        with G.Plan32(N, p32, kern) as p:
+            def step32(i):
+                b = b32[i % nb32].data_ptr()
+                _ok(G, lib.ntt_forward32(p.handle, b, 1, s.cuda_stream), "u32 forward")
+                _ok(G, lib.ntt_inverse32(p.handle, b, 1, s.cuda_stream), "u32 inverse")
+            out[name] = timed(step32)
+            if p.device_status() != 0:
+                raise RuntimeError("32-bit plan device status reports a failed bounded wait")
     if not all(torch.equal(b, src32) for b in b32):
         raise RuntimeError("32-bit word-size round trip mismatch")
     out["u32_vs_u64_per_pass"] = out["u64_per_pass_us"] / out["u32_per_pass_us"]
-    out["u32_vs_u64_fused"] = out["u64_fused_us"] / out["u32_per_pass_us"]
+    out["u32_fused_vs_u64_fused"] = out["u64_fused_us"] / out["u32_fused_us"]
     return out
 
 

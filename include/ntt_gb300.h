@@ -418,18 +418,20 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t* primes, uint32_t L, uint32_t
  * over primes q < 2^28 with q = 1 mod 2N, residues held in uint32_t.  The
  * transform is the same negacyclic NTT as ntt_forward / ntt_inverse (same psi
  * rule: psi = g^{(q-1)/2N} for the smallest generator g of Z_q^*), with table
- * twiddles and one launch per pass.
+ * twiddles: for N >= 2^13 the fused two-pass kernel (NTT_KERNEL_FUSED, the
+ * default) or one launch per pass (NTT_KERNEL_PER_PASS); one pass below.
  */
 typedef struct ntt_plan32 ntt_plan32;
 
 /*
  * Create a 32-bit plan.  N as for ntt_plan_create; primes: host array of L
- * primes with q = 1 mod 2N and q < 2^28 (copied); 1 <= L <= 4096.  Device
- * tables of 8 * N * L bytes, created on the current CUDA device.  Errors:
- * NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME, NTT_ERR_OOM, NTT_ERR_CUDA; *out is
- * left untouched on error.
+ * primes with q = 1 mod 2N and q < 2^28 (copied); 1 <= L <= 4096; kernel:
+ * NTT_KERNEL_AUTO (= FUSED), NTT_KERNEL_FUSED or NTT_KERNEL_PER_PASS.  Device
+ * tables of 8 * N * L bytes and a work area, created on the current CUDA
+ * device.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME, NTT_ERR_OOM,
+ * NTT_ERR_CUDA; *out is left untouched on error.
  */
-ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L);
+ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L, uint32_t kernel);
 
 /* Free a 32-bit plan.  NULL is allowed.  Work that uses it must have finished. */
 void ntt_plan32_destroy(ntt_plan32* plan);
@@ -446,6 +448,9 @@ ntt_status ntt_inverse32(const ntt_plan32* plan, uint32_t* data, uint32_t batch,
 
 /* psi for prime l (0 <= l < L) of a 32-bit plan, into *psi. */
 ntt_status ntt_plan32_psi(const ntt_plan32* plan, uint32_t l, uint32_t* psi);
+
+/* Device status word of a 32-bit plan, as ntt_plan_device_status. */
+ntt_status ntt_plan32_device_status(const ntt_plan32* plan, uint32_t* status);
 
 /*
  * Measurement helper for the roofline of the transform kernels (not part of

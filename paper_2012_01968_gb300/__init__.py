@@ -171,7 +171,9 @@ def _lib():
             L.ntt_autotune.argtypes = [_u32, _u64p, _u32, _u32, _u32, ctypes.POINTER(PlanOpts),
                                        ctypes.POINTER(TuneEntry), _u32, ctypes.POINTER(_u32)]
             L.ntt_plan32_create.restype = S
-            L.ntt_plan32_create.argtypes = [ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32), _u32]
+            L.ntt_plan32_create.argtypes = [ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32), _u32, _u32]
+            L.ntt_plan32_device_status.restype = S
+            L.ntt_plan32_device_status.argtypes = [_vp, ctypes.POINTER(_u32)]
             L.ntt_plan32_destroy.restype = None
             L.ntt_plan32_destroy.argtypes = [_vp]
             for f in ("ntt_forward32", "ntt_inverse32"):
@@ -395,18 +397,18 @@ def ntt_autotune(N: int, primes, batch: int = 1, reps: int = 0, entries: bool = 
     return best, out
 
 
-def ntt_plan32_create_status(N: int, primes):
+def ntt_plan32_create_status(N: int, primes, kernel: int = NTT_KERNEL_AUTO):
     """Create a 32-bit plan; returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
     arr = (_u32 * max(1, len(primes)))(*primes)
     out = _vp()
-    st = _lib().ntt_plan32_create(ctypes.byref(out), N, arr if primes else None, len(primes))
+    st = _lib().ntt_plan32_create(ctypes.byref(out), N, arr if primes else None, len(primes), kernel)
     return st, (int(out.value) if out.value else 0)
 
 
-def ntt_plan32_create(N: int, primes) -> int:
+def ntt_plan32_create(N: int, primes, kernel: int = NTT_KERNEL_AUTO) -> int:
     """Create a 32-bit plan (primes q < 2^28); returns the handle.  Raises NttError."""
-    st, h = ntt_plan32_create_status(N, primes)
+    st, h = ntt_plan32_create_status(N, primes, kernel)
     _check(st, "ntt_plan32_create")
     return h
 
@@ -421,6 +423,12 @@ def ntt_forward32(plan: int, data, batch: int, stream=None) -> None:
 
 def ntt_inverse32(plan: int, data, batch: int, stream=None) -> None:
     _check(_lib().ntt_inverse32(plan, _addr(data), batch, _stream(stream, data)), "ntt_inverse32")
+
+
+def ntt_plan32_device_status(plan: int) -> int:
+    v = _u32()
+    _check(_lib().ntt_plan32_device_status(plan, ctypes.byref(v)), "ntt_plan32_device_status")
+    return int(v.value)
 
 
 def ntt_plan32_psi(plan: int, l: int) -> int:
@@ -487,11 +495,14 @@ class Plan:
 class Plan32:
     """RAII wrapper over a 32-bit plan handle (residues in int32/uint32 tensors)."""
 
-    def __init__(self, N: int, primes):
+    def __init__(self, N: int, primes, kernel: int = NTT_KERNEL_AUTO):
         self.N = N
         self.primes = [int(p) for p in primes]
         self.L = len(self.primes)
-        self.handle = ntt_plan32_create(N, self.primes)
+        self.handle = ntt_plan32_create(N, self.primes, kernel)
+
+    def device_status(self) -> int:
+        return ntt_plan32_device_status(self.handle)
 
     def forward(self, data, batch: int = 1, stream=None):
         ntt_forward32(self.handle, data, batch, stream)

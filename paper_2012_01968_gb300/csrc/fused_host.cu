@@ -28,7 +28,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 cudaError_t encode_2d(CUtensorMap* m, void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
-                      uint32_t box_inner, uint32_t box_outer)
+                      uint32_t box_inner, uint32_t box_outer, CUtensorMapDataType type = CU_TENSOR_MAP_DATA_TYPE_UINT64)
 {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
@@ -36,7 +36,7 @@ cudaError_t encode_2d(CUtensorMap* m, void* base, uint64_t inner, uint64_t outer
     const cuuint64_t strides[1] = {row_bytes};
     const cuuint32_t box[2] = {box_inner, box_outer};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, estr,
+    const CUresult r = fn(m, type, 2, base, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -53,6 +53,17 @@ cudaError_t encode_tile_maps(u64* data, u32 limbs, u32 n, int p1, int row_tile_w
     cudaError_t e = encode_2d(mapC, data, N2, N1 * limbs, N2 * 8, 16, (uint32_t)N1);
     if (e != cudaSuccess) return e;
     return encode_2d(mapR, data, 16, (N / 16) * limbs, 128, 16, (uint32_t)(row_tile_words / 16));
+}
+
+// The same views of 32-bit words: 128-byte lines of 32 words.
+cudaError_t encode_tile_maps32(u32* data, u32 limbs, u32 n, int p1, int row_tile_words, CUtensorMap* mapC,
+                               CUtensorMap* mapR)
+{
+    const uint64_t N = 1ull << n, N1 = 1ull << p1, N2 = N >> p1;
+    cudaError_t e = encode_2d(mapC, data, N2, N1 * limbs, N2 * 4, 32, (uint32_t)N1, CU_TENSOR_MAP_DATA_TYPE_UINT32);
+    if (e != cudaSuccess) return e;
+    return encode_2d(mapR, data, 32, (N / 32) * limbs, 128, 32, (uint32_t)(row_tile_words / 32),
+                     CU_TENSOR_MAP_DATA_TYPE_UINT32);
 }
 
 namespace {

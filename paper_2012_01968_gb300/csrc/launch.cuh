@@ -156,14 +156,19 @@ cudaError_t launch_two_pass_w32(const PassLaunch<u32>& c, bool fwd)
     return launch_pass_w<P1, LOGC_C, KMAX_R, false, false, X1, true, true, 0, true, u32>(c, 0, nullptr, nullptr);
 }
 
-// 32-bit launchers by size (k_w32_single.cu: n <= 12, k_w32_two.cu: 13 <= n <= 17)
+// 32-bit launchers by size (k_w32_single.cu: n <= 12, k_w32_two.cu: 13 <= n <= 17,
+// one launch per pass; k_w32_fused.cu: 13 <= n <= 17, the fused kernel)
 cudaError_t launch_w32_single(const PassLaunch<u32>& c, bool fwd);
 cudaError_t launch_w32_two(const PassLaunch<u32>& c, bool fwd);
+struct Fused32Launch;
+cudaError_t launch_w32_fused(const Fused32Launch& c, bool fwd);
 
 // host helpers for the fused launch (fused_host.cu)
 u32 fused_window_limbs(size_t limb_bytes);
 cudaError_t encode_tile_maps(u64* data, u32 limbs, u32 n, int p1, int row_tile_words, CUtensorMap* mapC,
                              CUtensorMap* mapR);
+cudaError_t encode_tile_maps32(u32* data, u32 limbs, u32 n, int p1, int row_tile_words, CUtensorMap* mapC,
+                               CUtensorMap* mapR);
 int device_sm_count();
 
 // One persistent launch over all limbs of all jobs, both passes.
@@ -225,6 +230,65 @@ cudaError_t launch_fused(const JobsCtx& c, bool fwd)
                        : launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 2, MAXJ>(c);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// The fused kernel on 32-bit words (one job, table twiddles): what a launch needs.
+struct Fused32Launch {
+    u32* data;
+    u32 limbs, L, n;
+    const PrimeDev32* primes;
+    const Tw32* tw;
+    u32 tw_len;
+    u32* status;
+    u32* work;               // zero, fused_work_words(work_limbs) words
+    u32 work_limbs;
+    cudaStream_t stream;
+};
+
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD>
+cudaError_t launch_fused32_dir(const Fused32Launch& c)
+{
+    using F = FusedCfg<P1, P2, LOGC_R, KMAX, u32>;
+    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, 0, 1, u32>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int occ = 0;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, F::THREADS, F::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    if (c.limbs == 0 || c.limbs > 0x7FFFFFFFu || !c.work || c.work_limbs < c.limbs) return cudaErrorInvalidValue;
+    FusedParams<1, u32> a{};
+    cudaError_t e = encode_tile_maps32(c.data, c.limbs, c.n, P1, F::TILE_R, &a.mapC[0], &a.mapR[0]);
+    if (e != cudaSuccess) return e;
+    a.job[0].primes = c.primes;
+    a.job[0].tw = c.tw;
+    a.job[0].ota = nullptr;
+    a.job[0].otb = nullptr;
+    a.job[0].tw_len = c.tw_len;
+    a.job[0].L = c.L;
+    a.job[0].limb0 = 0;
+    constexpr u32 UC = F::R2 / F::COLW, UR = F::R1 / F::CR;
+    const u64 units = (u64)c.limbs * (UC + UR);
+    const u64 slots = (u64)device_sm_count() * (u64)occ;
+    const u32 grid = (u32)(units < slots ? units : slots);
+    a.ctl = c.work;
+    a.status = c.status;
+    a.njobs = 1;
+    a.limbs = c.limbs;
+    a.a_window = fused_window_limbs(sizeof(u32) << (P1 + P2));
+    a.max_polls = 1u << 22;
+    kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P1, int P2, int LOGC_R, int KMAX>
+cudaError_t launch_fused32(const Fused32Launch& c, bool fwd)
+{
+    return fwd ? launch_fused32_dir<P1, P2, LOGC_R, KMAX, true>(c) : launch_fused32_dir<P1, P2, LOGC_R, KMAX, false>(c);
 }
 
 // A single call: one launch per pass, or the fused kernel with one job.

@@ -59,31 +59,37 @@
 #ifndef NTT_FUSED_THREADS_PER_SM
 #define NTT_FUSED_THREADS_PER_SM 576    // resident threads per SM the registers are sized for
 #endif
+#ifndef NTT_FUSED32_THREADS_PER_SM
+#define NTT_FUSED32_THREADS_PER_SM 1088 // the same for 32-bit words (two CTAs of 512 + 32 threads)
+#endif
 
 namespace ntt {
 
 // bits of the device status word
 enum : u32 { STATUS_DEP_TIMEOUT = 1u, STATUS_TMA_TIMEOUT = 2u };
 
-// One job of a launch: a [batch][L][N] array and the tables of its plan.
-struct FusedJob {
-    const PrimeDev* primes;  // [L]
-    const Tw* tw;            // [L][tw_len]
-    const Tw* ota;           // [L][2^p2]      OT A factors, this direction
-    const Tw* otb;           // [L][p2 << p1]  OT B factors, this direction
+// One job of a launch: a [batch][L][N] array and the tables of its plan
+// (W: the data word, 64 or 32 bits).
+template <class W = u64>
+struct FusedJobT {
+    const typename WordTypes<W>::Prime* primes;  // [L]
+    const typename WordTypes<W>::Tw* tw;         // [L][tw_len]
+    const typename WordTypes<W>::Tw* ota;        // [L][2^p2]      OT A factors, this direction
+    const typename WordTypes<W>::Tw* otb;        // [L][p2 << p1]  OT B factors, this direction
     u32 tw_len;
     u32 L;                   // primes per polynomial (local limb l uses prime l % L)
     u32 limb0;               // first limb of the job in the launch's numbering
     u32 reserved;
 };
+using FusedJob = FusedJobT<u64>;
 
 // Kernel parameters (passed by value as one __grid_constant__ block, so the
 // tensor maps live in parameter space).
-template <int MAXJ>
+template <int MAXJ, class W = u64>
 struct FusedParams {
     CUtensorMap mapC[MAXJ];  // column view of each job's data
     CUtensorMap mapR[MAXJ];  // row view of each job's data
-    FusedJob job[MAXJ];
+    FusedJobT<W> job[MAXJ];
     u32* ctl;                // work area (see the file comment)
     u32* status;             // persistent error word
     u32 njobs;
@@ -92,27 +98,32 @@ struct FusedParams {
     u32 max_polls;           // bound of every wait loop
 };
 
-template <int P1, int P2, int LOGC_R, int KMAX>
+template <int P1, int P2, int LOGC_R, int KMAX, class W = u64>
 struct FusedCfg {
+    using TwT = typename WordTypes<W>::Tw;
+    using PrimeT = typename WordTypes<W>::Prime;
     static constexpr int R1 = 1 << P1, R2 = 1 << P2, CR = 1 << LOGC_R;
-    static constexpr int TILE_C = 16 * R1;             // column tile: 16 columns x R1 rows
+    // a column tile is one 128-byte line wide: 16 words of 64 bits or 32 of 32
+    static constexpr int LOGC_COL = sizeof(W) == 8 ? 4 : 5;
+    static constexpr int COLW = 1 << LOGC_COL;
+    static constexpr int TILE_C = COLW * R1;           // column tile: COLW columns x R1 rows
     static constexpr int TILE_R = CR * R2;             // row tile: CR rows of R2 words
     static constexpr int TILE = TILE_C > TILE_R ? TILE_C : TILE_R;
-    static constexpr int TC = pass_threads(P1, 4, KMAX);
+    static constexpr int TC = pass_threads(P1, LOGC_COL, KMAX);
     static constexpr int TR = pass_threads(P2, LOGC_R, KMAX);
     static constexpr int NT = TC > TR ? TC : TR;       // compute threads
     static constexpr int THREADS = NT + 32;            // + the producer warp
     // per buffer: the tile, the column pass's twiddles Psi[0, R1), the prime's
     // constants and the unit descriptor, the first three filled by one
     // mbarrier transaction
-    static constexpr size_t TW_OFF = (size_t)TILE * 8;
-    static constexpr size_t PR_OFF = TW_OFF + (size_t)R1 * sizeof(Tw);
-    static constexpr size_t DESC_OFF = PR_OFF + sizeof(PrimeDev);
+    static constexpr size_t TW_OFF = (size_t)TILE * sizeof(W);
+    static constexpr size_t PR_OFF = TW_OFF + (size_t)R1 * sizeof(TwT);
+    static constexpr size_t DESC_OFF = PR_OFF + sizeof(PrimeT);
     static constexpr size_t BUF = (DESC_OFF + 32 + 1023) / 1024 * 1024;
     static constexpr int NBUF = 3;                     // ring of tile buffers
     static constexpr size_t SMEM = NBUF * BUF + 1024;
-    static constexpr int MIN_CTAS =
-        NTT_FUSED_THREADS_PER_SM / THREADS > 1 ? NTT_FUSED_THREADS_PER_SM / THREADS : 1;
+    static constexpr int TPS = sizeof(W) == 8 ? NTT_FUSED_THREADS_PER_SM : NTT_FUSED32_THREADS_PER_SM;
+    static constexpr int MIN_CTAS = TPS / THREADS > 1 ? TPS / THREADS : 1;
 };
 
 // unit descriptor written by the producer into the buffer it fills
@@ -143,23 +154,26 @@ __device__ __forceinline__ bool compute_any(bool flag)
     return r != 0;
 }
 
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ>
-__global__ void __launch_bounds__(FusedCfg<P1, P2, LOGC_R, KMAX>::THREADS, FusedCfg<P1, P2, LOGC_R, KMAX>::MIN_CTAS)
-ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ> a)
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, class W = u64>
+__global__ void __launch_bounds__(FusedCfg<P1, P2, LOGC_R, KMAX, W>::THREADS,
+                                  FusedCfg<P1, P2, LOGC_R, KMAX, W>::MIN_CTAS)
+ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
 {
-    using F = FusedCfg<P1, P2, LOGC_R, KMAX>;
+    using F = FusedCfg<P1, P2, LOGC_R, KMAX, W>;
+    using TwT = typename F::TwT;
+    using PrimeT = typename F::PrimeT;
     constexpr int NT = F::NT;
     constexpr int NBUF = F::NBUF;
-    constexpr u32 UC = F::R2 / 16;          // column tiles per limb
+    constexpr u32 UC = F::R2 / F::COLW;     // column tiles per limb
     constexpr u32 UR = F::R1 / F::CR;       // row tiles per limb
     constexpr u32 UA = FWD ? UC : UR, UB = FWD ? UR : UC;
     constexpr int X_B = FWD ? ct_range_after(1, P1) : gs_range_after(1, P2);
     constexpr u32 NONE = 0xFFFFFFFFu;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    auto buf_tile = [&](int b) { return reinterpret_cast<u64*>(smem_raw + b * F::BUF); };
-    auto buf_tw = [&](int b) { return reinterpret_cast<Tw*>(smem_raw + b * F::BUF + F::TW_OFF); };
-    auto buf_pr = [&](int b) { return reinterpret_cast<PrimeDev*>(smem_raw + b * F::BUF + F::PR_OFF); };
+    auto buf_tile = [&](int b) { return reinterpret_cast<W*>(smem_raw + b * F::BUF); };
+    auto buf_tw = [&](int b) { return reinterpret_cast<TwT*>(smem_raw + b * F::BUF + F::TW_OFF); };
+    auto buf_pr = [&](int b) { return reinterpret_cast<PrimeT*>(smem_raw + b * F::BUF + F::PR_OFF); };
     auto buf_desc = [&](int b) { return reinterpret_cast<volatile UnitDesc*>(smem_raw + b * F::BUF + F::DESC_OFF); };
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + NBUF * F::BUF);
     uint64_t* empty = full + NBUF;
@@ -237,7 +251,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ> a)
         auto load = [&](u32 kind, u32 limb, u32 tile) {
             const int b = (int)(issued % NBUF);
             const u32 j = job_of(limb);
-            const FusedJob& J = a.job[j];
+            const FusedJobT<W>& J = a.job[j];
             const u32 local = limb - J.limb0, pi = local % J.L;
             volatile UnitDesc* d = buf_desc(b);
             d->kind = kind;
@@ -251,26 +265,28 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ> a)
             // committed after that one; waiting for all but the newest suffices
             bulk_wait_read<1>();
             if (kind == KIND_B) fence_proxy_async_global();
-            u64* dst = buf_tile(b);
+            W* dst = buf_tile(b);
             if (is_col(kind)) {
-                mbar_arrive_expect_tx(&full[b], F::TILE_C * 8 + F::R1 * (u32)sizeof(Tw) + (u32)sizeof(PrimeDev));
-                tma_load_2d(dst, &a.mapC[j], (int)(tile * 16), (int)(local * F::R1), &full[b]);
-                bulk_load(buf_tw(b), J.tw + (size_t)pi * J.tw_len, F::R1 * (u32)sizeof(Tw), &full[b]);
+                mbar_arrive_expect_tx(&full[b], F::TILE_C * (u32)sizeof(W) + F::R1 * (u32)sizeof(TwT) +
+                                                    (u32)sizeof(PrimeT));
+                tma_load_2d(dst, &a.mapC[j], (int)(tile * F::COLW), (int)(local * F::R1), &full[b]);
+                bulk_load(buf_tw(b), J.tw + (size_t)pi * J.tw_len, F::R1 * (u32)sizeof(TwT), &full[b]);
             } else {
-                mbar_arrive_expect_tx(&full[b], F::TILE_R * 8 + (u32)sizeof(PrimeDev));
-                tma_load_2d(dst, &a.mapR[j], 0, (int)(local * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), &full[b]);
+                mbar_arrive_expect_tx(&full[b], F::TILE_R * (u32)sizeof(W) + (u32)sizeof(PrimeT));
+                tma_load_2d(dst, &a.mapR[j], 0,
+                            (int)(local * (F::R1 * F::R2 / F::COLW) + tile * (F::TILE_R / F::COLW)), &full[b]);
                 // table runs of the row pass, into L2: stage sl of rows [u0, u0 + CR)
                 // reads CR << sl consecutive entries (mirrored for the inverse)
-                const Tw* base = J.tw + (size_t)pi * J.tw_len;
+                const TwT* base = J.tw + (size_t)pi * J.tw_len;
                 const u32 u0 = tile * (u32)F::CR;
 #pragma unroll
                 for (int sl = 0; sl < P2 - OTS; ++sl) {
                     const u32 start = FWD ? (1u << (P1 + sl)) + (u0 << sl)
                                           : (2u << (P1 + sl)) - ((u0 + (u32)F::CR) << sl);
-                    bulk_prefetch_l2(base + start, ((u32)F::CR << sl) * (u32)sizeof(Tw));
+                    bulk_prefetch_l2(base + start, ((u32)F::CR << sl) * (u32)sizeof(TwT));
                 }
             }
-            bulk_load(buf_pr(b), J.primes + pi, (u32)sizeof(PrimeDev), &full[b]);
+            bulk_load(buf_pr(b), J.primes + pi, (u32)sizeof(PrimeT), &full[b]);
             ++issued;
         };
         // limb of B ticket t: the (t / UB)-th published limb, NONE while unpublished
@@ -302,11 +318,12 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ> a)
                 const volatile UnitDesc* d = buf_desc(b);
                 const u32 kind = d->kind, limb = d->limb, tile = d->tile, local = d->local;
                 const u32 j = MAXJ > 1 ? d->job : 0u;
-                const u64* src = buf_tile(b);
+                const W* src = buf_tile(b);
                 if (is_col(kind))
-                    tma_store_2d(&a.mapC[j], (int)(tile * 16), (int)(local * F::R1), src);
+                    tma_store_2d(&a.mapC[j], (int)(tile * F::COLW), (int)(local * F::R1), src);
                 else
-                    tma_store_2d(&a.mapR[j], 0, (int)(local * (F::R1 * F::R2 / 16) + tile * (F::TILE_R / 16)), src);
+                    tma_store_2d(&a.mapR[j], 0, (int)(local * (F::R1 * F::R2 / F::COLW) + tile * (F::TILE_R / F::COLW)),
+                                 src);
                 bulk_commit();
                 const u32 e = kind == KIND_A ? (0x80000000u | limb) : 0u;
                 if (qn == 0) q0 = e;
@@ -401,21 +418,21 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ> a)
         if (kind == KIND_STOP) break;
         const u32 tile = buf_desc(b)->tile;
         const u32 pi = buf_desc(b)->prime;
-        u64* sm = buf_tile(b);
-        const PrimeDev& pr = *buf_pr(b);
+        W* sm = buf_tile(b);
+        const PrimeT& pr = *buf_pr(b);
         if (is_col(kind)) {
             // column pass: twiddles Psi[0, R1) staged with the tile
             if constexpr (FWD)
-                compute_tile<P1, 4, KMAX, false, true, 1, false, true, 0, true, NT, NoHook, true>(
+                compute_tile<P1, F::LOGC_COL, KMAX, false, true, 1, false, true, 0, true, NT, NoHook, true>(
                     sm, pr, buf_tw(b), nullptr, nullptr, 0u, 0u, tid);
             else
-                compute_tile<P1, 4, KMAX, false, false, X_B, true, true, 0, true, NT, NoHook, true>(
+                compute_tile<P1, F::LOGC_COL, KMAX, false, false, X_B, true, true, 0, true, NT, NoHook, true>(
                     sm, pr, buf_tw(b), nullptr, nullptr, 0u, 0u, tid);
         } else {
-            const FusedJob& J = a.job[MAXJ > 1 ? buf_desc(b)->job : 0u];
-            const Tw* tw = J.tw + (size_t)pi * J.tw_len;
-            const Tw* ota = J.ota ? J.ota + (size_t)pi * F::R2 : nullptr;
-            const Tw* otb = J.otb ? J.otb + (size_t)pi * ((size_t)P2 << P1) : nullptr;
+            const FusedJobT<W>& J = a.job[MAXJ > 1 ? buf_desc(b)->job : 0u];
+            const TwT* tw = J.tw + (size_t)pi * J.tw_len;
+            const TwT* ota = J.ota ? J.ota + (size_t)pi * F::R2 : nullptr;
+            const TwT* otb = J.otb ? J.otb + (size_t)pi * ((size_t)P2 << P1) : nullptr;
             if constexpr (FWD)
                 compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
                     sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);

@@ -53,14 +53,14 @@ __host__ __device__ constexpr int gs_range_max(int X, int stages)
 // strided per-thread accesses of every round conflict-free.
 __device__ __forceinline__ u32 swz(u32 w) { return w ^ (((w >> 4) & 7u) << 1); }
 
-// The same for 32-bit words: pair index XOR (line index mod 8), line = 32
-// words (128 bytes), so that a warp reading word pairs at a stride of 16 words
-// still covers every bank pair once per 16 lanes.
+// The same for 32-bit words: 16-byte chunk index XOR (line index mod 8), line
+// = 32 words (128 bytes), which is the TMA 128-byte swizzle for 4-byte
+// elements; quads, hence word pairs, stay together.
 template <class W>
 __device__ __forceinline__ u32 swzw(u32 w)
 {
     if constexpr (sizeof(W) == 8) return swz(w);
-    else return w ^ (((w >> 5) & 7u) << 1);
+    else return w ^ (((w >> 5) & 7u) << 2);
 }
 
 // Twiddle slots.  Within stage s the butterfly with index j = (u << sl) |

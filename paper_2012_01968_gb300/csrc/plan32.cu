@@ -1,5 +1,6 @@
 // 32-bit word plans (Sec. IV, "32b vs. 64b word size"): primes q < 2^28,
-// residues in 32-bit words, table twiddles, one launch per pass.
+// residues in 32-bit words, table twiddles; the fused two-pass kernel for
+// N >= 2^13 (or one launch per pass), one pass below.
 //
 // Tables per prime q, in the slot order of the 64-bit kernels (the pass split
 // and the per-thread radix are the same):
@@ -7,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -21,10 +23,15 @@ extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
 
 struct ntt_plan32 {
     uint32_t N = 0, n = 0, L = 0, p1 = 0;
+    uint32_t kernel = 0;                  // NTT_KERNEL_FUSED or NTT_KERNEL_PER_PASS (two-pass sizes)
     int device = 0;
     std::vector<uint32_t> primes, psis;
     PrimeDev32* d_primes = nullptr;
     Tw32* d_tw = nullptr;
+    uint32_t* d_status = nullptr;         // device status word (fused kernel's bounded waits)
+    uint32_t* d_work = nullptr;           // fused kernel's work area, fused_work_words(work_limbs) words
+    uint32_t work_limbs = 0;
+    std::mutex work_mu;
 };
 
 namespace {
@@ -36,7 +43,29 @@ void free_plan32(ntt_plan32* p)
     if (!p) return;
     cudaFree(p->d_primes);
     cudaFree(p->d_tw);
+    cudaFree(p->d_status);
+    cudaFree(p->d_work);
     delete p;
+}
+
+// Make the work area cover `limbs` limbs (zero-filled); a larger area
+// replaces the old one after the device has drained.
+cudaError_t grow_work32(ntt_plan32* p, uint32_t limbs)
+{
+    std::lock_guard<std::mutex> g(p->work_mu);
+    if (p->work_limbs >= limbs) return cudaSuccess;
+    if (p->d_work) {
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return e;
+        cudaFree(p->d_work);
+        p->d_work = nullptr;
+        p->work_limbs = 0;
+    }
+    const size_t bytes = ntt::fused_work_words(limbs) * sizeof(uint32_t);
+    cudaError_t e = cudaMalloc(&p->d_work, bytes);
+    if (e == cudaSuccess) e = cudaMemset(p->d_work, 0, bytes);
+    if (e == cudaSuccess) p->work_limbs = limbs;
+    return e;
 }
 
 ntt_status to_status32(cudaError_t e)
@@ -52,18 +81,30 @@ ntt_status transform32(const ntt_plan32* p, uint32_t* data, uint32_t batch, void
     if (((uintptr_t)data & 15u) != 0) return NTT_ERR_MISALIGNED;
     const uint64_t limbs = (uint64_t)batch * p->L;
     if (limbs > 0xFFFFFFFFull) return NTT_ERR_INVALID_ARG;
-    const ntt::PassLaunch<ntt::u32> c{data, (uint32_t)limbs, p->L, p->n, p->d_primes, p->d_tw, p->N,
-                                      (cudaStream_t)stream};
-    const cudaError_t e = p->n <= (uint32_t)ntt::SINGLE_PASS_MAX ? ntt::launch_w32_single(c, fwd)
-                                                                 : ntt::launch_w32_two(c, fwd);
-    return to_status32(e);
+    if (p->n <= (uint32_t)ntt::SINGLE_PASS_MAX || p->kernel == NTT_KERNEL_PER_PASS) {
+        const ntt::PassLaunch<ntt::u32> c{data, (uint32_t)limbs, p->L, p->n, p->d_primes, p->d_tw, p->N,
+                                          (cudaStream_t)stream};
+        return to_status32(p->n <= (uint32_t)ntt::SINGLE_PASS_MAX ? ntt::launch_w32_single(c, fwd)
+                                                                  : ntt::launch_w32_two(c, fwd));
+    }
+    if (limbs > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
+    if (p->work_limbs < limbs) {
+        const cudaError_t e = grow_work32(const_cast<ntt_plan32*>(p), (uint32_t)limbs);
+        if (e != cudaSuccess) return to_status32(e);
+    }
+    const ntt::Fused32Launch c{data,     (uint32_t)limbs, p->L,       p->n,          p->d_primes,
+                               p->d_tw,  p->N,            p->d_status, p->d_work,    p->work_limbs,
+                               (cudaStream_t)stream};
+    return to_status32(ntt::launch_w32_fused(c, fwd));
 }
 
 }  // namespace
 
-extern "C" ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L)
+extern "C" ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L,
+                                        uint32_t kernel)
 {
     if (!out || !primes || L == 0 || L > 4096) return NTT_ERR_INVALID_ARG;
+    if (kernel > NTT_KERNEL_PER_PASS) return NTT_ERR_INVALID_ARG;
     if (N < 2 || N > (1u << 17) || (N & (N - 1))) return NTT_ERR_INVALID_ARG;
     for (uint32_t l = 0; l < L; ++l) {
         const uint64_t q = primes[l];
@@ -77,6 +118,7 @@ extern "C" ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint
     p->n = (uint32_t)__builtin_ctz(N);
     p->L = L;
     p->p1 = (uint32_t)ntt::split_p1((int)p->n);
+    p->kernel = kernel == NTT_KERNEL_PER_PASS ? NTT_KERNEL_PER_PASS : NTT_KERNEL_FUSED;
     cudaError_t ce = cudaGetDevice(&p->device);
     if (ce != cudaSuccess) {
         free_plan32(p);
@@ -116,7 +158,9 @@ extern "C" ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint
         d.ninv = make_tw32(ninv, q);
         d.w1ninv = make_tw32(pw[nt::brv(1, n)] * ninv % q, q);     // Psi[1] N^{-1}
     }
-    ce = cudaMalloc(&p->d_primes, pd.size() * sizeof(PrimeDev32));
+    ce = cudaMalloc(&p->d_status, sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(p->d_status, 0, sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_primes, pd.size() * sizeof(PrimeDev32));
     if (ce == cudaSuccess) ce = cudaMemcpy(p->d_primes, pd.data(), pd.size() * sizeof(PrimeDev32), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMalloc(&p->d_tw, tw.size() * sizeof(Tw32));
     if (ce == cudaSuccess) ce = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(Tw32), cudaMemcpyHostToDevice);
@@ -139,6 +183,18 @@ extern "C" ntt_status ntt_forward32(const ntt_plan32* p, uint32_t* data, uint32_
 extern "C" ntt_status ntt_inverse32(const ntt_plan32* p, uint32_t* data, uint32_t batch, void* stream)
 {
     return transform32(p, data, batch, stream, false);
+}
+
+extern "C" ntt_status ntt_plan32_device_status(const ntt_plan32* p, uint32_t* status)
+{
+    if (!p || !status) return NTT_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    uint32_t v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(v));
+    if (e != cudaSuccess) return to_status32(e);
+    *status = v;
+    return NTT_OK;
 }
 
 extern "C" ntt_status ntt_plan32_psi(const ntt_plan32* p, uint32_t l, uint32_t* psi)

@@ -95,6 +95,12 @@ def test_plan32_create_rejects(lib, N, primes, want):
     assert h == 0
 
 
+@pytest.mark.parametrize("kernel", [G.NTT_KERNEL_RADIX2, G.NTT_KERNEL_HIGH_RADIX, 9])
+def test_plan32_rejects_kernel(lib, kernel):
+    st, h = G.ntt_plan32_create_status(1 << 13, SMALL[:1], kernel)
+    assert st == G.NTT_ERR_INVALID_ARG and h == 0
+
+
 def test_plan32_primes_are_28_bit():
     assert all((1 << 27) <= q < (1 << 28) and q % (1 << 13) == 1 and I.is_prime(q) for q in SMALL)
     assert SMALL[1] % (1 << 14) != 1
@@ -111,7 +117,8 @@ def test_null_arguments_rejected(lib):
     assert lib.ntt_forward32(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_inverse32(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_plan32_psi(None, 0, None) == G.NTT_ERR_INVALID_ARG
-    assert lib.ntt_plan32_create(None, 16, None, 1) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_plan32_create(None, 16, None, 1, 0) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_plan32_device_status(None, None) == G.NTT_ERR_INVALID_ARG
     best = G.PlanOpts()
     assert lib.ntt_autotune(16, None, 1, 1, 1, ctypes.byref(best), None, 0, None) == G.NTT_ERR_INVALID_ARG
     arr = (ctypes.c_uint64 * 1)(BIG[0])

@@ -38,9 +38,9 @@ def host32(t):
     return t.cpu().numpy().view(np.uint32).astype(np.uint64)
 
 
-def _roundtrip(orc, N, primes, batch, seed):
+def _roundtrip(orc, N, primes, batch, seed, kernel=G.NTT_KERNEL_AUTO):
     data = I.batch_uniform(seed, batch, primes, N)
-    with G.Plan32(N, primes) as p:
+    with G.Plan32(N, primes, kernel) as p:
         d = dev32(data)
         p.forward(d, batch)
         torch.cuda.synchronize()
@@ -51,6 +51,7 @@ def _roundtrip(orc, N, primes, batch, seed):
         dy = dev32(y)
         p.inverse(dy, batch)
         assert np.array_equal(host32(dy), oracle_inv(orc, y, primes)), "inverse mismatch"
+        assert p.device_status() == 0
 
 
 @pytest.mark.parametrize("n", list(range(1, 18)))
@@ -59,11 +60,34 @@ def test_every_size(orc, n):
     _roundtrip(orc, N, primes28(N, 3), 2, 300 + n)
 
 
-@pytest.mark.parametrize("n", [12, 13, 16, 17])
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+def test_per_pass_organisation(orc, n):
+    """The two-pass sizes also with one launch per pass."""
+    N = 1 << n
+    _roundtrip(orc, N, primes28(N, 3), 2, 360 + n, G.NTT_KERNEL_PER_PASS)
+
+
+@pytest.mark.parametrize("n", [12, 13, 14, 15, 16, 17])
 def test_several_polynomials_and_limbs(orc, n):
-    """Many limbs: tiles of several polynomials and primes in one launch."""
+    """Many limbs: tiles of several polynomials and primes in one launch
+    (the fused kernel's queues, publication order and work area)."""
     N = 1 << n
     _roundtrip(orc, N, primes28(N, 5), 3, 320 + n)
+
+
+def test_fused_many_limbs_full_size(orc):
+    """The bench's 32-bit workload shape: N = 2^16 with 98 primes (the C2
+    modulus size) through the fused kernel."""
+    N = 1 << 16
+    primes = primes28(N, 98)
+    data = I.batch_uniform(350, 1, primes, N)
+    with G.Plan32(N, primes) as p:
+        d = dev32(data)
+        p.forward(d, 1)
+        assert np.array_equal(host32(d), oracle_fwd(orc, data, primes))
+        p.inverse(d, 1)
+        assert np.array_equal(host32(d), data)
+        assert p.device_status() == 0
 
 
 def test_psi_matches_oracle(orc):
