@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--ablation-only", action="store_true",
                     help="run only the kernel-organisation sweep and print it (for profiling its launches)")
     ap.add_argument("--ablation-reps", type=int, default=40)
+    ap.add_argument("--word-size-only", action="store_true",
+                    help="run only the word-size comparison and print it (for profiling its launches)")
     ap.add_argument("--no-tune", action="store_true",
                     help="plans with the fixed default options instead of the autotuner's choice")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -756,9 +758,14 @@ def main():
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
     G.lib()
-    if args.ablation_only:
+    if args.ablation_only or args.word_size_only:
         if rank == 0:
-            print(json.dumps({"paper_ablation": paper_ablation(G, torch, args.ablation_reps, (16, 17))}), flush=True)
+            if args.ablation_only:
+                out = {"paper_ablation": paper_ablation(G, torch, args.ablation_reps, (16, 17))}
+            else:
+                w2 = I.workload_c2()
+                out = {"word_size": {"c2_n65536": word_size(G, torch, w2.N, w2.primes, w2.seed, args.ablation_reps)}}
+            print(json.dumps(out), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return
