@@ -418,7 +418,8 @@ def batched_c4(G, torch, reps, tuned=None):
             p.close()
 
 
-def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None):
+def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jobs=64, slots=3,
+             loads=(0.5, 0.8, 0.95)):
     """The serving workload: `count` requests (N in 2^15..2^17, L in [4, 60],
     mixed directions) on device-resident data, admitted by an HBM budget.
     A capacity run (every request submitted at once), then Poisson arrivals at
@@ -448,7 +449,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None):
                 gc.enable()
 
         def run_load(rate):
-            with G.Server(budget_gb << 30, max_batch_jobs=32, slots=3) as srv:
+            with G.Server(budget_gb << 30, max_batch_jobs=max_batch_jobs, slots=slots) as srv:
                 inflight = collections.deque()          # (ticket, start, end) in ring order
                 tickets = []
                 off = 0
@@ -485,7 +486,8 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None):
         cap = run(None)
         out = {"requests": count, "budget_gb": budget_gb, "data": "device-resident, in place",
                "capacity": cap}
-        for frac in (0.5, 0.8, 0.95):
+        out["max_batch_jobs"], out["slots"] = max_batch_jobs, slots
+        for frac in loads:
             out[f"poisson_{int(frac * 100)}pct"] = dict(run(frac * cap["requests_per_s"]),
                                                        offered_requests_per_s=frac * cap["requests_per_s"])
         return out

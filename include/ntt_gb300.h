@@ -336,7 +336,7 @@ typedef struct ntt_server ntt_server;
 typedef struct ntt_server_opts {
     uint64_t hbm_budget_bytes;    /* bytes of admitted requests at any time (> 0) */
     uint64_t arena_bytes;         /* device staging for NTT_REQ_HOST requests (0: none) */
-    uint32_t max_batch_jobs;      /* requests per batch (0: 32) */
+    uint32_t max_batch_jobs;      /* requests per batch (0: 64) */
     uint32_t slots;               /* batches in flight (0: 3; at most 16) */
     uint32_t max_queue;           /* waiting requests before NTT_ERR_BUSY (0: 2^20) */
     uint32_t reserved[3];         /* must be zero */
