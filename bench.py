@@ -203,13 +203,14 @@ def measured_peak_hbm():
 # ----------------------------------------------------------------------------
 # CPU oracle leg
 # ----------------------------------------------------------------------------
-def oracle_time(primes, N, seconds_target: float):
-    """Oracle forward + inverse over all limbs of one C2 polynomial, repeated
-    until ~seconds_target elapse; returns (limb-NTT/s, cores, sample text)."""
+def oracle_time(primes, N, seconds_target: float, threads: int | None = None, batch: int = 1):
+    """Oracle forward + inverse over all limbs of `batch` polynomials, repeated
+    until ~seconds_target elapse, limb-parallel on `threads` host threads (all
+    cores by default); returns (limb-NTT/s, threads, sample text)."""
     import oracle
     orc = oracle.get()
-    cores = os.cpu_count() or 1
-    data = I.batch_uniform(2, 1, primes, N)
+    cores = threads or os.cpu_count() or 1
+    data = I.batch_uniform(2, batch, primes, N)
     reps = 0
     t0 = time.perf_counter()
     while True:
@@ -221,8 +222,8 @@ def oracle_time(primes, N, seconds_target: float):
             break
     if not np.array_equal(b, data):
         raise RuntimeError("oracle round trip failed")
-    v = reps * 2 * len(primes) / el
-    return v, cores, f"{reps} x (forward + inverse of all {len(primes)} limbs), N={N}, {el:.1f} s"
+    v = reps * 2 * batch * len(primes) / el
+    return v, cores, f"{reps} x (forward + inverse of all {batch * len(primes)} limbs), N={N}, {el:.1f} s"
 
 
 def run_reference(args, metric, unit, w):
@@ -437,6 +438,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
     base = I.serving_requests(count, 1.0, seed=5)   # sizes and directions; gaps rescaled per rate
     sizes = [r.L * r.N for r in base]
     limbs_total = sum(r.L for r in base)
+    bytes_total = 16 * sum(sizes)              # one read and one write of every limb
     try:
         def run(rate):
             # the load generator must not pause: no Python garbage collection
@@ -480,6 +482,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
             lat = (done - sub) / 1e3
             span = (done.max() - sub.min()) / 1e9
             return {"limb_ntt_per_s": limbs_total / span, "requests_per_s": count / span,
+                    "gb_per_s": bytes_total / span / 1e9,
                     "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                    "mean": float(lat.mean())}}
 
@@ -954,6 +957,12 @@ def main():
     if ws == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_time(primes, N, 10.0)
         cpu = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
+        # the other views of the same baseline: one host thread, and the large ring (C3)
+        v1, _, s1 = oracle_time(primes, N, 5.0, threads=1)
+        w3 = I.workload_c3()
+        v3, c3, s3 = oracle_time(w3.primes, w3.N, 5.0, batch=2)
+        cpu["single_thread"] = {"value": v1, "unit": unit, "cores": 1, "sample": s1}
+        cpu["large_ring_c3"] = {"value": v3, "unit": unit, "cores": c3, "sample": s3}
     # the committed DRAM counters are for the fused kernel with OT1 in geometry 0
     profiled = (info.kernel == G.NTT_KERNEL_FUSED and info.twiddle_mode == G.NTT_TWIDDLE_OT
                 and info.ot_stages == 1 and info.geometry == 0)
