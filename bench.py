@@ -424,7 +424,9 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
     """The serving workload: `count` requests (N in 2^15..2^17, L in [4, 60],
     mixed directions) on device-resident data, admitted by an HBM budget.
     A capacity run (every request submitted at once), then Poisson arrivals at
-    50 / 80 / 95% of that capacity; latency = submission to completion."""
+    50 / 80 / 95% of that capacity; latency = submission to completion.  At
+    each Poisson load the first tenth of the requests is a warm-up, left out
+    of the statistics."""
     import collections
     chain = I.chain_2_18_60()
     plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain))
@@ -437,8 +439,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
     ring.random_(0, 1 << 59, generator=gen)         # residues below every prime of the chain
     base = I.serving_requests(count, 1.0, seed=5)   # sizes and directions; gaps rescaled per rate
     sizes = [r.L * r.N for r in base]
-    limbs_total = sum(r.L for r in base)
-    bytes_total = 16 * sum(sizes)              # one read and one write of every limb
+    warm = count // 10                         # warm-up requests of each Poisson run
     try:
         def run(rate):
             # the load generator must not pause: no Python garbage collection
@@ -477,12 +478,16 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                 for t in tickets:
                     srv.wait(t)
                 times = [srv.times(t) for t in tickets]
-            sub = np.array([x[0] for x in times], dtype=np.float64)
-            done = np.array([x[2] for x in times], dtype=np.float64)
+            # at a Poisson load the first `warm` requests bring host and device
+            # to that load's steady state and are left out of the statistics
+            first = warm if rate is not None else 0
+            sub = np.array([x[0] for x in times[first:]], dtype=np.float64)
+            done = np.array([x[2] for x in times[first:]], dtype=np.float64)
             lat = (done - sub) / 1e3
             span = (done.max() - sub.min()) / 1e9
-            return {"limb_ntt_per_s": limbs_total / span, "requests_per_s": count / span,
-                    "gb_per_s": bytes_total / span / 1e9,
+            limbs = sum(r.L for r in base[first:])
+            return {"limb_ntt_per_s": limbs / span, "requests_per_s": (count - first) / span,
+                    "gb_per_s": 16 * sum(sizes[first:]) / span / 1e9, "measured_requests": count - first,
                     "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                    "mean": float(lat.mean())}}
 
