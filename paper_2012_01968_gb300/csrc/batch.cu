@@ -31,6 +31,7 @@ struct ntt_batch {
     uint32_t* d_work = nullptr;   // work areas of the fused launches, back to back
     size_t work_words = 0;
     uint32_t* d_status = nullptr;
+    uint32_t test_stall_polls = 0;  // test hook: the next submission's fused launches stall (bounded)
     std::mutex mu;
 };
 
@@ -175,6 +176,21 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         if (e != cudaSuccess) return cuda_status(e);
     }
 
+    // test hook: mark every fused launch's first-pass queue as taken, so that
+    // no limb is ever published and every wait for one runs out after
+    // test_stall_polls polls (the kernels then set the status word)
+    const uint32_t stall = b->test_stall_polls;
+    b->test_stall_polls = 0;
+    if (stall) {
+        static const uint32_t taken = 0x40000000u;
+        size_t o = 0;
+        for (const ntt::host::Chunk& c : chunks) {
+            cudaError_t e = cudaMemcpyAsync(b->d_work + o, &taken, sizeof(taken), cudaMemcpyHostToDevice, caller);
+            if (e != cudaSuccess) return cuda_status(e);
+            o += ntt::fused_work_words(c.limbs);
+        }
+    }
+
     // fork onto the internal streams
     const int used = (int)std::min<size_t>(kStreams, chunks.size() + direct.size());
     cudaError_t e = cudaEventRecord(b->fork, caller);
@@ -200,7 +216,7 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         const uint32_t n = std::get<0>(c.key) & 0xFFu, geom = std::get<0>(c.key) >> 8, ots = std::get<2>(c.key);
         const bool fwd = std::get<1>(c.key) == NTT_OP_FORWARD;
         const ntt::JobsCtx ctx{jc.data(), (uint32_t)jc.size(), n, ots, b->d_status, b->d_work + off,
-                               (uint32_t)c.limbs, b->s[k], 0u, geom};
+                               (uint32_t)c.limbs, b->s[k], stall, geom};
         off += ntt::fused_work_words(c.limbs);
         e = ntt::launch_fused_jobs(ctx, fwd);
         if (e != cudaSuccess) break;
@@ -217,6 +233,30 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         cudaEventRecord(b->join[k], b->s[k]);
         cudaStreamWaitEvent(caller, b->join[k], 0);
     }
+    return cuda_status(e);
+}
+
+// Test hook (not part of the public interface): the next submission's fused
+// launches find their first-pass queue taken and their waits bounded by
+// `max_polls`, so they end with the dependency-timeout status and the data
+// untouched.
+ntt_status ntt_internal_batch_test_stall(ntt_batch* b, uint32_t max_polls)
+{
+    if (!b || max_polls == 0) return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(b->mu);
+    b->test_stall_polls = max_polls;
+    return NTT_OK;
+}
+
+// Library-internal: copy the batch's device status word to `host_word`
+// (page-locked) and clear it, in order on `stream` (the serving loop reads it
+// in its completion callback, without a device synchronisation).
+ntt_status ntt_internal_batch_status_async(ntt_batch* b, uint32_t* host_word, void* stream)
+{
+    if (!b || !host_word) return NTT_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(host_word, b->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(uint32_t), (cudaStream_t)stream);
     return cuda_status(e);
 }
 

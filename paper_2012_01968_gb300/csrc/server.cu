@@ -29,6 +29,8 @@
 
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
 extern "C" ntt_status ntt_internal_batch_reserve(ntt_batch* b, uint64_t words, void* stream);
+extern "C" ntt_status ntt_internal_batch_status_async(ntt_batch* b, uint32_t* host_word, void* stream);
+extern "C" ntt_status ntt_internal_batch_test_stall(ntt_batch* b, uint32_t max_polls);
 
 namespace {
 
@@ -53,6 +55,7 @@ struct Req {
 struct Slot {
     cudaStream_t stream = nullptr;
     ntt_batch* batch = nullptr;
+    uint32_t* status = nullptr;   // page-locked copy of the batch's device status word
     std::vector<Req*> reqs;       // of the batch in flight (empty when free)
     bool busy = false;
     bool finished = false;        // set by the completion callback
@@ -78,6 +81,7 @@ struct ntt_server {
     std::thread worker;
     bool stop = false;
     cudaError_t fatal = cudaSuccess;
+    uint32_t test_stall_polls = 0;    // test hook: the next batch's kernels stall (bounded)
 };
 
 namespace {
@@ -87,9 +91,14 @@ void CUDART_CB on_batch_done(void* arg)
     Slot* s = static_cast<Slot*>(arg);
     ntt_server* srv = s->owner;
     const int64_t t = now_ns();
+    // a bounded wait of the batch's kernels that ran out fails its requests
+    const bool device_error = *static_cast<volatile uint32_t*>(s->status) != 0;
     {
         std::lock_guard<std::mutex> g(srv->mu);
-        for (Req* r : s->reqs) r->t_done = t;
+        for (Req* r : s->reqs) {
+            r->t_done = t;
+            if (device_error) r->status = NTT_ERR_DEVICE;
+        }
         s->finished = true;
     }
     srv->cv_work.notify_one();
@@ -112,6 +121,8 @@ bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
     s.busy = true;
     s.finished = false;
     s.reqs = take;
+    const uint32_t stall = srv->test_stall_polls;
+    srv->test_stall_polls = 0;
     const int64_t t = now_ns();
     for (Req* r : take) r->t_start = t;
     lk.unlock();
@@ -127,6 +138,7 @@ bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
         }
         jobs.push_back(ntt_job{r->r.plan, dev, r->r.batch, r->r.levels, r->r.op, 0});
     }
+    if (stall) ntt_internal_batch_test_stall(s.batch, stall);
     ntt_status st = e == cudaSuccess ? ntt_batch_submit(s.batch, jobs.data(), (uint32_t)jobs.size(), s.stream)
                                      : NTT_ERR_CUDA;
     for (Req* r : take) {
@@ -136,7 +148,8 @@ bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
             if (e != cudaSuccess) st = NTT_ERR_CUDA;
         }
     }
-    if (e == cudaSuccess) e = cudaLaunchHostFunc(s.stream, on_batch_done, &s);
+    if (st == NTT_OK) st = ntt_internal_batch_status_async(s.batch, s.status, s.stream);
+    if (e == cudaSuccess && st == NTT_OK) e = cudaLaunchHostFunc(s.stream, on_batch_done, &s);
     lk.lock();
     if (e != cudaSuccess || st != NTT_OK) {
         // nothing will call back: finish the batch here once the stream drains
@@ -219,6 +232,8 @@ ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
     for (Slot& s : srv->slots) {
         s.owner = srv.get();
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaHostAlloc(&s.status, sizeof(uint32_t), cudaHostAllocDefault);
+        if (e == cudaSuccess) *s.status = 0;
         if (e == cudaSuccess && ntt_batch_create(&s.batch) != NTT_OK) e = cudaErrorMemoryAllocation;
     }
     // every slot's batch gets its fused-kernel work area now: one batch holds
@@ -234,6 +249,7 @@ ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
         for (Slot& s : srv->slots) {
             if (s.batch) ntt_batch_destroy(s.batch);
             if (s.stream) cudaStreamDestroy(s.stream);
+            if (s.status) cudaFreeHost(s.status);
         }
         cudaFree(srv->arena_mem);
         ntt_internal_set_cuda_error(e);
@@ -259,6 +275,7 @@ void ntt_server_destroy(ntt_server* srv)
         if (s.stream) cudaStreamSynchronize(s.stream);
         if (s.batch) ntt_batch_destroy(s.batch);
         if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.status) cudaFreeHost(s.status);
     }
     cudaFree(srv->arena_mem);
     delete srv;
@@ -300,6 +317,16 @@ ntt_status ntt_server_submit(ntt_server* srv, const ntt_request* req, uint64_t* 
         srv->reqs.emplace(r->ticket, std::move(r));
     }
     srv->cv_work.notify_one();
+    return NTT_OK;
+}
+
+// Test hook (not part of the public interface): the next batch the server
+// starts has its fused launches stall, with waits bounded by `max_polls`.
+ntt_status ntt_internal_server_test_stall_next(ntt_server* srv, uint32_t max_polls)
+{
+    if (!srv || max_polls == 0) return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(srv->mu);
+    srv->test_stall_polls = max_polls;
     return NTT_OK;
 }
 

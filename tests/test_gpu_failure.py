@@ -47,3 +47,24 @@ def test_unpublished_dependency_times_out_and_recovers(orc, n):
         torch.cuda.synchronize()
         assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
         assert p.device_status() == 0
+
+
+def test_served_batch_reports_a_stalled_kernel(orc):
+    """A served batch whose kernels' bounded waits run out fails its requests
+    with NTT_ERR_DEVICE (the status word is read back with the batch, without
+    a device synchronisation); the next request on the same server is exact."""
+    N = 1 << 14
+    primes = I.prime_chain(3, 2 * N)
+    data = I.batch_uniform(190, 1, primes, N)
+    lib = G.lib()
+    lib.ntt_internal_server_test_stall_next.restype = ctypes.c_int
+    lib.ntt_internal_server_test_stall_next.argtypes = [ctypes.c_void_p, ctypes.c_uint32]
+    with G.Plan(N, primes) as p, G.Server(1 << 30, max_batch_jobs=1, slots=1) as srv:
+        d = dev(data)
+        assert lib.ntt_internal_server_test_stall_next(srv.handle, 1 << 12) == G.NTT_OK
+        t = srv.submit(p.handle, d, 1, len(primes), G.NTT_OP_FORWARD)
+        assert srv.wait_status(t) == G.NTT_ERR_DEVICE
+        assert np.array_equal(host(d), data)     # no tile was stored
+        t = srv.submit(p.handle, d, 1, len(primes), G.NTT_OP_FORWARD)
+        assert srv.wait_status(t) == G.NTT_OK
+        assert np.array_equal(host(d), oracle_fwd(orc, data, primes))
