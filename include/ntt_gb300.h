@@ -373,7 +373,9 @@ void ntt_server_destroy(ntt_server* server);
 ntt_status ntt_server_submit(ntt_server* server, const ntt_request* request, uint64_t* ticket);
 
 /* Wait up to timeout_ns for a request: its status (NTT_OK, or the error of
- * its batch), or NTT_ERR_TIMEOUT if it is not done yet. */
+ * its batch: NTT_ERR_DEVICE when a bounded wait of the batch's kernels ran
+ * out, its data then being invalid), or NTT_ERR_TIMEOUT if it is not done
+ * yet. */
 ntt_status ntt_server_wait(ntt_server* server, uint64_t ticket, uint64_t timeout_ns);
 
 /* Timestamps of a request (for latency statistics). */
