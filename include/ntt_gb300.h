@@ -200,7 +200,9 @@ enum {
  * Uses a device staging buffer, the streams and per-stream work areas owned by
  * the plan (grown on first use and kept until ntt_plan_destroy); host_in and
  * host_out may be the same array and should be page-locked for full copy
- * bandwidth.  Calls on one plan are serialised.
+ * bandwidth.  Calls on one plan are serialised.  Returns NTT_ERR_DEVICE when
+ * the plan's status word is set after the call (a bounded wait of the kernels
+ * ran out; see ntt_plan_device_status, which still reads and clears it).
  */
 ntt_status ntt_execute_host(const ntt_plan* plan, const uint64_t* host_in, uint64_t* host_out,
                             uint32_t batch, uint32_t ops, void* stream);

@@ -325,7 +325,12 @@ static ntt_status host_pipeline(const ntt_plan* cp, const uint64_t* host_in, uin
     // drain every stream, also after an error, before the staging can be reused
     const cudaError_t se = drain();
     if (e != cudaSuccess) p->h_prev_segs[sb] = 0;
-    return to_status(e != cudaSuccess ? e : se);
+    if (e != cudaSuccess || se != cudaSuccess) return to_status(e != cudaSuccess ? e : se);
+    // a bounded wait of the kernels that ran out (left set for ntt_plan_device_status)
+    uint32_t dev_status = 0;
+    e = cudaMemcpy(&dev_status, p->d_status, sizeof(dev_status), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return to_status(e);
+    return dev_status ? NTT_ERR_DEVICE : NTT_OK;
 }
 
 ntt_status ntt_execute_host(const ntt_plan* cp, const uint64_t* host_in, uint64_t* host_out, uint32_t batch,
