@@ -484,12 +484,15 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
             sub = np.array([x[0] for x in times[first:]], dtype=np.float64)
             done = np.array([x[2] for x in times[first:]], dtype=np.float64)
             lat = (done - sub) / 1e3
+            dev_us = np.array([x[3] for x in times[first:]], dtype=np.float64) / 1e3
             span = (done.max() - sub.min()) / 1e9
             limbs = sum(r.L for r in base[first:])
             return {"limb_ntt_per_s": limbs / span, "requests_per_s": (count - first) / span,
                     "gb_per_s": 16 * sum(sizes[first:]) / span / 1e9, "measured_requests": count - first,
                     "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                                   "mean": float(lat.mean())}}
+                                   "mean": float(lat.mean())},
+                    "batch_device_us": {"p50": float(np.percentile(dev_us, 50)),
+                                        "p99": float(np.percentile(dev_us, 99))}}
 
         cap = run(None)
         out = {"requests": count, "budget_gb": budget_gb, "data": "device-resident, in place",

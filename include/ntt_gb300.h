@@ -358,6 +358,8 @@ typedef struct ntt_request_times {
     int64_t submit_ns;            /* steady-clock times of submission, */
     int64_t start_ns;             /* of admission into a batch, */
     int64_t done_ns;              /* and of completion (0 while not done) */
+    int64_t device_ns;            /* device time of the request's batch, from its
+                                     first to its last operation (0 while not done) */
 } ntt_request_times;
 
 /* Create a server on the current device.  Errors: NTT_ERR_INVALID_ARG,

@@ -90,7 +90,8 @@ class Request(ctypes.Structure):
 
 
 class RequestTimes(ctypes.Structure):
-    _fields_ = [("submit_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+    _fields_ = [("submit_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("device_ns", ctypes.c_int64)]
 
 
 class NttError(RuntimeError):
@@ -605,10 +606,11 @@ class Server:
         _check(self.wait_status(ticket, timeout_s), "ntt_server_wait")
 
     def times(self, ticket: int):
-        """(submit_ns, start_ns, done_ns) on the steady clock."""
+        """(submit_ns, start_ns, done_ns) on the steady clock, and the device
+        time of the request's batch (device_ns)."""
         t = RequestTimes()
         _check(_lib().ntt_server_request_times(self.handle, ticket, ctypes.byref(t)), "ntt_server_request_times")
-        return t.submit_ns, t.start_ns, t.done_ns
+        return t.submit_ns, t.start_ns, t.done_ns, t.device_ns
 
     def close(self):
         if self.handle:

@@ -7,10 +7,12 @@
 // (and, for host-buffer requests, the device arena), and starts a batch in
 // the first free slot.  A slot is a stream with its own batch object:
 // copy-in of the host-buffer requests, one ntt_batch_submit over all the
-// batch's requests, copy-out, then a host callback that timestamps the
-// requests and wakes the scheduler and the waiters.  Requests that arrive
-// while batches are on the device are admitted into the next free slot as
-// memory frees up, so several batches overlap on the device.
+// batch's requests, copy-out, the copy of the batch's kernel status word,
+// then an event.  The scheduler polls the slots' events (no host callback
+// on the device's streams, so a late callback thread cannot hold back the
+// other slots), timestamps finished requests and wakes the waiters.
+// Requests that arrive while batches are on the device are admitted into the
+// next free slot as memory frees up, so several batches overlap on the device.
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
@@ -47,7 +49,7 @@ struct Req {
     size_t bytes = 0;
     size_t arena_off = 0;         // host-buffer requests: device staging offset
     bool host = false;
-    int64_t t_submit = 0, t_start = 0, t_done = 0;
+    int64_t t_submit = 0, t_start = 0, t_done = 0, t_device = 0;
     ntt_status status = NTT_OK;
     bool done = false;
 };
@@ -58,7 +60,9 @@ struct Slot {
     uint32_t* status = nullptr;   // page-locked copy of the batch's device status word
     std::vector<Req*> reqs;       // of the batch in flight (empty when free)
     bool busy = false;
-    bool finished = false;        // set by the completion callback
+    bool finished = false;        // set when the scheduler sees `done` complete
+    cudaEvent_t done = nullptr;   // recorded after the batch's last copy
+    cudaEvent_t begin = nullptr;  // recorded before its first operation (timing)
     struct ntt_server* owner = nullptr;
 };
 
@@ -86,22 +90,45 @@ struct ntt_server {
 
 namespace {
 
-void CUDART_CB on_batch_done(void* arg)
+// Mark the busy slots whose batch has completed (called with the lock held;
+// the event queries run with it released, so that submissions and waits
+// never queue behind a CUDA call).  Returns true when a slot is still running.
+bool poll_slots(ntt_server* srv, std::unique_lock<std::mutex>& lk)
 {
-    Slot* s = static_cast<Slot*>(arg);
-    ntt_server* srv = s->owner;
-    const int64_t t = now_ns();
-    // a bounded wait of the batch's kernels that ran out fails its requests
-    const bool device_error = *static_cast<volatile uint32_t*>(s->status) != 0;
-    {
-        std::lock_guard<std::mutex> g(srv->mu);
-        for (Req* r : s->reqs) {
-            r->t_done = t;
-            if (device_error) r->status = NTT_ERR_DEVICE;
+    bool running = false;
+    std::vector<Slot*> busy;
+    for (Slot& s : srv->slots)
+        if (s.busy && !s.finished) busy.push_back(&s);
+    if (busy.empty()) return false;
+    std::vector<cudaError_t> q(busy.size());
+    lk.unlock();
+    for (size_t i = 0; i < busy.size(); ++i) q[i] = cudaEventQuery(busy[i]->done);
+    lk.lock();
+    for (size_t i = 0; i < busy.size(); ++i) {
+        Slot& s = *busy[i];
+        if (q[i] == cudaErrorNotReady) {
+            running = true;
+            continue;
         }
-        s->finished = true;
+        const cudaError_t qe = q[i];
+        const int64_t t = now_ns();
+        // a bounded wait of the batch's kernels that ran out fails its requests
+        const bool device_error = qe == cudaSuccess && *static_cast<volatile uint32_t*>(s.status) != 0;
+        float ms = 0.f;
+        if (qe == cudaSuccess && cudaEventElapsedTime(&ms, s.begin, s.done) != cudaSuccess) ms = 0.f;
+        for (Req* r : s.reqs) {
+            r->t_done = t;
+            r->t_device = (int64_t)((double)ms * 1e6);
+            if (qe != cudaSuccess) r->status = NTT_ERR_CUDA;
+            else if (device_error) r->status = NTT_ERR_DEVICE;
+        }
+        if (qe != cudaSuccess) {
+            cudaGetLastError();
+            srv->fatal = qe;
+        }
+        s.finished = true;
     }
-    srv->cv_work.notify_one();
+    return running;
 }
 
 // Start one batch in slot `s` from the head of the queue (called with the
@@ -127,7 +154,7 @@ bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
     for (Req* r : take) r->t_start = t;
     lk.unlock();
 
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(s.begin, s.stream);
     std::vector<ntt_job> jobs;
     jobs.reserve(take.size());
     for (Req* r : take) {
@@ -149,7 +176,7 @@ bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
         }
     }
     if (st == NTT_OK) st = ntt_internal_batch_status_async(s.batch, s.status, s.stream);
-    if (e == cudaSuccess && st == NTT_OK) e = cudaLaunchHostFunc(s.stream, on_batch_done, &s);
+    if (e == cudaSuccess && st == NTT_OK) e = cudaEventRecord(s.done, s.stream);
     lk.lock();
     if (e != cudaSuccess || st != NTT_OK) {
         // nothing will call back: finish the batch here once the stream drains
@@ -193,6 +220,7 @@ void scheduler(ntt_server* srv)
     cudaSetDevice(srv->device);
     std::unique_lock<std::mutex> lk(srv->mu);
     for (;;) {
+        const bool running = poll_slots(srv, lk);
         retire(srv);
         bool started = false;
         for (Slot& s : srv->slots)
@@ -201,8 +229,9 @@ void scheduler(ntt_server* srv)
         for (const Slot& s : srv->slots) inflight |= s.busy;
         if (srv->stop && srv->pending.empty() && !inflight) break;
         if (started) continue;
-        // wait for a completion callback or a new request
-        srv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+        // poll again soon while batches run; otherwise wait for a request
+        if (running) srv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        else srv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
     }
 }
 
@@ -233,6 +262,8 @@ ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
         s.owner = srv.get();
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaHostAlloc(&s.status, sizeof(uint32_t), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaEventCreate(&s.done);
+        if (e == cudaSuccess) e = cudaEventCreate(&s.begin);
         if (e == cudaSuccess) *s.status = 0;
         if (e == cudaSuccess && ntt_batch_create(&s.batch) != NTT_OK) e = cudaErrorMemoryAllocation;
     }
@@ -250,6 +281,9 @@ ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
             if (s.batch) ntt_batch_destroy(s.batch);
             if (s.stream) cudaStreamDestroy(s.stream);
             if (s.status) cudaFreeHost(s.status);
+            if (s.done) cudaEventDestroy(s.done);
+        if (s.begin) cudaEventDestroy(s.begin);
+            if (s.begin) cudaEventDestroy(s.begin);
         }
         cudaFree(srv->arena_mem);
         ntt_internal_set_cuda_error(e);
@@ -276,6 +310,7 @@ void ntt_server_destroy(ntt_server* srv)
         if (s.batch) ntt_batch_destroy(s.batch);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.status) cudaFreeHost(s.status);
+        if (s.done) cudaEventDestroy(s.done);
     }
     cudaFree(srv->arena_mem);
     delete srv;
@@ -354,6 +389,7 @@ ntt_status ntt_server_request_times(ntt_server* srv, uint64_t ticket, ntt_reques
     times->submit_ns = r->t_submit;
     times->start_ns = r->t_start;
     times->done_ns = r->done ? r->t_done : 0;
+    times->device_ns = r->done ? r->t_device : 0;
     return NTT_OK;
 }
 

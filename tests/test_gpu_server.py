@@ -75,8 +75,9 @@ def test_mixed_requests_equal_alone(plans):
         times = [srv.times(t) for t in tickets]
     for k, (a, b) in enumerate(zip(mix, alone)):
         assert torch.equal(a, b), f"request {k} differs from the same request alone"
-    for s, st, d in times:
+    for s, st, d, dev_ns in times:
         assert 0 < s <= st <= d
+        assert 0 < dev_ns <= d - st              # the batch's device time fits its wall time
 
 
 def test_host_requests_through_arena(plans, orc):
