@@ -63,7 +63,6 @@ struct Slot {
     bool finished = false;        // set when the scheduler sees `done` complete
     cudaEvent_t done = nullptr;   // recorded after the batch's last copy
     cudaEvent_t begin = nullptr;  // recorded before its first operation (timing)
-    struct ntt_server* owner = nullptr;
 };
 
 using Arena = ntt::host::Arena;
@@ -259,7 +258,6 @@ ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
     srv->arena.reset(e == cudaSuccess ? arena : 0);
     srv->slots.resize(srv->opts.slots);
     for (Slot& s : srv->slots) {
-        s.owner = srv.get();
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaHostAlloc(&s.status, sizeof(uint32_t), cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaEventCreate(&s.done);
