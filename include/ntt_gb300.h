@@ -50,7 +50,7 @@ extern "C" {
 typedef enum ntt_status {
     NTT_OK = 0,
     NTT_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad option */
-    NTT_ERR_BAD_PRIME = 2,    /* composite, q != 1 mod 2N, or q outside (2^32, 2^60) */
+    NTT_ERR_BAD_PRIME = 2,    /* composite, q != 1 mod 2N, or q outside (2^32, 2^60) (32-bit plans: q >= 2^28) */
     NTT_ERR_MISALIGNED = 3,   /* a device pointer is not 16-byte aligned */
     NTT_ERR_CUDA = 4,         /* a CUDA runtime call failed */
     NTT_ERR_OOM = 5,          /* device or host allocation failed */
