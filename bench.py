@@ -640,7 +640,7 @@ def word_size(G, torch, N, primes64, seed, reps=100):
     in 64-bit words, or from 28-bit primes in 32-bit words (about twice as
     many limbs, at least as many bits), forward + inverse per step on one
     stream.  Each word size with one launch per pass (table twiddles) and with
-    the fused kernel (the 64-bit default, OT1; the 32-bit one, table)."""
+    the fused kernel (OT1, the default of both; 32-bit also with the table)."""
     import math
     bits64 = sum(math.log2(q) for q in primes64)
     cand = I.prime_chain(4 * len(primes64), 2 * N, below=1 << 28)
@@ -684,8 +684,10 @@ def word_size(G, torch, N, primes64, seed, reps=100):
     src32 = torch.from_numpy(h32.astype(np.uint32).view(np.int32).copy()).cuda()
     nb32 = max(2, -(-2 * L2_BYTES // (src32.numel() * 4)) + 1)
     b32 = [src32.clone() for _ in range(nb32)]
-    for name, kern in (("u32_per_pass_us", G.NTT_KERNEL_PER_PASS), ("u32_fused_us", G.NTT_KERNEL_FUSED)):
-        with G.Plan32(N, p32, kern) as p:
+    for name, kern, mode in (("u32_per_pass_us", G.NTT_KERNEL_PER_PASS, G.NTT_TWIDDLE_TABLE),
+                             ("u32_fused_table_us", G.NTT_KERNEL_FUSED, G.NTT_TWIDDLE_TABLE),
+                             ("u32_fused_us", G.NTT_KERNEL_FUSED, G.NTT_TWIDDLE_OT)):
+        with G.Plan32(N, p32, kern, mode) as p:
             def step32(i):
                 b = b32[i % nb32].data_ptr()
                 _ok(G, lib.ntt_forward32(p.handle, b, 1, s.cuda_stream), "u32 forward")

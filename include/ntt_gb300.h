@@ -423,21 +423,26 @@ ntt_status ntt_autotune(uint32_t N, const uint64_t* primes, uint32_t L, uint32_t
  * built from twice as many primes of half the width).  A separate plan type
  * over primes q < 2^28 with q = 1 mod 2N, residues held in uint32_t.  The
  * transform is the same negacyclic NTT as ntt_forward / ntt_inverse (same psi
- * rule: psi = g^{(q-1)/2N} for the smallest generator g of Z_q^*), with table
- * twiddles: for N >= 2^13 the fused two-pass kernel (NTT_KERNEL_FUSED, the
- * default) or one launch per pass (NTT_KERNEL_PER_PASS); one pass below.
+ * rule: psi = g^{(q-1)/2N} for the smallest generator g of Z_q^*): for
+ * N >= 2^13 the fused two-pass kernel (NTT_KERNEL_FUSED, the default) with
+ * table twiddles or the last stage twiddled on the fly (OT), or one launch per
+ * pass (NTT_KERNEL_PER_PASS, table); one pass below (table).
  */
 typedef struct ntt_plan32 ntt_plan32;
 
 /*
  * Create a 32-bit plan.  N as for ntt_plan_create; primes: host array of L
  * primes with q = 1 mod 2N and q < 2^28 (copied); 1 <= L <= 4096; kernel:
- * NTT_KERNEL_AUTO (= FUSED), NTT_KERNEL_FUSED or NTT_KERNEL_PER_PASS.  Device
- * tables of 8 * N * L bytes and a work area, created on the current CUDA
- * device.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME, NTT_ERR_OOM,
- * NTT_ERR_CUDA; *out is left untouched on error.
+ * NTT_KERNEL_AUTO (= FUSED), NTT_KERNEL_FUSED or NTT_KERNEL_PER_PASS;
+ * twiddle_mode: NTT_TWIDDLE_AUTO (OT of the last stage for fused two-pass
+ * plans, table otherwise), NTT_TWIDDLE_TABLE or NTT_TWIDDLE_OT (fused two-pass
+ * plans only).  Device tables of 8 * N * L bytes (table) or about half (OT)
+ * and a work area, created on the current CUDA device.  Errors:
+ * NTT_ERR_INVALID_ARG, NTT_ERR_BAD_PRIME, NTT_ERR_OOM, NTT_ERR_CUDA; *out is
+ * left untouched on error.
  */
-ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L, uint32_t kernel);
+ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint32_t* primes, uint32_t L, uint32_t kernel,
+                             uint32_t twiddle_mode);
 
 /* Free a 32-bit plan.  NULL is allowed.  Work that uses it must have finished. */
 void ntt_plan32_destroy(ntt_plan32* plan);

@@ -172,7 +172,7 @@ def _lib():
             L.ntt_autotune.argtypes = [_u32, _u64p, _u32, _u32, _u32, ctypes.POINTER(PlanOpts),
                                        ctypes.POINTER(TuneEntry), _u32, ctypes.POINTER(_u32)]
             L.ntt_plan32_create.restype = S
-            L.ntt_plan32_create.argtypes = [ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32), _u32, _u32]
+            L.ntt_plan32_create.argtypes = [ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32), _u32, _u32, _u32]
             L.ntt_plan32_device_status.restype = S
             L.ntt_plan32_device_status.argtypes = [_vp, ctypes.POINTER(_u32)]
             L.ntt_plan32_destroy.restype = None
@@ -398,18 +398,18 @@ def ntt_autotune(N: int, primes, batch: int = 1, reps: int = 0, entries: bool = 
     return best, out
 
 
-def ntt_plan32_create_status(N: int, primes, kernel: int = NTT_KERNEL_AUTO):
+def ntt_plan32_create_status(N: int, primes, kernel: int = NTT_KERNEL_AUTO, twiddle_mode: int = NTT_TWIDDLE_AUTO):
     """Create a 32-bit plan; returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
     arr = (_u32 * max(1, len(primes)))(*primes)
     out = _vp()
-    st = _lib().ntt_plan32_create(ctypes.byref(out), N, arr if primes else None, len(primes), kernel)
+    st = _lib().ntt_plan32_create(ctypes.byref(out), N, arr if primes else None, len(primes), kernel, twiddle_mode)
     return st, (int(out.value) if out.value else 0)
 
 
-def ntt_plan32_create(N: int, primes, kernel: int = NTT_KERNEL_AUTO) -> int:
+def ntt_plan32_create(N: int, primes, kernel: int = NTT_KERNEL_AUTO, twiddle_mode: int = NTT_TWIDDLE_AUTO) -> int:
     """Create a 32-bit plan (primes q < 2^28); returns the handle.  Raises NttError."""
-    st, h = ntt_plan32_create_status(N, primes, kernel)
+    st, h = ntt_plan32_create_status(N, primes, kernel, twiddle_mode)
     _check(st, "ntt_plan32_create")
     return h
 
@@ -496,11 +496,11 @@ class Plan:
 class Plan32:
     """RAII wrapper over a 32-bit plan handle (residues in int32/uint32 tensors)."""
 
-    def __init__(self, N: int, primes, kernel: int = NTT_KERNEL_AUTO):
+    def __init__(self, N: int, primes, kernel: int = NTT_KERNEL_AUTO, twiddle_mode: int = NTT_TWIDDLE_AUTO):
         self.N = N
         self.primes = [int(p) for p in primes]
         self.L = len(self.primes)
-        self.handle = ntt_plan32_create(N, self.primes, kernel)
+        self.handle = ntt_plan32_create(N, self.primes, kernel, twiddle_mode)
 
     def device_status(self) -> int:
         return ntt_plan32_device_status(self.handle)

@@ -243,13 +243,16 @@ struct Fused32Launch {
     u32* work;               // zero, fused_work_words(work_limbs) words
     u32 work_limbs;
     cudaStream_t stream;
+    u32 ots;                 // last stages twiddled on the fly (0 or 1)
+    const Tw32* ota;         // OT factors of this direction (ots > 0)
+    const Tw32* otb;
 };
 
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD>
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS>
 cudaError_t launch_fused32_dir(const Fused32Launch& c)
 {
     using F = FusedCfg<P1, P2, LOGC_R, KMAX, u32>;
-    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, 0, 1, u32>;
+    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS, 1, u32>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int occ = 0;
@@ -266,8 +269,8 @@ cudaError_t launch_fused32_dir(const Fused32Launch& c)
     if (e != cudaSuccess) return e;
     a.job[0].primes = c.primes;
     a.job[0].tw = c.tw;
-    a.job[0].ota = nullptr;
-    a.job[0].otb = nullptr;
+    a.job[0].ota = OTS ? c.ota : nullptr;
+    a.job[0].otb = OTS ? c.otb : nullptr;
     a.job[0].tw_len = c.tw_len;
     a.job[0].L = c.L;
     a.job[0].limb0 = 0;
@@ -288,7 +291,13 @@ cudaError_t launch_fused32_dir(const Fused32Launch& c)
 template <int P1, int P2, int LOGC_R, int KMAX>
 cudaError_t launch_fused32(const Fused32Launch& c, bool fwd)
 {
-    return fwd ? launch_fused32_dir<P1, P2, LOGC_R, KMAX, true>(c) : launch_fused32_dir<P1, P2, LOGC_R, KMAX, false>(c);
+    if (c.ots == 0)
+        return fwd ? launch_fused32_dir<P1, P2, LOGC_R, KMAX, true, 0>(c)
+                   : launch_fused32_dir<P1, P2, LOGC_R, KMAX, false, 0>(c);
+    if (c.ots == 1)
+        return fwd ? launch_fused32_dir<P1, P2, LOGC_R, KMAX, true, 1>(c)
+                   : launch_fused32_dir<P1, P2, LOGC_R, KMAX, false, 1>(c);
+    return cudaErrorInvalidValue;
 }
 
 // A single call: one launch per pass, or the fused kernel with one job.

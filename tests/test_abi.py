@@ -101,6 +101,14 @@ def test_plan32_rejects_kernel(lib, kernel):
     assert st == G.NTT_ERR_INVALID_ARG and h == 0
 
 
+@pytest.mark.parametrize("N,kernel,mode", [(1 << 12, G.NTT_KERNEL_AUTO, G.NTT_TWIDDLE_OT),       # one pass
+                                           (1 << 13, G.NTT_KERNEL_PER_PASS, G.NTT_TWIDDLE_OT),  # per pass: table
+                                           (1 << 13, G.NTT_KERNEL_AUTO, 3)])
+def test_plan32_rejects_twiddle_mode(lib, N, kernel, mode):
+    st, h = G.ntt_plan32_create_status(N, SMALL[:1], kernel, mode)
+    assert st == G.NTT_ERR_INVALID_ARG and h == 0
+
+
 def test_plan32_primes_are_28_bit():
     assert all((1 << 27) <= q < (1 << 28) and q % (1 << 13) == 1 and I.is_prime(q) for q in SMALL)
     assert SMALL[1] % (1 << 14) != 1
@@ -117,7 +125,7 @@ def test_null_arguments_rejected(lib):
     assert lib.ntt_forward32(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_inverse32(None, None, 1, None) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_plan32_psi(None, 0, None) == G.NTT_ERR_INVALID_ARG
-    assert lib.ntt_plan32_create(None, 16, None, 1, 0) == G.NTT_ERR_INVALID_ARG
+    assert lib.ntt_plan32_create(None, 16, None, 1, 0, 0) == G.NTT_ERR_INVALID_ARG
     assert lib.ntt_plan32_device_status(None, None) == G.NTT_ERR_INVALID_ARG
     best = G.PlanOpts()
     assert lib.ntt_autotune(16, None, 1, 1, 1, ctypes.byref(best), None, 0, None) == G.NTT_ERR_INVALID_ARG

@@ -38,9 +38,9 @@ def host32(t):
     return t.cpu().numpy().view(np.uint32).astype(np.uint64)
 
 
-def _roundtrip(orc, N, primes, batch, seed, kernel=G.NTT_KERNEL_AUTO):
+def _roundtrip(orc, N, primes, batch, seed, kernel=G.NTT_KERNEL_AUTO, mode=G.NTT_TWIDDLE_AUTO):
     data = I.batch_uniform(seed, batch, primes, N)
-    with G.Plan32(N, primes, kernel) as p:
+    with G.Plan32(N, primes, kernel, mode) as p:
         d = dev32(data)
         p.forward(d, batch)
         torch.cuda.synchronize()
@@ -58,6 +58,13 @@ def _roundtrip(orc, N, primes, batch, seed, kernel=G.NTT_KERNEL_AUTO):
 def test_every_size(orc, n):
     N = 1 << n
     _roundtrip(orc, N, primes28(N, 3), 2, 300 + n)
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+def test_fused_table_twiddles(orc, n):
+    """The fused kernel with the full table instead of OT (the AUTO choice)."""
+    N = 1 << n
+    _roundtrip(orc, N, primes28(N, 3), 2, 370 + n, G.NTT_KERNEL_FUSED, G.NTT_TWIDDLE_TABLE)
 
 
 @pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
