@@ -278,4 +278,25 @@ def pin_batch_driver(o):
         assert list(prod[0, l]) == want
 
 
+def pin_word32_primes(o):
+    """The oracle on the 28-bit primes the 32-bit word path uses (below 2^28,
+    q = 1 mod 2N): radix-2 equals the definition at small N, psi is a
+    primitive 2N-th root, and the batch driver round-trips at N = 2^12."""
+    rng = random.Random(21)
+    for N in (8, 64):
+        for q in I.prime_chain(2, 2 * N, below=1 << 28):
+            a = _rand_vec(rng, N, q)
+            A = o.ntt_schoolbook(a, q)
+            assert list(o.ntt_radix2(a, q)) == list(A), (q, N)
+            assert list(o.intt_radix2(A, q)) == list(a)
+            psi = o.psi(q, N)
+            assert pow(psi, N, q) == q - 1 and pow(psi, 2 * N, q) == 1
+    N = 1 << 12
+    primes = I.prime_chain(3, 2 * N, below=1 << 28)
+    data = np.stack([_rand_vec(rng, N, q) for q in primes])[None]
+    fwd = o.ntt_batch(data, primes, +1, 2)
+    assert (o.ntt_batch(fwd, primes, -1, 2) == data).all()
+    assert (fwd[0, 1] == o.ntt_radix2(data[0, 1], primes[1])).all()
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]
