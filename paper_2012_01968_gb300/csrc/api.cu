@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(256) pointwise_kernel(const PrimeDev* __restri
         const ulonglong2 x = reinterpret_cast<const ulonglong2*>(a)[i];
         const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b)[i];
         ulonglong2 r;
-        r.x = canon<3>(mulmod_barrett(x.x, y.x, p.q, p.mu, p.k), p.q, p.mbar);
-        r.y = canon<3>(mulmod_barrett(x.y, y.y, p.q, p.mu, p.k), p.q, p.mbar);
+        r.x = canon<3>(mulmod_barrett(x.x, y.x, p.q, p.mu, p.k), p.q, p.rc, p.rsh);
+        r.y = canon<3>(mulmod_barrett(x.y, y.y, p.q, p.mu, p.k), p.q, p.rc, p.rsh);
         reinterpret_cast<ulonglong2*>(out)[i] = r;
     }
 }

@@ -39,61 +39,34 @@ __device__ __forceinline__ u64 shoup_lazy(u64 y, u64 w, u64 wp, u64 q)
     return y * w - qhat * q;      // exact value < 4q, so the wrapped difference is it
 }
 
-// The same product with the quotient's two middle partial products taken
-// whole (IMAD.WIDE, half rate on sm_103a, where IMAD.HI is quarter rate) and
-// summed with their carry:
-//   qhat = yh*wh' + floor((yh*wl' + yl*wh') / 2^32)
-//   r    = lo64(y*w + qhat*(2^64 - q))
-// Only yl*wl' (< 2^64) is dropped, so floor(y w / q) - qhat <= 2 and r lies in
-// [0, 3q) for every y < 2^64.  nq = 2^64 - q.
-__device__ __forceinline__ u64 shoup3(u64 y, u64 w, u64 wp, u64 nq)
+// x in [0, 2c) -> [0, c), for c <= 2^63: x - c wraps to at least 2^63 exactly
+// when x < c, so its sign bit decides (one test of the high word).
+__device__ __forceinline__ u64 csub(u64 x, u64 c)
 {
-    const u32 yl = lo32(y), yh = hi32(y), wl = lo32(wp), wh = hi32(wp);
-    u64 t1, t2;
-    asm("mul.wide.u32 %0, %1, %2;" : "=l"(t1) : "r"(yh), "r"(wl));
-    asm("mul.wide.u32 %0, %1, %2;" : "=l"(t2) : "r"(yl), "r"(wh));
-    u32 mid_hi, carry;
-    asm("{\n\t.reg .u32 t;\n\t"
-        "add.cc.u32 t, %2, %3;\n\t"
-        "addc.cc.u32 %0, %4, %5;\n\t"
-        "addc.u32 %1, 0, 0;\n\t}"
-        : "=r"(mid_hi), "=r"(carry)
-        : "r"(lo32(t1)), "r"(lo32(t2)), "r"(hi32(t1)), "r"(hi32(t2)));
-    u64 qhat;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(qhat) : "r"(yh), "r"(wh), "l"(((u64)carry << 32) | mid_hi));
-    return y * w + qhat * nq;
+    const u64 d = x - c;
+    return (long long)d < 0 ? x : d;
 }
 
-// x mod q into [0, 3q) for any 64-bit x, the quotient estimate taken from a
-// whole 32x32 product (see shoup3).  zero must be a run-time 0.
-__device__ __forceinline__ u64 reduce3w(u64 x, u64 nq, u32 mbar, u64 zero)
+// x mod q into [0, 2q) for x < 16 q.  k is the bit length of q, sh = k - 28,
+// rc = floor(2^(k+31) / q) (2^31 <= rc < 2^32).  The quotient estimate
+//   kq = floor(floor(x / 2^sh) rc / 2^59)
+// uses the top 32 bits of x (x < 2^(k+4)).  Dropping the low sh bits of x
+// loses under 2^sh / q < 2^-27 of a quotient unit and truncating rc under
+// 2^32 / 2^59, so kq is floor(x / q) or one less.
+__device__ __forceinline__ u64 reduce2(u64 x, u64 q, u32 rc, u32 sh)
 {
-    u64 p;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(p) : "r"(hi32(x)), "r"(mbar), "l"(zero));
-    return x + (u64)hi32(p) * nq;
+    u32 xs;
+    asm("shf.r.clamp.b32 %0, %1, %2, %3;" : "=r"(xs) : "r"(lo32(x)), "r"(hi32(x)), "r"(sh));
+    const u32 kq = hi32(mul_wide(xs, rc)) >> 27;
+    return x - (u64)kq * q;
 }
-
-// x mod q into [0, 3q) for any 64-bit x; mbar = floor(2^64 / q) < 2^32.
-__device__ __forceinline__ u64 reduce3(u64 x, u64 q, u32 mbar)
-{
-    // qh = floor(xh mbar / 2^32) is at most 2 below floor(x / q): [0, 3q)
-    const u32 qh = __umulhi(hi32(x), mbar);
-    return x - (u64)qh * q;
-}
-
-// x in [0, 2c) -> [0, c)
-__device__ __forceinline__ u64 csub(u64 x, u64 c) { return x >= c ? x - c : x; }
 
 // Bring x in [0, X q) to [0, q), X a compile-time bound <= 16.
 template <int X>
-__device__ __forceinline__ u64 canon(u64 x, u64 q, u32 mbar)
+__device__ __forceinline__ u64 canon(u64 x, u64 q, u32 rc, u32 sh)
 {
     static_assert(X >= 1 && X <= 16, "range");
-    if (X > 4) {
-        x = reduce3(x, q, mbar);            // [0, 3q)
-        x = csub(x, 2 * q);                 // [0, 2q)
-        return csub(x, q);
-    }
+    if (X > 4) return csub(reduce2(x, q, rc, sh), q);
     if (X > 2) x = csub(x, 2 * q);
     if (X > 1) x = csub(x, q);
     return x;
@@ -117,7 +90,7 @@ __host__ __device__ constexpr int ct_range_after(int X, int stages)
 
 template <int X>
 __device__ __forceinline__ void ct_bfly(u64& x, u64& y, const u64 w, const u64 wp,
-                                        const u64 q, const u64 q4, const u32 mbar)
+                                        const u64 q, const u64 q4)
 {
     u64 a = x;
     if (ct_reduces(X)) a = csub(a, q4 << 1);
@@ -130,7 +103,7 @@ __device__ __forceinline__ void ct_bfly(u64& x, u64& y, const u64 w, const u64 w
 // t = (y * w1) * w2, each a Shoup product
 template <int X>
 __device__ __forceinline__ void ct_bfly_ot(u64& x, u64& y, const Tw f1, const Tw f2,
-                                           const u64 q, const u64 q4, const u32 mbar)
+                                           const u64 q, const u64 q4)
 {
     u64 a = x;
     if (ct_reduces(X)) a = csub(a, q4 << 1);
@@ -162,7 +135,7 @@ __host__ __device__ constexpr int gs_range_after(int X, int stages)
 // difference is taken as y - x.
 template <int X, bool NEG>
 __device__ __forceinline__ void gs_bfly(u64& x, u64& y, const u64 w, const u64 wp,
-                                        const u64 q, const u32 mbar)
+                                        const u64 q)
 {
     static_assert(X <= 8, "GS inputs must stay below 8q");
     const u64 Xq = (u64)X * q;
@@ -175,7 +148,7 @@ __device__ __forceinline__ void gs_bfly(u64& x, u64& y, const u64 w, const u64 w
 
 template <int X, bool NEG>
 __device__ __forceinline__ void gs_bfly_ot(u64& x, u64& y, const Tw f1, const Tw f2,
-                                           const u64 q, const u32 mbar)
+                                           const u64 q)
 {
     static_assert(X <= 8, "GS inputs must stay below 8q");
     const u64 Xq = (u64)X * q;
@@ -216,10 +189,11 @@ __device__ __forceinline__ u32 shoup_lazy(u32 y, u32 w, u32 wp, u32 q)
     return y * w - qhat * q;      // exact value < 2q
 }
 
-__device__ __forceinline__ u32 csub(u32 x, u32 c) { return x >= c ? x - c : x; }
+// x in [0, 2c) -> [0, c): x - c wraps above x exactly when x < c
+__device__ __forceinline__ u32 csub(u32 x, u32 c) { return min(x, x - c); }
 
 template <int X>
-__device__ __forceinline__ u32 canon(u32 x, u32 q, u32)
+__device__ __forceinline__ u32 canon(u32 x, u32 q, u32, u32)
 {
     static_assert(X >= 1 && X <= 16, "range");
     if (X > 8) x = csub(x, q << 3);
@@ -230,8 +204,7 @@ __device__ __forceinline__ u32 canon(u32 x, u32 q, u32)
 }
 
 template <int X>
-__device__ __forceinline__ void ct_bfly(u32& x, u32& y, const u32 w, const u32 wp, const u32 q, const u32 q4,
-                                        const u32)
+__device__ __forceinline__ void ct_bfly(u32& x, u32& y, const u32 w, const u32 wp, const u32 q, const u32 q4)
 {
     u32 a = x;
     if (ct_reduces(X)) a = csub(a, q4 << 1);
@@ -242,7 +215,7 @@ __device__ __forceinline__ void ct_bfly(u32& x, u32& y, const u32 w, const u32 w
 
 template <int X>
 __device__ __forceinline__ void ct_bfly_ot(u32& x, u32& y, const Tw32 f1, const Tw32 f2, const u32 q,
-                                           const u32 q4, const u32)
+                                           const u32 q4)
 {
     u32 a = x;
     if (ct_reduces(X)) a = csub(a, q4 << 1);
@@ -252,7 +225,7 @@ __device__ __forceinline__ void ct_bfly_ot(u32& x, u32& y, const Tw32 f1, const 
 }
 
 template <int X, bool NEG>
-__device__ __forceinline__ void gs_bfly(u32& x, u32& y, const u32 w, const u32 wp, const u32 q, const u32)
+__device__ __forceinline__ void gs_bfly(u32& x, u32& y, const u32 w, const u32 wp, const u32 q)
 {
     static_assert(X <= 8, "GS inputs must stay below 8q");
     const u32 Xq = (u32)X * q;
@@ -264,7 +237,7 @@ __device__ __forceinline__ void gs_bfly(u32& x, u32& y, const u32 w, const u32 w
 }
 
 template <int X, bool NEG>
-__device__ __forceinline__ void gs_bfly_ot(u32& x, u32& y, const Tw32 f1, const Tw32 f2, const u32 q, const u32)
+__device__ __forceinline__ void gs_bfly_ot(u32& x, u32& y, const Tw32 f1, const Tw32 f2, const u32 q)
 {
     static_assert(X <= 8, "GS inputs must stay below 8q");
     const u32 Xq = (u32)X * q;

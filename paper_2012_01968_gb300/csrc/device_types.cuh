@@ -10,17 +10,19 @@ struct __align__(16) PrimeDev {
     u64 mu;          // floor(2^{2k} / q), Barrett constant for data x data
     Tw ninv;         // N^{-1} mod q and its Shoup companion
     Tw w1ninv;       // Psi[1] * N^{-1} mod q (the last inverse stage, applied to y - x)
-    u32 mbar;        // floor(2^64 / q) (< 2^32 because q > 2^32)
+    u32 rc;          // floor(2^(k+31) / q), the final reduction's reciprocal
     u32 k;           // bit length of q
+    u32 rsh;         // k - 28, its shift
 };
 
 // Per-prime constants of a 32-bit plan (primes q < 2^28).
 struct __align__(16) PrimeDev32 {
     u32 q;
-    u32 mbar;        // unused by the 32-bit kernels (kept for a common shape)
+    u32 rc;          // unused by the 32-bit kernels (kept for a common shape)
     Tw32 ninv;       // N^{-1} mod q and its Shoup companion
     Tw32 w1ninv;     // Psi[1] * N^{-1} mod q (the last inverse stage, applied to y - x)
     u32 k;           // bit length of q
+    u32 rsh;         // unused by the 32-bit kernels
 };
 
 // Word-size traits of the pass kernels: the data word, the twiddle pair and

@@ -19,7 +19,7 @@ namespace {
 
 template <int K, int r, int X>
 __device__ __forceinline__ void hr_fwd(u64 (&x)[1 << K], const Tw* __restrict__ tw, const u32 s0, const u32 b,
-                                       const u64 q, const u64 q4, const u32 mbar)
+                                       const u64 q, const u64 q4)
 {
     if constexpr (r < K) {
         constexpr int h = 1 << (K - 1 - r);
@@ -28,9 +28,9 @@ __device__ __forceinline__ void hr_fwd(u64 (&x)[1 << K], const Tw* __restrict__ 
         for (int g = 0; g < (1 << r); ++g) {
             const Tw w = tw[(1u << s) + (b << r) + (u32)g];
 #pragma unroll
-            for (int i = 0; i < h; ++i) ct_bfly<X>(x[g * 2 * h + i], x[g * 2 * h + i + h], w.w, w.wp, q, q4, mbar);
+            for (int i = 0; i < h; ++i) ct_bfly<X>(x[g * 2 * h + i], x[g * 2 * h + i + h], w.w, w.wp, q, q4);
         }
-        hr_fwd<K, r + 1, ct_next(X)>(x, tw, s0, b, q, q4, mbar);
+        hr_fwd<K, r + 1, ct_next(X)>(x, tw, s0, b, q, q4);
     }
 }
 
@@ -54,7 +54,7 @@ __device__ __forceinline__ void hr_inv(u64 (&x)[1 << K], const Tw* __restrict__ 
                 const u32 jj = (b << r) + (u32)g;
                 const Tw w = tw[(2u << s) - 1u - jj];
 #pragma unroll
-                for (int i = 0; i < h; ++i) gs_bfly<X, true>(x[g * 2 * h + i], x[g * 2 * h + i + h], w.w, w.wp, q, pr.mbar);
+                for (int i = 0; i < h; ++i) gs_bfly<X, true>(x[g * 2 * h + i], x[g * 2 * h + i + h], w.w, w.wp, q);
             }
         }
         hr_inv<K, r - 1, gs_next(X), S0>(x, tw, s0, b, pr, q);
@@ -93,14 +93,14 @@ __global__ void __launch_bounds__(256) high_radix_kernel(u64* __restrict__ data,
             for (int i = 0; i < E; ++i) x[i] = d[base + ((u32)i << nb)];
         }
         if constexpr (FWD) {
-            hr_fwd<K, 0, 1>(x, t, s0, b, q, q << 2, pr.mbar);
+            hr_fwd<K, 0, 1>(x, t, s0, b, q, q << 2);
 #pragma unroll
-            for (int i = 0; i < E; ++i) x[i] = canon<ct_range_after(1, K)>(x[i], q, pr.mbar);
+            for (int i = 0; i < E; ++i) x[i] = canon<ct_range_after(1, K)>(x[i], q, pr.rc, pr.rsh);
         } else {
             hr_inv<K, K - 1, 1, S0>(x, t, s0, b, pr, q);
             constexpr int XO = S0 ? 4 : gs_range_after(1, K);
 #pragma unroll
-            for (int i = 0; i < E; ++i) x[i] = canon<XO>(x[i], q, pr.mbar);
+            for (int i = 0; i < E; ++i) x[i] = canon<XO>(x[i], q, pr.rc, pr.rsh);
         }
         if (nb == 0 && E >= 2) {
 #pragma unroll

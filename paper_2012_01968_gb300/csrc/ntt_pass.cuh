@@ -85,7 +85,7 @@ struct ItemCtxT {
     const TwT* ota;      // OT A factors for this prime (smem)
     const TwT* otb;      // OT B factors for this prime (global)
     W q, q4;
-    u32 mbar;
+    u32 rc, rsh;         // final reduction constants
     u32 u;               // upper index bits (which 2^{n-s0} block)
     u32 hi;              // bits of v above the round digit
     u32 s0;              // first stage of the pass
@@ -138,13 +138,13 @@ __device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
                 const auto f2 = c.ota[(1u << sl) + jlo];
 #pragma unroll
                 for (int i = 0; i < half; ++i)
-                    ct_bfly_ot<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q, c.q4, c.mbar);
+                    ct_bfly_ot<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q, c.q4);
             } else {
                 const u32 idx = TWG ? (1u << (c.s0 + sl)) + (c.u << sl) + jlo : (1u << sl) + jlo;
                 const auto t = c.tw[idx];
 #pragma unroll
                 for (int i = 0; i < half; ++i)
-                    ct_bfly<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.q4, c.mbar);
+                    ct_bfly<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.q4);
             }
         }
         fwd_stages<P, KR, K0, k + 1, ct_next(X), OTS, TWG, E>(x, c);
@@ -176,7 +176,7 @@ __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c)
                     const auto f2 = c.ota[(1u << sl) + jlo];
 #pragma unroll
                     for (int i = 0; i < half; ++i)
-                        gs_bfly_ot<X, false>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q, c.mbar);
+                        gs_bfly_ot<X, false>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q);
                 } else {
                     // Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j]
                     const u32 j = TWG ? (c.u << sl) + jlo : jlo;
@@ -184,7 +184,7 @@ __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c)
                     const auto t = c.tw[idx];
 #pragma unroll
                     for (int i = 0; i < half; ++i)
-                        gs_bfly<X, true>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.mbar);
+                        gs_bfly<X, true>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q);
                 }
             }
         }
@@ -242,7 +242,7 @@ __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base
             inv_stages<P, KR, K0, KR - 1, XR, OTS, HAS_S0, TWG, E>(x, c);
         if constexpr (CANON > 0) {
 #pragma unroll
-            for (int i = 0; i < E; ++i) x[i] = canon<CANON>(x[i], c.q, c.mbar);
+            for (int i = 0; i < E; ++i) x[i] = canon<CANON>(x[i], c.q, c.rc, c.rsh);
         }
         if constexpr (PAIRS) {
 #pragma unroll
@@ -302,7 +302,8 @@ __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>:
     ItemCtxT<W> c;
     c.q = pr.q;
     c.q4 = pr.q << 2;
-    c.mbar = pr.mbar;
+    c.rc = pr.rc;
+    c.rsh = pr.rsh;
     c.u = u_base;
     c.hi = 0;
     c.s0 = s0;

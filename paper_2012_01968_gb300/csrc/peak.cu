@@ -30,8 +30,8 @@ __global__ void __launch_bounds__(256) bfly_rate_kernel(u64* out, u64 q, u64 w0,
 #pragma unroll
                 for (int i = 0; i < half; ++i) {
                     const int a = pre * 2 * half + i;
-                    if (k & 1) ct_bfly<16>(x[a], x[a + half], w, wp, q, q4, 0u);
-                    else ct_bfly<12>(x[a], x[a + half], w, wp, q, q4, 0u);
+                    if (k & 1) ct_bfly<16>(x[a], x[a + half], w, wp, q, q4);
+                    else ct_bfly<12>(x[a], x[a + half], w, wp, q, q4);
                 }
             }
         }

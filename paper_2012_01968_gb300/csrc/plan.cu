@@ -85,7 +85,8 @@ void build_prime(const ntt_plan& p, uint32_t l, HostTables& h)
     d.q = q;
     d.k = (uint32_t)nt::bitlen(q);
     d.mu = (uint64_t)(((nt::u128)1 << (2 * d.k)) / q);
-    d.mbar = (uint32_t)((~(uint64_t)0) / q);       // floor((2^64 - 1)/q) = floor(2^64/q) for odd q
+    d.rc = (uint32_t)(((nt::u128)1 << (d.k + 31)) / q);   // < 2^32: q > 2^(k-1)
+    d.rsh = d.k - 28;
     const uint64_t ninv = nt::powmod(N % q, q - 2, q);
     d.ninv = make_tw(ninv, q);
     const uint64_t psi_half = N >= 2 ? fwd(nt::brv(1, n)) : 1;   // Psi[1] = psi^{N/2}

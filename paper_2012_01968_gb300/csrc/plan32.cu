@@ -206,7 +206,8 @@ extern "C" ntt_status ntt_plan32_create(ntt_plan32** out, uint32_t N, const uint
         }
         PrimeDev32& d = pd[l];
         d.q = (uint32_t)q;
-        d.mbar = 0;
+        d.rc = 0;
+        d.rsh = 0;
         d.k = (uint32_t)nt::bitlen(q);
         const uint64_t ninv = nt::powmod(N % q, q - 2, q);
         d.ninv = make_tw32(ninv, q);

@@ -3,7 +3,7 @@
 Mirrors paper_2012_01968_gb300/csrc/ntt_pass.cuh and arith.cuh: the tile
 geometry, item decomposition, round schedule, twiddle indices (table and
 on-the-fly), the lazy Shoup product with its 3-partial-product quotient, the
-reduce3 step and the range bookkeeping, with every value checked against the
+final reduction and the range bookkeeping, with every value checked against the
 bound the kernel assumes (below 2^64 and below X q).  Used to check the
 kernel design against the oracle on the CPU before it runs on a GPU.
 """
@@ -30,25 +30,35 @@ def shoup_lazy(y, w, wp, q):
     return r
 
 
-def reduce3(x, q, mbar):
-    assert 0 <= x <= M64
-    qh = ((x >> 32) * mbar) >> 32
-    r = x - qh * q
-    assert 0 <= r < 3 * q
+def reduce2(x, q, rc, rsh):
+    """x mod q into [0, 2q) for x < 16q from the top 32 bits of x (arith.cuh)."""
+    assert 0 <= x < 16 * q and rsh == q.bit_length() - 28 and 5 <= rsh <= 32
+    xs = x >> rsh
+    assert xs <= M32
+    kq = ((xs * rc) >> 32) >> 27
+    r = x - kq * q
+    assert 0 <= r < 2 * q
     return r
 
 
-def canon(x, X, q, mbar):
+def canon(x, X, q, rc, rsh):
     assert x < X * q
     if X > 4:
-        x = reduce3(x, q, mbar)
-        x = x - 2 * q if x >= 2 * q else x
+        x = reduce2(x, q, rc, rsh)
         return x - q if x >= q else x
     if X > 2:
         x = x - 2 * q if x >= 2 * q else x
     if X > 1:
         x = x - q if x >= q else x
     return x
+
+
+def reduction_constants(q):
+    """(rc, rsh) = (floor(2^(k+31) / q), k - 28), k the bit length of q."""
+    k = q.bit_length()
+    rc = (1 << (k + 31)) // q
+    assert (1 << 31) <= rc <= M32
+    return rc, k - 28
 
 
 def ct_reduces(X):
@@ -138,7 +148,7 @@ class PrimeTables:
                 w = fwd(brv((1 << s) + j, n))
                 self.tw[(1 << s) + tw_slot(j, sl, K0, k)] = (w, comp(w))
             s += 1
-        self.mbar = M64 // q
+        self.rc, self.rsh = reduction_constants(q)
         ninv = pow(N, q - 2, q)
         self.ninv = (ninv, comp(ninv))
         w1 = fwd(brv(1, n)) if N >= 2 else 1
@@ -294,9 +304,9 @@ def run_pass(data, T: PrimeTables, *, P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_
                         X = ct_next(X)
                 if canon_here:
                     if FWD:
-                        x = [canon(v, ct_after(XIN, P), q, T.mbar) for v in x]
+                        x = [canon(v, ct_after(XIN, P), q, T.rc, T.rsh) for v in x]
                     else:
-                        x = [canon(v, 4 if HAS_S0 else gs_after(XIN, P), q, T.mbar) for v in x]
+                        x = [canon(v, 4 if HAS_S0 else gs_after(XIN, P), q, T.rc, T.rsh) for v in x]
                 for j, v in zip(idx, x):
                     sm[j] = v
         # store

@@ -67,6 +67,39 @@ def test_model_extreme_values(orc):
     assert KM.transform(a, q, psi, n, False) == [int(v) for v in orc.intt_radix2(a, q)]
 
 
+def test_final_reduction_every_bit_length():
+    """The final reduction's quotient estimate is floor(x / q) or one less for
+    every modulus bit length the 64-bit plans accept (2^32 < q < 2^60) and
+    every x < 16q: the ends of each bit length, the multiples of q and their
+    neighbours, and random values; canon gives x mod q."""
+    rng = random.Random(2012)
+    for k in range(33, 61):
+        qs = [(1 << (k - 1)) + 1, (1 << k) - 1, rng.randrange(1 << (k - 1), 1 << k) | 1]
+        for q in qs:
+            rc, rsh = KM.reduction_constants(q)
+            xs = [0, 16 * q - 1] + [m * q + d for m in range(1, 16) for d in (-1, 0, 1)]
+            xs += [rng.randrange(16 * q) for _ in range(200)]
+            for x in xs:
+                r = KM.reduce2(x, q, rc, rsh)
+                assert r % q == x % q
+                for X in (5, 12, 16):
+                    if x < X * q:
+                        assert KM.canon(x, X, q, rc, rsh) == x % q
+
+
+def test_final_reduction_worst_truncation():
+    """x just below a multiple of q with every low bit below the shift set:
+    the estimate's two truncations at their largest."""
+    for k in (33, 40, 59, 60):
+        q = (1 << k) - 1
+        rc, rsh = KM.reduction_constants(q)
+        for m in range(1, 16):
+            x = m * q - 1
+            x |= (1 << rsh) - 1
+            if x < 16 * q:
+                assert KM.reduce2(x, q, rc, rsh) % q == x % q
+
+
 def test_swizzle_is_a_bijection_keeping_pairs():
     for tile in (2, 64, 4096, 8192):
         img = [KM.swz(w) for w in range(tile)]
