@@ -437,7 +437,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
                     sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
             else
-                compute_tile<P2, LOGC_R, KMAX, true, false, 1, false, false, OTS, false, NT, NoHook, true>(
+                compute_tile<P2, LOGC_R, KMAX, true, false, 1, false, false, OTS, false, NT, NoHook, true, sizeof(W) == 8>(
                     sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
         }
         // make this thread's shared-memory writes visible to the TMA store

@@ -152,10 +152,30 @@ __device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
 }
 
 // ---------------------------------------------------------------- inverse --
+// Global table index of the inverse twiddle for stage sl of the pass, slot
+// jlo: Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j].
+template <bool TWG, class W>
+__device__ __forceinline__ u32 inv_tw_index(const ItemCtxT<W>& c, const int sl, const u32 jlo)
+{
+    const u32 j = TWG ? (c.u << sl) + jlo : jlo;
+    return TWG ? (2u << (c.s0 + sl)) - 1u - j : (2u << sl) - 1u - j;
+}
+
+// Whether the first stage an inverse round runs (its largest, 2^{KR-1}
+// twiddles per item) reads table twiddles from global memory; those are then
+// loaded before the round's shared-memory reads, to overlap their latency.
+template <int P, int KR, int K0, int OTS, bool HAS_S0, bool TWG>
+__host__ __device__ constexpr bool inv_preloads()
+{
+    return TWG && K0 + KR - 1 < P - OTS && !(HAS_S0 && K0 == 0 && KR == 1);
+}
+
 // Stages run from KR-1 down to 0.  HAS_S0: this round holds global stage 0
-// (K0 == 0 and s0 == 0), whose butterfly also applies N^{-1}.
-template <int P, int KR, int K0, int k, int X, int OTS, bool HAS_S0, bool TWG, int E, class W>
-__device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c)
+// (K0 == 0 and s0 == 0), whose butterfly also applies N^{-1}.  t0: the
+// twiddles of stage KR-1 when inv_preloads().
+template <int P, int KR, int K0, int k, int X, int OTS, bool HAS_S0, bool TWG, bool PRE, int E, class W>
+__device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c,
+                                           const typename WordTypes<W>::Tw (&t0)[(E >> 1) > 0 ? (E >> 1) : 1])
 {
     if constexpr (k >= 0) {
         constexpr int half = E >> (k + 1);
@@ -178,25 +198,25 @@ __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c)
                     for (int i = 0; i < half; ++i)
                         gs_bfly_ot<X, false>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q);
                 } else {
-                    // Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j]
-                    const u32 j = TWG ? (c.u << sl) + jlo : jlo;
-                    const u32 idx = TWG ? (2u << (c.s0 + sl)) - 1u - j : (2u << sl) - 1u - j;
-                    const auto t = c.tw[idx];
+                    constexpr bool pre_loaded = PRE && k == KR - 1 && inv_preloads<P, KR, K0, OTS, HAS_S0, TWG>();
+                    const auto t = pre_loaded ? t0[pre] : c.tw[inv_tw_index<TWG>(c, sl, jlo)];
 #pragma unroll
                     for (int i = 0; i < half; ++i)
                         gs_bfly<X, true>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q);
                 }
             }
         }
-        inv_stages<P, KR, K0, k - 1, gs_next(X), OTS, HAS_S0, TWG, E>(x, c);
+        inv_stages<P, KR, K0, k - 1, gs_next(X), OTS, HAS_S0, TWG, PRE, E>(x, c, t0);
     }
 }
 
 // ------------------------------------------------------------------ round --
 // One round: every item of the tile reads its 2^KR elements from shared
 // memory, runs KR stages in registers and writes them back.
+// PRE: an inverse round loads the global twiddles of its first stage before
+// its shared-memory reads (see inv_preloads).
 template <int P, int LOGC, int KMAX, int r, bool ROWS, bool FWD, int XR, int OTS,
-          bool HAS_S0, int CANON, bool TWG, int NT, class W>
+          bool HAS_S0, int CANON, bool TWG, int NT, bool PRE, class W>
 __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base, const u32 tid)
 {
     constexpr int KR = rsize(P, KMAX, r);
@@ -221,6 +241,12 @@ __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base
         c.hi = hi;
         if constexpr (ROWS) c.u = u_base + cc;
         const u32 vbase = (hi << (P - K0)) | lo;
+        typename WordTypes<W>::Tw t0[(E >> 1) > 0 ? (E >> 1) : 1];
+        if constexpr (!FWD && PRE && inv_preloads<P, KR, K0, OTS, HAS_S0, TWG>()) {
+#pragma unroll
+            for (int pre = 0; pre < (E >> 1); ++pre)
+                t0[pre] = c.tw[inv_tw_index<TWG>(c, K0 + KR - 1, ((u32)pre << K0) | hi)];
+        }
         W x[E];
         if constexpr (PAIRS) {
 #pragma unroll
@@ -239,7 +265,7 @@ __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base
         if constexpr (FWD)
             fwd_stages<P, KR, K0, 0, XR, OTS, TWG, E>(x, c);
         else
-            inv_stages<P, KR, K0, KR - 1, XR, OTS, HAS_S0, TWG, E>(x, c);
+            inv_stages<P, KR, K0, KR - 1, XR, OTS, HAS_S0, TWG, PRE, E>(x, c, t0);
         if constexpr (CANON > 0) {
 #pragma unroll
             for (int i = 0; i < E; ++i) x[i] = canon<CANON>(x[i], c.q, c.rc, c.rsh);
@@ -289,7 +315,7 @@ __device__ __forceinline__ void round_barrier()
 // `mid` runs (in every thread) after the first round executed, before the
 // barrier that follows it.
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
-          bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false, class W = u64>
+          bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false, bool PRELOAD_TW = false, class W = u64>
 __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>::Prime& pr,
                                              const typename WordTypes<W>::Tw* tw,
                                              const typename WordTypes<W>::Tw* ota,
@@ -320,44 +346,44 @@ __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>:
 
     if constexpr (FWD) {
         run_round<P, LOGC, KMAX, 0, ROWS, true, round_in_range<P, KMAX, true, XIN, 0>(), OTS, false,
-                  (NR == 1 ? CANON_FWD : 0), !TW_SMEM, NT>(sm, c, u_base, tid);
+                  (NR == 1 ? CANON_FWD : 0), !TW_SMEM, NT, false>(sm, c, u_base, tid);
         mid();
         if constexpr (NR > 1) {
             round_barrier<NT, NAMED>();
             run_round<P, LOGC, KMAX, 1, ROWS, true, round_in_range<P, KMAX, true, XIN, 1>(), OTS, false,
-                      (NR == 2 ? CANON_FWD : 0), !TW_SMEM, NT>(sm, c, u_base, tid);
+                      (NR == 2 ? CANON_FWD : 0), !TW_SMEM, NT, false>(sm, c, u_base, tid);
         }
         if constexpr (NR > 2) {
             round_barrier<NT, NAMED>();
             run_round<P, LOGC, KMAX, 2, ROWS, true, round_in_range<P, KMAX, true, XIN, 2>(), OTS, false,
-                      (NR == 3 ? CANON_FWD : 0), !TW_SMEM, NT>(sm, c, u_base, tid);
+                      (NR == 3 ? CANON_FWD : 0), !TW_SMEM, NT, false>(sm, c, u_base, tid);
         }
         if constexpr (NR > 3) {
             round_barrier<NT, NAMED>();
             run_round<P, LOGC, KMAX, 3, ROWS, true, round_in_range<P, KMAX, true, XIN, 3>(), OTS, false,
-                      CANON_FWD, !TW_SMEM, NT>(sm, c, u_base, tid);
+                      CANON_FWD, !TW_SMEM, NT, false>(sm, c, u_base, tid);
         }
     } else {
         if constexpr (NR > 3) {
-            run_round<P, LOGC, KMAX, 3, ROWS, false, round_in_range<P, KMAX, false, XIN, 3>(), OTS, false, 0, !TW_SMEM, NT>(
+            run_round<P, LOGC, KMAX, 3, ROWS, false, round_in_range<P, KMAX, false, XIN, 3>(), OTS, false, 0, !TW_SMEM, NT, PRELOAD_TW>(
                 sm, c, u_base, tid);
             if constexpr (NR == 4) mid();
             round_barrier<NT, NAMED>();
         }
         if constexpr (NR > 2) {
-            run_round<P, LOGC, KMAX, 2, ROWS, false, round_in_range<P, KMAX, false, XIN, 2>(), OTS, false, 0, !TW_SMEM, NT>(
+            run_round<P, LOGC, KMAX, 2, ROWS, false, round_in_range<P, KMAX, false, XIN, 2>(), OTS, false, 0, !TW_SMEM, NT, PRELOAD_TW>(
                 sm, c, u_base, tid);
             if constexpr (NR == 3) mid();
             round_barrier<NT, NAMED>();
         }
         if constexpr (NR > 1) {
-            run_round<P, LOGC, KMAX, 1, ROWS, false, round_in_range<P, KMAX, false, XIN, 1>(), OTS, false, 0, !TW_SMEM, NT>(
+            run_round<P, LOGC, KMAX, 1, ROWS, false, round_in_range<P, KMAX, false, XIN, 1>(), OTS, false, 0, !TW_SMEM, NT, PRELOAD_TW>(
                 sm, c, u_base, tid);
             if constexpr (NR == 2) mid();
             round_barrier<NT, NAMED>();
         }
         run_round<P, LOGC, KMAX, 0, ROWS, false, round_in_range<P, KMAX, false, XIN, 0>(), OTS, HAS_S0,
-                  CANON_INV, !TW_SMEM, NT>(sm, c, u_base, tid);
+                  CANON_INV, !TW_SMEM, NT, PRELOAD_TW>(sm, c, u_base, tid);
         if constexpr (NR == 1) mid();
     }
 }
