@@ -45,11 +45,11 @@ def canon(x, X, q, rc, rsh):
     assert x < X * q
     if X > 4:
         x = reduce2(x, q, rc, rsh)
-        return x - q if x >= q else x
+        return csub(x, q)
     if X > 2:
-        x = x - 2 * q if x >= 2 * q else x
+        x = csub(x, 2 * q)
     if X > 1:
-        x = x - q if x >= q else x
+        x = csub(x, q)
     return x
 
 
@@ -78,8 +78,13 @@ def gs_next(X):
 
 
 def csub(x, c):
-    assert 0 <= x < 2 * c
-    return x - c if x >= c else x
+    """x in [0, 2c) -> [0, c) the way arith.cuh decides it for 64-bit words:
+    by the sign bit of the wrapped difference x - c (valid for c <= 2^63)."""
+    assert 0 <= x < 2 * c and c <= 1 << 63
+    d = (x - c) & M64
+    r = x if d >> 63 else d
+    assert r == (x - c if x >= c else x)
+    return r
 
 
 def ct_after(X, k):

@@ -87,6 +87,19 @@ def test_final_reduction_every_bit_length():
                         assert KM.canon(x, X, q, rc, rsh) == x % q
 
 
+def test_sign_tested_subtraction_edges():
+    """The sign-bit conditional subtraction at its limits: c = 8q for the
+    largest q the plans accept (8q just below 2^63), x at 0, c - 1, c and
+    2c - 1."""
+    for q in ((1 << 60) - 1, (1 << 59) + 1, (1 << 32) + 15):
+        for c in (q, 2 * q, 8 * q):
+            for x in (0, 1, c - 1, c, c + 1, 2 * c - 1):
+                assert KM.csub(x, c) == (x - c if x >= c else x)
+    c = 1 << 63
+    for x in (0, c - 1, c, 2 * c - 1):
+        assert KM.csub(x, c) == (x - c if x >= c else x)
+
+
 def test_final_reduction_worst_truncation():
     """x just below a multiple of q with every low bit below the shift set:
     the estimate's two truncations at their largest."""
