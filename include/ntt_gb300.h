@@ -176,9 +176,12 @@ ntt_status ntt_mul_pointwise(const ntt_plan* plan, const uint64_t* a, const uint
  * product, iNTT):  c = a * b mod (X^N + 1), limb by limb mod q_l, for
  * `batch` pairs of polynomials [batch][L][N].  Both forward transforms run in
  * one launch (fused plans), then the element-wise product into c, then the
- * inverse of c.  a and b are left holding their forward transforms (natural
- * input order in, bit-reversed transform out, as ntt_forward); c may alias
- * a or b; a and b must not overlap.  Errors as ntt_forward, and
+ * inverse of c.  With a fused plan and c aliasing a or b, the product is not
+ * a separate pass: the inverse's first pass multiplies each tile of c by the
+ * other factor's transform before its stages.  The factor that c does not
+ * alias is left holding its forward transform (natural input order in,
+ * bit-reversed transform out, as ntt_forward), and so are both when c aliases
+ * neither; a and b must not overlap.  Errors as ntt_forward, and
  * NTT_ERR_INVALID_ARG for overlapping a and b.
  */
 ntt_status ntt_mul_negacyclic(const ntt_plan* plan, uint64_t* a, uint64_t* b, uint64_t* c, uint32_t batch,

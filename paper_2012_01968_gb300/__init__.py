@@ -289,7 +289,9 @@ def ntt_mul_pointwise(plan: int, a, b, c, batch: int, stream=None) -> None:
 
 
 def ntt_mul_negacyclic(plan: int, a, b, c, batch: int, stream=None) -> None:
-    """c = a * b mod (X^N + 1) per limb; a and b are left holding their transforms."""
+    """c = a * b mod (X^N + 1) per limb; a factor that c does not alias is left
+    holding its transform.  With c aliasing a or b (fused plans) the inverse's
+    first pass applies the element-wise product."""
     _check(_lib().ntt_mul_negacyclic(plan, _addr(a), _addr(b), _addr(c), batch, _stream(stream, a)),
            "ntt_mul_negacyclic")
 

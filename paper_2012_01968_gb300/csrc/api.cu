@@ -178,6 +178,15 @@ ntt_status ntt_mul_negacyclic(const ntt_plan* p, uint64_t* a, uint64_t* b, uint6
         const uint32_t ots = p->twiddle_mode == NTT_TWIDDLE_OT ? p->ot_stages : 0;
         const ntt::JobsCtx jc{jobs, 2u, p->n, ots, p->d_status, p->d_work, p->work_limbs, s, 0u, p->geom};
         e = ntt::launch_fused_jobs(jc, true);
+        if (e != cudaSuccess) return to_status(e);
+        if (c == a || c == b) {
+            // the product in place: the inverse's first pass multiplies each
+            // tile of c by the other factor before its stages (no separate
+            // element-wise pass over the data)
+            ntt::LaunchCtx ci = p->ctx(c, (uint32_t)limbs, p->L, s);
+            ci.mulb = reinterpret_cast<const ntt::u64*>(c == a ? b : a);
+            return to_status(ntt::launch_transform(ci, false));
+        }
     } else {
         const ntt::LaunchCtx ca = p->ctx(a, (uint32_t)limbs, p->L, s);
         e = ntt::launch_transform(ca, true);

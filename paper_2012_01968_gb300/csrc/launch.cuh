@@ -172,11 +172,11 @@ cudaError_t encode_tile_maps32(u32* data, u32 limbs, u32 n, int p1, int row_tile
 int device_sm_count();
 
 // One persistent launch over all limbs of all jobs, both passes.
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ>
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, bool MULB = false>
 cudaError_t launch_fused_dir(const JobsCtx& c)
 {
     using F = FusedCfg<P1, P2, LOGC_R, KMAX>;
-    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS, MAXJ>;
+    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS, MAXJ, u64, MULB>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int occ = 0;
@@ -198,6 +198,9 @@ cudaError_t launch_fused_dir(const JobsCtx& c)
         a.job[j].tw = J.tw;
         a.job[j].ota = FWD ? J.ota_f : J.ota_i;
         a.job[j].otb = FWD ? J.otb_f : J.otb_i;
+        // a product operand is only taken by the MULB instantiation
+        if ((J.mulb != nullptr) != MULB || (J.mulb && ((uintptr_t)J.mulb & 15u))) return cudaErrorInvalidValue;
+        a.job[j].mulb = J.mulb;
         a.job[j].tw_len = J.tw_len;
         a.job[j].L = J.L;
         a.job[j].limb0 = (u32)limbs;
@@ -221,6 +224,17 @@ cudaError_t launch_fused_dir(const JobsCtx& c)
 template <int P1, int P2, int LOGC_R, int KMAX, int MAXJ>
 cudaError_t launch_fused(const JobsCtx& c, bool fwd)
 {
+    if constexpr (MAXJ == 1) {
+        // the inverse of an in-place negacyclic product (one job)
+        if (!fwd && c.njobs == 1 && c.jobs[0].mulb) {
+            switch (c.ots) {
+            case 0: return launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 0, 1, true>(c);
+            case 1: return launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 1, 1, true>(c);
+            case 2: return launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 2, 1, true>(c);
+            default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     switch (c.ots) {
     case 0: return fwd ? launch_fused_dir<P1, P2, LOGC_R, KMAX, true, 0, MAXJ>(c)
                        : launch_fused_dir<P1, P2, LOGC_R, KMAX, false, 0, MAXJ>(c);
@@ -312,7 +326,7 @@ cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
         default: return cudaErrorInvalidValue;
         }
     }
-    const JobCtx job{c.data, c.limbs, c.L, c.primes, c.tw, c.tw_len, c.ota_f, c.otb_f, c.ota_i, c.otb_i};
+    const JobCtx job{c.data, c.limbs, c.L, c.primes, c.tw, c.tw_len, c.ota_f, c.otb_f, c.ota_i, c.otb_i, c.mulb};
     const JobsCtx jc{&job,   1u,         c.n,      c.ots,        c.status,  c.work,   c.work_limbs,
                      c.stream, c.max_polls, c.geom, c.l2_base, c.l2_bytes, c.l2_hit};
     return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(jc, fwd);

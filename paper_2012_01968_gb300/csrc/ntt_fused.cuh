@@ -76,6 +76,8 @@ struct FusedJobT {
     const typename WordTypes<W>::Tw* tw;         // [L][tw_len]
     const typename WordTypes<W>::Tw* ota;        // [L][2^p2]      OT A factors, this direction
     const typename WordTypes<W>::Tw* otb;        // [L][p2 << p1]  OT B factors, this direction
+    const W* mulb;           // inverse, 64-bit words: data *= mulb element-wise
+                             // before the first pass (null: no product)
     u32 tw_len;
     u32 L;                   // primes per polynomial (local limb l uses prime l % L)
     u32 limb0;               // first limb of the job in the launch's numbering
@@ -154,7 +156,9 @@ __device__ __forceinline__ bool compute_any(bool flag)
     return r != 0;
 }
 
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, class W = u64>
+// MULB: an inverse whose first pass applies an element-wise product
+// (FusedJobT::mulb; 64-bit words only)
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, class W = u64, bool MULB = false>
 __global__ void __launch_bounds__(FusedCfg<P1, P2, LOGC_R, KMAX, W>::THREADS,
                                   FusedCfg<P1, P2, LOGC_R, KMAX, W>::MIN_CTAS)
 ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
@@ -284,6 +288,13 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                     const u32 start = FWD ? (1u << (P1 + sl)) + (u0 << sl)
                                           : (2u << (P1 + sl)) - ((u0 + (u32)F::CR) << sl);
                     bulk_prefetch_l2(base + start, ((u32)F::CR << sl) * (u32)sizeof(TwT));
+                }
+                // the other factor of a fused element-wise product (the inverse's
+                // first pass multiplies the tile by it), into L2
+                if constexpr (MULB && !FWD && sizeof(W) == 8) {
+                    if (J.mulb)
+                        bulk_prefetch_l2(J.mulb + (size_t)local * (F::R1 * F::R2) + (size_t)tile * F::TILE_R,
+                                         (u32)F::TILE_R * (u32)sizeof(W));
                 }
             }
             bulk_load(buf_pr(b), J.primes + pi, (u32)sizeof(PrimeT), &full[b]);
@@ -433,6 +444,23 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             const TwT* tw = J.tw + (size_t)pi * J.tw_len;
             const TwT* ota = J.ota ? J.ota + (size_t)pi * F::R2 : nullptr;
             const TwT* otb = J.otb ? J.otb + (size_t)pi * ((size_t)P2 << P1) : nullptr;
+            if constexpr (MULB && !FWD && sizeof(W) == 8) {
+                // fused element-wise product (Sec. III-A): the tile of the first
+                // factor's transform times the second's, canonical, before the
+                // inverse stages; the row tile is TILE_R consecutive words of the limb
+                if (J.mulb) {
+                    const W* bt = J.mulb + (size_t)buf_desc(b)->local * (F::R1 * F::R2) + (size_t)tile * F::TILE_R;
+                    for (u32 w = 2u * tid; w < (u32)F::TILE_R; w += 2u * NT) {
+                        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(bt + w);
+                        W x0, x1;
+                        load_pair(sm + swzw<W>(w), x0, x1);
+                        x0 = canon<3>(mulmod_barrett(x0, v.x, pr.q, pr.mu, pr.k), pr.q, pr.rc, pr.rsh);
+                        x1 = canon<3>(mulmod_barrett(x1, v.y, pr.q, pr.mu, pr.k), pr.q, pr.rc, pr.rsh);
+                        store_pair(sm + swzw<W>(w), x0, x1);
+                    }
+                    round_barrier<NT, true>();
+                }
+            }
             if constexpr (FWD)
                 compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
                     sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);

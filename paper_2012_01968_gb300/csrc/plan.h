@@ -92,6 +92,9 @@ struct LaunchCtx {
     const void* l2_base;     // L2 access-policy window of the launches (l2_bytes 0: none)
     size_t l2_bytes;
     float l2_hit;            // fraction of the window that persists
+    // inverse through the fused kernel only: the other factor of an
+    // element-wise product that the first pass applies (see JobCtx::mulb)
+    const u64* mulb = nullptr;
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
@@ -109,6 +112,9 @@ struct JobCtx {
     const Tw* otb_f;
     const Tw* ota_i;
     const Tw* otb_i;
+    // inverse only: the other factor of an element-wise product, in the same
+    // layout as data; the first pass multiplies by it before its stages
+    const u64* mulb = nullptr;
 };
 
 // Jobs of one size N = 2^n and one OT setting in one launch of the fused

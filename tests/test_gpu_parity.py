@@ -92,10 +92,17 @@ def test_config3_full_size_and_product(orc):
         p.inverse(da, 1)
         torch.cuda.synchronize()
         c = host(da)
+        # the same product in one call, in place (fused element-wise step)
+        da, db = dev(a), dev(b)
+        G.ntt_mul_negacyclic(p.handle, da, db, da, 1)
+        torch.cuda.synchronize()
+        c_in_place = host(da)
+        assert p.device_status() == 0
     A = oracle_fwd(orc, a, primes)
     B = oracle_fwd(orc, b, primes)
     want = oracle_inv(orc, orc.pointwise_batch(A, B, primes), primes)
     assert np.array_equal(c, want)
+    assert np.array_equal(c_in_place, want)
     # sampled outputs checked one by one: c(x) = a(x) b(x) at roots of X^N + 1
     rng = np.random.default_rng(3)
     for l in rng.choice(len(primes), 3, replace=False):
@@ -370,6 +377,41 @@ def test_mul_negacyclic(orc, n, kernel, mode, ots):
         G.ntt_mul_negacyclic(p.handle, da, db, da, 2)                      # c aliases a
         torch.cuda.synchronize()
         assert np.array_equal(host(da), want)
+        assert np.array_equal(host(db), B)
+        da, db = dev(a), dev(b)
+        G.ntt_mul_negacyclic(p.handle, da, db, db, 2)                      # c aliases b
+        torch.cuda.synchronize()
+        assert np.array_equal(host(db), want)
+        assert np.array_equal(host(da), A)
+        assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+@pytest.mark.parametrize("geometry,ots", [(0, 1), (1, 0), (2, 2)])
+def test_fused_product_in_place(orc, n, geometry, ots):
+    """The in-place product of fused plans (the inverse's first pass multiplies
+    each tile by the other factor) for every geometry, both twiddle supplies and
+    both aliasings, against the oracle's transforms; several polynomials so that
+    tiles of different limbs and primes meet in one launch."""
+    N = 1 << n
+    primes = I.prime_chain(3, 2 * N)
+    a = I.batch_uniform(170 + n, 3, primes, N)
+    b = I.batch_uniform(180 + n, 3, primes, N)
+    A = oracle_fwd(orc, a, primes)
+    B = oracle_fwd(orc, b, primes)
+    want = oracle_inv(orc, orc.pointwise_batch(A, B, primes), primes)
+    mode = G.NTT_TWIDDLE_OT if ots else G.NTT_TWIDDLE_TABLE
+    with G.Plan(N, primes, mode, ots, G.NTT_KERNEL_FUSED, geometry) as p:
+        for alias_a in (True, False):
+            da, db = dev(a), dev(b)
+            G.ntt_mul_negacyclic(p.handle, da, db, da if alias_a else db, 3)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(da if alias_a else db), want), f"n={n} g={geometry} ots={ots} a={alias_a}"
+            assert np.array_equal(host(db if alias_a else da), B if alias_a else A)
+        # the plan's own inverse is unaffected afterwards
+        d = dev(A)
+        p.inverse(d, 3)
+        assert np.array_equal(host(d), a)
         assert p.device_status() == 0
 
 
