@@ -247,7 +247,10 @@ ntt_status ntt_execute_host_async(const ntt_plan* plan, const uint64_t* host_in,
  *
  * The first call on a device does a one-time set-up (it looks up the
  * array's device address, which may load the library's device code): make
- * it before any stream capture.  All calls to this function on one device
+ * it before any stream capture.  The address belongs to the CUDA context:
+ * after cudaDeviceReset, or under a context the caller made current itself,
+ * the next call looks it up again (and starts from a zeroed array), so that
+ * first call in the new context also belongs before any capture.  All calls to this function on one device
  * share the one array, whatever the plan: calls that overlap in time (on
  * different streams, or from different host threads without ordering) race
  * on it and give wrong results.  Order them on one stream or with events.

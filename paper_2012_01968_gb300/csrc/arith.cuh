@@ -7,13 +7,16 @@
 //
 // shoup_lazy is Shoup's modular multiplication (Algorithm 4) with the
 // quotient estimated from three 32x32-bit partial products instead of the
-// exact high word of the 128-bit product:
-//   qhat = yh*wh' + hi32(yh*wl') + hi32(yl*wh')   (w' = floor(w 2^64 / q))
-//   r    = lo64(y*w - qhat*q)
+// exact high word of the 128-bit product (w' = floor(w 2^64 / q)):
+//   qhat = yh*wh' + hi32(yh*wl') + hi32(yl*wh')
+//   r    = lo64(y*w + qhat*(2^64 - q))  =  y*w - qhat*q  mod 2^64
 // For every y < 2^64 and w < q the exact quotient floor(y w / q) exceeds qhat
 // by at most 3, so r lies in [0, 4q).  (Dropped: lo32 parts of both middle
 // products and the low product, each < 1 in units of 2^64, and < 1 from the
-// floor in w'.)
+// floor in w'.)  The products are written as PTX 32-bit multiplies so that
+// each maps to one multiply-pipe instruction: two high products and one wide
+// multiply-add (their sum as its addend) for qhat, two wide and four low
+// products for r.
 #pragma once
 #include <stdint.h>
 
@@ -35,8 +38,24 @@ __device__ __forceinline__ u64 mul_wide(u32 a, u32 b) { return (u64)a * (u64)b; 
 __device__ __forceinline__ u64 shoup_lazy(u64 y, u64 w, u64 wp, u64 q)
 {
     const u32 yl = lo32(y), yh = hi32(y);
-    const u64 qhat = mul_wide(yh, hi32(wp)) + __umulhi(yh, lo32(wp)) + __umulhi(yl, hi32(wp));
-    return y * w - qhat * q;      // exact value < 4q, so the wrapped difference is it
+    const u64 nq = 0ull - q;      // 2^64 - q
+    u64 r;
+    u32 h1, h2;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(h1) : "r"(yh), "r"(lo32(wp)));
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(h2) : "r"(yl), "r"(hi32(wp)));
+    u64 qhat;   // yh*wh' + h1 + h2: the two high parts as the wide product's addend
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(qhat) : "r"(yh), "r"(hi32(wp)), "l"((u64)h1 + h2));
+    // low word of y*w + qhat*nq: the low partial products in 64 bits (a carry
+    // out of bit 63 is a multiple of 2^64 and drops out), then the four
+    // cross products into the high word
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(r) : "r"(yl), "r"(lo32(w)));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(r) : "r"(lo32(qhat)), "r"(lo32(nq)));
+    u32 rh = hi32(r);
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(rh) : "r"(yl), "r"(hi32(w)));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(rh) : "r"(yh), "r"(lo32(w)));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(rh) : "r"(lo32(qhat)), "r"(hi32(nq)));
+    asm("mad.lo.u32 %0, %1, %2, %0;" : "+r"(rh) : "r"(hi32(qhat)), "r"(lo32(nq)));
+    return ((u64)rh << 32) | lo32(r);
 }
 
 // x in [0, 2c) -> [0, c), for c <= 2^63: x - c wraps to at least 2^63 exactly

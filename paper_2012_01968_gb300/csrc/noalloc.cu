@@ -11,15 +11,20 @@
 // first launch and every completed launch restores it.  The kernel itself is the
 // same one the plan's own entry points launch; only the work area differs.
 //
-// Each device has its own copy of the array.  Its address is looked up once
-// per device (cudaGetSymbolAddress, with that device current) and cached; that
-// first call may load the module, so it belongs before any stream capture.
-// All calls on one device share the one area, so calls that overlap in time
-// (two streams, two host threads, two plans) race on it.
-#include <atomic>
+// Each device has its own copy of the array, and each CUDA context on that
+// device (the primary context is destroyed by cudaDeviceReset and made again
+// later; a caller may also switch to a context of its own) loads the module
+// anew, at a new address.  The address is therefore looked up
+// (cudaGetSymbolAddress, with that device current) and cached per device
+// together with the unique id of the context it belongs to; a call under
+// another context looks it up again.  A look-up may load the module, so the
+// first call in each context belongs before any stream capture.  All calls in
+// one context share the one area, so calls that overlap in time (two streams,
+// two host threads, two plans) race on it.
 #include <cstdint>
 #include <mutex>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "plan.h"
@@ -31,30 +36,59 @@ static __device__ __align__(256) uint32_t g_noalloc_work[ntt::fused_work_words(N
 namespace {
 
 constexpr int kMaxDevices = 64;
-std::atomic<uint32_t*> g_work[kMaxDevices];
-std::mutex g_setup_mu;
+struct Cached {
+    unsigned long long ctx_id = 0;    // 0: none (context ids start at 1)
+    uint32_t* addr = nullptr;
+};
+Cached g_work[kMaxDevices];
+std::mutex g_mu;
 
-// Address of this device's copy of the work area; set-up on first use.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if it cannot be read).
+unsigned long long current_context_id()
+{
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Address of the current context's copy of the work area on `device`.
 ntt_status noalloc_work(int device, uint32_t** out)
 {
     if (device < 0 || device >= kMaxDevices) return NTT_ERR_INVALID_ARG;
-    uint32_t* w = g_work[device].load(std::memory_order_acquire);
-    if (!w) {
-        std::lock_guard<std::mutex> g(g_setup_mu);
-        w = g_work[device].load(std::memory_order_relaxed);
-        if (!w) {
-            void* addr = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_work);
-            if (e != cudaSuccess || !addr) {
-                ntt_internal_set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
-                cudaGetLastError();
-                return NTT_ERR_CUDA;
-            }
-            w = static_cast<uint32_t*>(addr);
-            g_work[device].store(w, std::memory_order_release);
+    const unsigned long long id = current_context_id();
+    std::lock_guard<std::mutex> g(g_mu);
+    Cached& c = g_work[device];
+    if (id == 0 || c.ctx_id != id || !c.addr) {
+        void* addr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_work);
+        if (e != cudaSuccess || !addr) {
+            ntt_internal_set_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+            cudaGetLastError();
+            return NTT_ERR_CUDA;
         }
+        c.addr = static_cast<uint32_t*>(addr);
+        c.ctx_id = id;
     }
-    *out = w;
+    *out = c.addr;
     return NTT_OK;
 }
 

@@ -391,13 +391,21 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 idle = 0;
                 continue;
             }
-            // nothing moved: publish what is complete (another limb may wait on it), then back off
+            // nothing moved: publish what is complete (another limb may wait on it), then wait
             publish_all();
             if (++idle > a.max_polls) {
                 failed = true;
                 break;
             }
-            __nanosleep(64);
+            if (stored < issued && (held == NONE || issued - stored >= 2u)) {
+                // the only event that can come is the oldest unit's compute
+                // finishing: suspend on its barrier (a bounded try_wait)
+                // instead of polling, which would take issue slots from the
+                // compute warps of this SM sub-partition
+                mbar_try_wait(&empty[stored % NBUF], (stored / NBUF) & 1u);
+            } else {
+                __nanosleep(held != NONE ? 256 : 64);
+            }
         }
         publish_all();
         if (failed) {

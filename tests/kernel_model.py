@@ -25,7 +25,13 @@ def shoup_lazy(y, w, wp, q):
     assert 0 <= y <= M64 and 0 <= w < q
     yl, yh = y & M32, y >> 32
     qhat = yh * (wp >> 32) + ((yh * (wp & M32)) >> 32) + ((yl * (wp >> 32)) >> 32)
-    r = (y * w - qhat * q) & M64
+    assert qhat <= M64
+    # the kernel forms the low word of y*w + qhat*(2^64 - q) from 32-bit pieces
+    nq = (1 << 64) - q
+    lo = ((y & M32) * (w & M32) + (qhat & M32) * (nq & M32)) & M64
+    rh = ((lo >> 32) + yl * (w >> 32) + yh * (w & M32) + (qhat & M32) * (nq >> 32) + (qhat >> 32) * (nq & M32)) & M32
+    r = (rh << 32) | (lo & M32)
+    assert r == (y * w - qhat * q) & M64
     assert r < 4 * q and r % q == (y * w) % q
     return r
 

@@ -22,6 +22,10 @@ def _built():
 
 
 def test_largest_plan_n131072_l4096(orc):
+    """The largest plan (N = 2^17, 4096 primes, 4 GiB of data).  A limits
+    test: the inputs are uniform in [0, 2^59), below every prime of the chain
+    (all primes exceed 2^59) rather than uniform in [0, q); six sampled limbs
+    are compared with the oracle and the whole array round-trips."""
     N, L = 1 << 17, 4096
     primes = I.prime_chain(L, 1 << 18)
     assert min(primes) > 1 << 59

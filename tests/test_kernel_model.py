@@ -197,3 +197,24 @@ def test_high_radix_index_maps(orc, n, k):
     got = KM.high_radix_transform(a, q, psi, n, k, True)
     assert got == [int(v) for v in orc.ntt_radix2(a, q)]
     assert KM.high_radix_transform(got, q, psi, n, k, False) == a
+
+
+def test_shoup_product_range_adversarial():
+    """The lazy Shoup product's quotient estimate (three partial products,
+    32-bit pieces for the remainder) gives y*w mod q in [0, 4q) for any 64-bit
+    y, checked at the extremes of y, w and the prime size."""
+    rng = random.Random(7)
+    primes = [I.prime_chain(1, 1 << 18)[0], (1 << 32) + 15 * (1 << 20) + 1, 1152921504266321921]
+    M64 = (1 << 64) - 1
+    for q in primes:
+        for w in (0, 1, q - 1, q // 2, rng.randrange(q)):
+            wp = (w << 64) // q
+            for y in (0, 1, M64, M64 - 1, 16 * q - 1, (1 << 63), (1 << 32) - 1, 1 << 32,
+                      rng.randrange(1 << 64)):
+                r = KM.shoup_lazy(y, w, wp, q)
+                assert 0 <= r < 4 * q and r % q == (y * w) % q
+        for _ in range(2000):
+            w = rng.randrange(q)
+            wp = (w << 64) // q
+            y = rng.randrange(1 << 64)
+            KM.shoup_lazy(y, w, wp, q)
