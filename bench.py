@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 import ntt_inputs as I  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
-PROFILE_MD = os.path.join(ROOT, "profiles", "ntt_c2_n65536_l45.md")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic_c2_n65536_l45.json")
 
 
 def parse():
@@ -112,24 +112,22 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per transform launch from the committed ncu summary, if it is
-    for the current kernel sources (else None)."""
+def profile_traffic(geometry: int, twiddle: str, direction: str):
+    """DRAM traffic of one steady-state launch of the C2 transform kernel
+    (ncu counters, committed under profiles/), for the plan's geometry,
+    twiddle supply and direction, if it was taken on the current kernel
+    sources (else None)."""
     try:
-        txt = open(PROFILE_MD).read()
-    except OSError:
+        with open(TRAFFIC_JSON) as f:
+            entries = json.load(f)["entries"]
+    except (OSError, KeyError, ValueError):
         return None
-    vals = {}
-    for line in txt.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    try:
-        return float(vals["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    h = kernel_source_hash()
+    for e in entries:
+        if (e.get("geometry"), e.get("twiddle"), e.get("direction"), e.get("source_hash")) == \
+                (geometry, twiddle, direction, h):
+            return e
+    return None
 
 
 class ClockSampler:
@@ -179,13 +177,14 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-# Integer-multiply roofline of the butterfly.  Per SM and clock the FMA-heavy
-# pipe retires 64 lanes of IMAD, 32 of IMAD.WIDE and 16 of IMAD.HI (measured
-# with a register-only micro-benchmark on this GPU); Shoup's lazy product
-# (arith.cuh) issues 3 IMAD.WIDE, 2 IMAD.HI and 4 IMAD per butterfly, so a
-# butterfly occupies 3/32 + 2/16 + 4/64 SM-clocks of the pipe.
+# Integer-multiply roofline of the butterfly (secondary bound).  Measured on
+# this GPU with a register-only micro-benchmark: a warp's IMAD occupies the
+# FMA-heavy pipe of its SM sub-partition for 2 cycles, IMAD.WIDE and IMAD.HI
+# for 4.  Shoup's lazy product (arith.cuh) issues 2 IMAD.HI, 3 IMAD.WIDE and
+# 4 IMAD per butterfly: 28 pipe cycles per warp butterfly, i.e. 4 x 32 / 28
+# butterflies per SM and clock.
 SMS, SM_MHZ_MAX = 152, 2070.0
-BFLY_PER_SM_CLK = 1.0 / (3 / 32 + 2 / 16 + 4 / 64)
+BFLY_PER_SM_CLK = 4 * 32 / (2 * 4 + 3 * 4 + 4 * 2)
 
 
 def alu_peak_gbfly(sm_mhz=SM_MHZ_MAX):
@@ -227,6 +226,11 @@ def oracle_time(primes, N, seconds_target: float, threads: int | None = None, ba
 
 
 def run_reference(args, metric, unit, w):
+    """The reference arm: the CPU oracle on the host cores, on this arm's
+    workload.  One step = the forward then the inverse of the whole C2
+    polynomial (all 45 limbs), limb-parallel on every host core.  The timed
+    sample is `--steps` steps, extended by whole steps until it lasts at least
+    5 s, so that the rate does not hang on one short sample."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -234,34 +238,34 @@ def run_reference(args, metric, unit, w):
     orc = oracle.get()
     cores = os.cpu_count() or 1
     N, primes = w.N, w.primes
-    data = I.batch_uniform(w.seed, 1, primes, N)[0]
-    # one step = forward + inverse of one limb (limb = step mod L); steps run
-    # `cores` at a time, one per host thread
-    def run_group(first, count):
-        done = 0
-        while done < count:
-            k = min(cores, count - done)
-            idx = [(first + done + i) % len(primes) for i in range(k)]
-            # all limbs of a group share N; the oracle threads over (batch x L)
-            blk = np.stack([data[i] for i in idx])[None]          # [1, k, N]
-            pr = [primes[i] for i in idx]
-            f = orc.ntt_batch(blk, pr, +1, k)
-            orc.ntt_batch(f, pr, -1, k)
-            done += k
-        return done
-    run_group(0, args.warmup)
+    data = I.batch_uniform(w.seed, 1, primes, N)
+
+    def one_step():
+        f = orc.ntt_batch(data, primes, +1, cores)
+        return orc.ntt_batch(f, primes, -1, cores)
+
+    for _ in range(max(0, args.warmup)):
+        one_step()
+    steps = 0
     t0 = time.perf_counter()
-    run_group(args.warmup, args.steps)
-    el = time.perf_counter() - t0
-    value = 2.0 * args.steps / el
+    while True:
+        back = one_step()
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= args.steps and el >= 5.0:
+            break
+    if not np.array_equal(back, data):
+        raise RuntimeError("oracle round trip failed")
+    L = len(primes)
+    value = 2.0 * L * steps / el
     line = {
         "impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": args.steps, "steps_timed": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic", "config": config_dict(w, args, ws),
         "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
-                         "sample": f"each step = forward + inverse of one N={N} limb (limb = step mod 45), "
-                                   f"{cores} steps in flight on {cores} host threads"},
+                         "sample": f"{steps} steps x (forward + inverse of all {L} limbs of the N={N} "
+                                   f"polynomial), limb-parallel on {cores} host threads, {el:.1f} s"},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -420,13 +424,14 @@ def batched_c4(G, torch, reps, tuned=None):
 
 
 def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jobs=64, slots=3,
-             loads=(0.5, 0.8, 0.95)):
+             loads=(0.5, 0.8, 0.95), repeats=5):
     """The serving workload: `count` requests (N in 2^15..2^17, L in [4, 60],
     mixed directions) on device-resident data, admitted by an HBM budget.
     A capacity run (every request submitted at once), then Poisson arrivals at
     50 / 80 / 95% of that capacity; latency = submission to completion.  At
     each Poisson load the first tenth of the requests is a warm-up, left out
-    of the statistics."""
+    of the statistics; the three loads run `repeats` times in a row, and each
+    load reports its median run with the p99 of every run."""
     import collections
     chain = I.chain_2_18_60()
     plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain))
@@ -478,6 +483,9 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                 for t in tickets:
                     srv.wait(t)
                 times = [srv.times(t) for t in tickets]
+                for t in tickets:
+                    srv.release(t)
+                sched = srv.stats()
             # at a Poisson load the first `warm` requests bring host and device
             # to that load's steady state and are left out of the statistics
             first = warm if rate is not None else 0
@@ -492,15 +500,28 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                     "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                    "mean": float(lat.mean())},
                     "batch_device_us": {"p50": float(np.percentile(dev_us, 50)),
-                                        "p99": float(np.percentile(dev_us, 99))}}
+                                        "p99": float(np.percentile(dev_us, 99))},
+                    "max_gap_between_completions_us": float(np.max(np.diff(np.sort(done)))) / 1e3,
+                    "scheduler": {k: (v / 1e3 if k.endswith("_ns") else v) for k, v in sched.items()}}
 
         cap = run(None)
         out = {"requests": count, "budget_gb": budget_gb, "data": "device-resident, in place",
                "capacity": cap}
         out["max_batch_jobs"], out["slots"] = max_batch_jobs, slots
+        # the three loads, `repeats` times in a row: the p99 of every run, to show
+        # whether a run's tail is an outlier
+        runs = {frac: [] for frac in loads}
+        for _ in range(repeats):
+            for frac in loads:
+                runs[frac].append(run(frac * cap["requests_per_s"]))
         for frac in loads:
-            out[f"poisson_{int(frac * 100)}pct"] = dict(run(frac * cap["requests_per_s"]),
-                                                       offered_requests_per_s=frac * cap["requests_per_s"])
+            p99 = [r["latency_us"]["p99"] for r in runs[frac]]
+            med = float(np.median(p99))
+            out[f"poisson_{int(frac * 100)}pct"] = dict(
+                runs[frac][int(np.argsort(p99)[len(p99) // 2])], offered_requests_per_s=frac * cap["requests_per_s"],
+                p99_us_runs=p99, p50_us_runs=[r["latency_us"]["p50"] for r in runs[frac]],
+                p99_max_over_median=max(p99) / med if med > 0 else None)
+        out["scheduler_units"] = "us (counts for batches and requests)"
         return out
     finally:
         for p in plans.values():
@@ -983,33 +1004,37 @@ def main():
         v3, c3, s3 = oracle_time(w3.primes, w3.N, 5.0, batch=2)
         cpu["single_thread"] = {"value": v1, "unit": unit, "cores": 1, "sample": s1}
         cpu["large_ring_c3"] = {"value": v3, "unit": unit, "cores": c3, "sample": s3}
-    # the committed DRAM counters are for the fused kernel with OT1 in geometry 0
-    profiled = (info.kernel == G.NTT_KERNEL_FUSED and info.twiddle_mode == G.NTT_TWIDDLE_OT
-                and info.ot_stages == 1 and info.geometry == 0)
-    traffic = profile_traffic() if profiled else None
+    twname = "table" if info.twiddle_mode == G.NTT_TWIDDLE_TABLE else f"ot{int(info.ot_stages)}"
+    kname = f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})"
+    prof = profile_traffic(int(info.geometry), twname, "forward" if dom_name == "ntt_forward" else "inverse") \
+        if info.kernel == G.NTT_KERNEL_FUSED else None
+    traffic = prof["dram_bytes"] if prof else None
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": config_dict(w, args, ws),
         "hbm_roofline_frac_step": frac_step,
-        "roofline": {"bound": "alu", "achieved": bfly_achieved, "peak": alu_peak_gbfly(),
-                     "unit": "G butterfly/s", "frac": bfly_achieved / alu_peak_gbfly(),
-                     "traffic": traffic,
-                     "kernel": f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})",
-                     "units_per_launch": f"{bfly_per_launch} butterflies (45 limbs x (N/2) log2 N)",
-                     "avg_launch_us": dom_ms * 1e3,
-                     "peak_source": "152 SMs x 2070 MHz x 3.56 butterflies per SM-clock (FMA-heavy pipe: "
-                                    "3 IMAD.WIDE + 2 IMAD.HI + 4 IMAD per butterfly at 32/16/64 lanes per clock)",
-                     "peak_measured": None if args.no_peak_measure else G.ntt_measure_butterfly_rate(),
-                     "peak_measured_source": "ntt_measure_butterfly_rate: register-only butterfly loop, live",
-                     "timed_region_frac": bfly_per_launch * 2 * K / (total_ms / 1e3) / 1e9 / alu_peak_gbfly()},
-        "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})",
+                     "traffic_split": None if not prof else {
+                         k: prof[k] for k in ("dram_read_bytes", "dram_write_bytes", "data_read_bytes",
+                                              "twiddle_read_bytes", "how") if k in prof},
+                     "kernel": kname,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
+                     "units_per_launch": f"{L} limb-NTTs of N={N} (16 N bytes each: one read, one write)",
                      "launch_timing": f"CUDA events around each of {Kp} forward and inverse launches on one stream",
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
+        "roofline_alu": {"bound": "alu", "achieved": bfly_achieved, "peak": alu_peak_gbfly(),
+                         "unit": "G butterfly/s", "frac": bfly_achieved / alu_peak_gbfly(),
+                         "kernel": kname,
+                         "units_per_launch": f"{bfly_per_launch} butterflies ({L} limbs x (N/2) log2 N)",
+                         "avg_launch_us": dom_ms * 1e3,
+                         "peak_source": "152 SMs x 2070 MHz x 4.57 butterflies per SM-clock (FMA-heavy pipe: "
+                                        "2 IMAD.HI + 3 IMAD.WIDE at 4 cycles and 4 IMAD at 2 cycles per warp butterfly)",
+                         "peak_measured": None if args.no_peak_measure else G.ntt_measure_butterfly_rate(),
+                         "peak_measured_source": "ntt_measure_butterfly_rate: register-only butterfly loop, live",
+                         "timed_region_frac": bfly_per_launch * 2 * K / (total_ms / 1e3) / 1e9 / alu_peak_gbfly()},
         "per_transform_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3,
                              "timed_region_per_transform": total_ms * 1e3 / (2 * K),
                              "single_stream_per_transform": single_ms * 1e3 / 2},

@@ -391,6 +391,28 @@ ntt_status ntt_server_wait(ntt_server* server, uint64_t ticket, uint64_t timeout
 /* Timestamps of a request (for latency statistics). */
 ntt_status ntt_server_request_times(ntt_server* server, uint64_t ticket, ntt_request_times* times);
 
+/* Forget a finished request: its ticket, status and times are released (the
+ * server otherwise keeps every request until ntt_server_destroy, so a
+ * long-running loop should release each request once it has read what it
+ * needs).  Errors: NTT_ERR_INVALID_ARG (unknown ticket), NTT_ERR_BUSY (the
+ * request is not done yet; nothing is released). */
+ntt_status ntt_server_release(ntt_server* server, uint64_t ticket);
+
+/* Counters of the scheduler since the server was created, for diagnosing
+ * latency: where a request's time went when its latency is far above the
+ * batch's device time. */
+typedef struct ntt_server_stats {
+    uint64_t batches;             /* batches started */
+    uint64_t requests;            /* requests finished */
+    int64_t max_launch_ns;        /* longest host time to enqueue one batch (copies, launches, events) */
+    int64_t max_loop_gap_ns;      /* longest interval between two passes of the scheduler loop */
+    int64_t max_completion_gap_ns;/* longest interval, with a batch in flight, without a batch completing */
+    int64_t max_device_ns;        /* longest device time of one batch */
+    int64_t reserved[4];
+} ntt_server_stats;
+
+ntt_status ntt_server_stats_get(ntt_server* server, ntt_server_stats* stats);
+
 /* One configuration tried by ntt_autotune, and its measured times. */
 typedef struct ntt_tune_entry {
     ntt_plan_opts opts;       /* the configuration, as plan options */

@@ -94,6 +94,12 @@ class RequestTimes(ctypes.Structure):
                 ("device_ns", ctypes.c_int64)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("batches", _u64), ("requests", _u64), ("max_launch_ns", ctypes.c_int64),
+                ("max_loop_gap_ns", ctypes.c_int64), ("max_completion_gap_ns", ctypes.c_int64),
+                ("max_device_ns", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4)]
+
+
 class NttError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -160,6 +166,10 @@ def _lib():
             L.ntt_server_wait.argtypes = [_vp, _u64, _u64]
             L.ntt_server_request_times.restype = S
             L.ntt_server_request_times.argtypes = [_vp, _u64, ctypes.POINTER(RequestTimes)]
+            L.ntt_server_release.restype = S
+            L.ntt_server_release.argtypes = [_vp, _u64]
+            L.ntt_server_stats_get.restype = S
+            L.ntt_server_stats_get.argtypes = [_vp, ctypes.POINTER(ServerStats)]
             L.ntt_measure_butterfly_rate.restype = S
             L.ntt_measure_butterfly_rate.argtypes = [ctypes.POINTER(ctypes.c_double)]
             L.ntt_plan_query.restype = S
@@ -613,6 +623,19 @@ class Server:
         t = RequestTimes()
         _check(_lib().ntt_server_request_times(self.handle, ticket, ctypes.byref(t)), "ntt_server_request_times")
         return t.submit_ns, t.start_ns, t.done_ns, t.device_ns
+
+    def release_status(self, ticket: int) -> int:
+        return _lib().ntt_server_release(self.handle, ticket)
+
+    def release(self, ticket: int) -> None:
+        """Forget a finished request (its ticket and times)."""
+        _check(self.release_status(ticket), "ntt_server_release")
+
+    def stats(self) -> dict:
+        """The scheduler's counters since creation (ntt_server_stats)."""
+        st = ServerStats()
+        _check(_lib().ntt_server_stats_get(self.handle, ctypes.byref(st)), "ntt_server_stats_get")
+        return {k: int(getattr(st, k)) for k, _ in ServerStats._fields_ if k != "reserved"}
 
     def close(self):
         if self.handle:

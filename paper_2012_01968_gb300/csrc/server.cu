@@ -13,6 +13,7 @@
 // other slots), timestamps finished requests and wakes the waiters.
 // Requests that arrive while batches are on the device are admitted into the
 // next free slot as memory frees up, so several batches overlap on the device.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
@@ -63,6 +64,7 @@ struct Slot {
     bool finished = false;        // set when the scheduler sees `done` complete
     cudaEvent_t done = nullptr;   // recorded after the batch's last copy
     cudaEvent_t begin = nullptr;  // recorded before its first operation (timing)
+    int64_t t_start = 0;          // host time the batch was started
 };
 
 using Arena = ntt::host::Arena;
@@ -85,6 +87,8 @@ struct ntt_server {
     bool stop = false;
     cudaError_t fatal = cudaSuccess;
     uint32_t test_stall_polls = 0;    // test hook: the next batch's kernels stall (bounded)
+    ntt_server_stats stats{};
+    int64_t t_last_completion = 0;
 };
 
 namespace {
@@ -115,6 +119,10 @@ bool poll_slots(ntt_server* srv, std::unique_lock<std::mutex>& lk)
         const bool device_error = qe == cudaSuccess && *static_cast<volatile uint32_t*>(s.status) != 0;
         float ms = 0.f;
         if (qe == cudaSuccess && cudaEventElapsedTime(&ms, s.begin, s.done) != cudaSuccess) ms = 0.f;
+        const int64_t gap = t - std::max(srv->t_last_completion, s.t_start);
+        srv->stats.max_completion_gap_ns = std::max(srv->stats.max_completion_gap_ns, gap);
+        srv->stats.max_device_ns = std::max(srv->stats.max_device_ns, (int64_t)((double)ms * 1e6));
+        srv->t_last_completion = t;
         for (Req* r : s.reqs) {
             r->t_done = t;
             r->t_device = (int64_t)((double)ms * 1e6);
@@ -151,6 +159,8 @@ bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
     srv->test_stall_polls = 0;
     const int64_t t = now_ns();
     for (Req* r : take) r->t_start = t;
+    s.t_start = t;
+    ++srv->stats.batches;
     lk.unlock();
 
     cudaError_t e = cudaEventRecord(s.begin, s.stream);
@@ -176,7 +186,9 @@ bool start_batch(ntt_server* srv, Slot& s, std::unique_lock<std::mutex>& lk)
     }
     if (st == NTT_OK) st = ntt_internal_batch_status_async(s.batch, s.status, s.stream);
     if (e == cudaSuccess && st == NTT_OK) e = cudaEventRecord(s.done, s.stream);
+    const int64_t t_enq = now_ns() - t;
     lk.lock();
+    srv->stats.max_launch_ns = std::max(srv->stats.max_launch_ns, t_enq);
     if (e != cudaSuccess || st != NTT_OK) {
         // nothing will call back: finish the batch here once the stream drains
         lk.unlock();
@@ -204,6 +216,7 @@ bool retire(ntt_server* srv)
             srv->admitted_bytes -= r->bytes;
             if (r->host) srv->arena.release(r->arena_off, r->bytes);
             r->done = true;
+            ++srv->stats.requests;
         }
         s.reqs.clear();
         s.busy = false;
@@ -218,7 +231,11 @@ void scheduler(ntt_server* srv)
 {
     cudaSetDevice(srv->device);
     std::unique_lock<std::mutex> lk(srv->mu);
+    int64_t t_prev = now_ns();
     for (;;) {
+        const int64_t t_now = now_ns();
+        srv->stats.max_loop_gap_ns = std::max(srv->stats.max_loop_gap_ns, t_now - t_prev);
+        t_prev = t_now;
         const bool running = poll_slots(srv, lk);
         retire(srv);
         bool started = false;
@@ -388,6 +405,25 @@ ntt_status ntt_server_request_times(ntt_server* srv, uint64_t ticket, ntt_reques
     times->start_ns = r->t_start;
     times->done_ns = r->done ? r->t_done : 0;
     times->device_ns = r->done ? r->t_device : 0;
+    return NTT_OK;
+}
+
+ntt_status ntt_server_release(ntt_server* srv, uint64_t ticket)
+{
+    if (!srv) return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return NTT_ERR_INVALID_ARG;
+    if (!it->second->done) return NTT_ERR_BUSY;
+    srv->reqs.erase(it);
+    return NTT_OK;
+}
+
+ntt_status ntt_server_stats_get(ntt_server* srv, ntt_server_stats* stats)
+{
+    if (!srv || !stats) return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(srv->mu);
+    *stats = srv->stats;
     return NTT_OK;
 }
 

@@ -49,10 +49,12 @@ def test_gpu_arm_line():
               "--no-ablation", "--no-peak-measure", "--e2e-steps", "4", "--launch-steps", "5"], 900)
     _common(d)
     r = d["roofline"]
-    assert r["bound"] == "alu" and r["achieved"] > 0 and r["peak"] > 0
-    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
-    h = d["roofline_hbm"]
-    assert h["bound"] == "hbm" and h["unit"] == "GB/s" and 0 < h["frac"] < 1
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["achieved"] > 0 and r["peak"] > 0
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9 and 0 < r["frac"] < 1
+    assert r["alg_bytes_per_launch"] == 16 * 45 * 65536
+    a = d["roofline_alu"]
+    assert a["bound"] == "alu" and a["achieved"] > 0 and a["peak"] > 0
+    assert abs(a["frac"] - a["achieved"] / a["peak"]) < 1e-9
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 45 * 65536 * 8
     per = 1 if d["plan"]["kernel"] == "fused" else d["plan"]["passes"]

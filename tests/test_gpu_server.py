@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import ntt_inputs as I
-from gpu_util import dev, oracle_fwd
+from gpu_util import dev, host, oracle_fwd, oracle_inv
 
 torch = pytest.importorskip("torch")
 G = pytest.importorskip("paper_2012_01968_gb300")
@@ -102,6 +102,54 @@ def test_host_requests_through_arena(plans, orc):
             want = orc.ntt_batch(d, chain[:L], -1, 8)
         assert np.array_equal(o, want)
         assert np.array_equal(ip, want)
+
+
+def test_served_c5_shapes_against_oracle(plans, orc):
+    """Requests of the serving workload's own shapes (its seeded draws of
+    N in {2^15, 2^16, 2^17}, L in [4, 60] and the direction, plus one
+    N = 2^17, L = 60 request per direction), uniform residues in [0, q),
+    served together under a budget that admits several at once: every
+    result against the oracle, element by element."""
+    chain = I.chain_2_18_60()
+    reqs = [(r.N.bit_length() - 1, r.L, FWD if r.dir > 0 else INV) for r in I.serving_requests(14, seed=5)]
+    reqs += [(17, 60, FWD), (17, 60, INV)]
+    datas = [I.batch_uniform(900 + i, 1, chain[:L], 1 << n) for i, (n, L, _) in enumerate(reqs)]
+    bufs = [dev(d) for d in datas]
+    with G.Server(256 << 20, max_batch_jobs=6, slots=3) as srv:
+        tickets = [srv.submit(plans[n].handle, b, 1, L, op) for (n, L, op), b in zip(reqs, bufs)]
+        for t in tickets:
+            srv.wait(t)
+    assert any(n == 17 and L == 60 for n, L, _ in reqs)
+    for k, ((n, L, op), d, b) in enumerate(zip(reqs, datas, bufs)):
+        want = oracle_fwd(orc, d, chain[:L]) if op == FWD else oracle_inv(orc, d, chain[:L])
+        assert np.array_equal(host(b).reshape(d.shape), want), f"request {k} (N=2^{n}, L={L})"
+
+
+def test_release_and_stats(plans):
+    """A finished request can be released (its ticket is then unknown); an
+    unfinished one cannot; the scheduler counters count batches and
+    requests."""
+    chain = I.chain_2_18_60()
+    big = torch.zeros(60 << 17, dtype=torch.int64, device="cuda")
+    a = dev(I.batch_uniform(31, 1, chain[:8], 1 << 15))
+    with G.Server(1 << 30, max_batch_jobs=4, slots=2) as srv:
+        tk = srv.submit(plans[17].handle, big, 1, 60, FWD)
+        busy = srv.release_status(tk)         # a 60-limb N = 2^17 batch is still running (almost surely)
+        srv.wait(tk)
+        assert busy in (G.NTT_ERR_BUSY, G.NTT_OK)
+        t2 = srv.submit(plans[15].handle, a, 1, 8, FWD)
+        srv.wait(t2)
+        srv.times(t2)
+        srv.release(t2)
+        assert srv.release_status(t2) == G.NTT_ERR_INVALID_ARG
+        with pytest.raises(G.NttError):
+            srv.times(t2)
+        st = srv.stats()
+        assert st["batches"] >= 2 and st["requests"] >= 2
+        assert 0 < st["max_device_ns"] and 0 < st["max_launch_ns"] and 0 < st["max_loop_gap_ns"]
+        if busy == G.NTT_OK:
+            return
+        srv.release(tk)
 
 
 def test_admission_refused_when_queue_full(plans):
