@@ -175,7 +175,7 @@ int device_sm_count();
 template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, bool MULB = false>
 cudaError_t launch_fused_dir(const JobsCtx& c)
 {
-    using F = FusedCfg<P1, P2, LOGC_R, KMAX>;
+    using F = FusedCfg<P1, P2, LOGC_R, KMAX, u64, OTS>;
     auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS, MAXJ, u64, MULB>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;

@@ -100,7 +100,7 @@ struct FusedParams {
     u32 max_polls;           // bound of every wait loop
 };
 
-template <int P1, int P2, int LOGC_R, int KMAX, class W = u64>
+template <int P1, int P2, int LOGC_R, int KMAX, class W = u64, int OTS = 0>
 struct FusedCfg {
     using TwT = typename WordTypes<W>::Tw;
     using PrimeT = typename WordTypes<W>::Prime;
@@ -115,17 +115,35 @@ struct FusedCfg {
     static constexpr int TR = pass_threads(P2, LOGC_R, KMAX);
     static constexpr int NT = TC > TR ? TC : TR;       // compute threads
     static constexpr int THREADS = NT + 32;            // + the producer warp
-    // per buffer: the tile, the column pass's twiddles Psi[0, R1), the prime's
-    // constants and the unit descriptor, the first three filled by one
-    // mbarrier transaction
+    // per buffer: the tile, the column pass's twiddles Psi[0, R1) (or a row
+    // tile's first-round twiddle runs), the prime's constants and the unit
+    // descriptor, the first three filled by one mbarrier transaction
     static constexpr size_t TW_OFF = (size_t)TILE * sizeof(W);
     static constexpr size_t PR_OFF = TW_OFF + (size_t)R1 * sizeof(TwT);
     static constexpr size_t DESC_OFF = PR_OFF + sizeof(PrimeT);
     static constexpr size_t BUF = (DESC_OFF + 32 + 1023) / 1024 * 1024;
-    static constexpr int NBUF = 3;                     // ring of tile buffers
-    static constexpr size_t SMEM = NBUF * BUF + 1024;
+    // Row tiles stage all their twiddles in shared memory (64-bit words, a row
+    // pass of two rounds or more) when a per-CTA buffer for the later rounds'
+    // runs and the OT factors fits beside two tile buffers at two CTAs per SM:
+    // STAGE 1 with round 0's runs in the tile buffer, STAGE 2 with all runs in
+    // the per-CTA buffer.  Otherwise three tile buffers, twiddles from global.
+    static constexpr size_t SMEM_TWO_PER_SM = 115712;  // dynamic bytes per CTA at two CTAs per SM
+    using RS1 = RowStaging<P2, CR, KMAX, OTS, 1>;
+    using RS2 = RowStaging<P2, CR, KMAX, OTS, 2>;
+    static constexpr size_t htw_bytes(int nh) { return ((size_t)nh * sizeof(TwT) + 1023) / 1024 * 1024; }
+    static constexpr bool STAGE_OK = sizeof(W) == 8 && nrounds(P2, KMAX) >= 2;
+    static constexpr bool FIT1 = RS1::N0 <= R1 && 2 * BUF + htw_bytes(RS1::NH) + 1024 <= SMEM_TWO_PER_SM;
+    static constexpr bool FIT2 = 2 * BUF + htw_bytes(RS2::NH) + 1024 <= SMEM_TWO_PER_SM;
+    static constexpr int STAGE = !STAGE_OK ? 0 : FIT1 ? 1 : FIT2 ? 2 : 0;
+    using RS = RowStaging<P2, CR, KMAX, OTS, STAGE>;
+    static constexpr size_t HTW_BYTES = STAGE ? htw_bytes(RS::NH) : 0;
+    static constexpr int NBUF = STAGE ? 2 : 3;         // ring of tile buffers
+    static constexpr size_t HTW_OFF = NBUF * BUF;
+    static constexpr size_t SMEM = NBUF * BUF + HTW_BYTES + 1024;
     static constexpr int TPS = sizeof(W) == 8 ? NTT_FUSED_THREADS_PER_SM : NTT_FUSED32_THREADS_PER_SM;
     static constexpr int MIN_CTAS = TPS / THREADS > 1 ? TPS / THREADS : 1;
+    // row tiles whose rounds exchange data within warps only
+    static constexpr bool ROW_WARPX = rows_stay_in_warp<P2, LOGC_R, KMAX, NT>();
 };
 
 // unit descriptor written by the producer into the buffer it fills
@@ -163,11 +181,13 @@ __global__ void __launch_bounds__(FusedCfg<P1, P2, LOGC_R, KMAX, W>::THREADS,
                                   FusedCfg<P1, P2, LOGC_R, KMAX, W>::MIN_CTAS)
 ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
 {
-    using F = FusedCfg<P1, P2, LOGC_R, KMAX, W>;
+    using F = FusedCfg<P1, P2, LOGC_R, KMAX, W, OTS>;
     using TwT = typename F::TwT;
     using PrimeT = typename F::PrimeT;
+    using RS = typename F::RS;
     constexpr int NT = F::NT;
     constexpr int NBUF = F::NBUF;
+    constexpr int STAGE = F::STAGE;
     constexpr u32 UC = F::R2 / F::COLW;     // column tiles per limb
     constexpr u32 UR = F::R1 / F::CR;       // row tiles per limb
     constexpr u32 UA = FWD ? UC : UR, UB = FWD ? UR : UC;
@@ -179,8 +199,11 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
     auto buf_tw = [&](int b) { return reinterpret_cast<TwT*>(smem_raw + b * F::BUF + F::TW_OFF); };
     auto buf_pr = [&](int b) { return reinterpret_cast<PrimeT*>(smem_raw + b * F::BUF + F::PR_OFF); };
     auto buf_desc = [&](int b) { return reinterpret_cast<volatile UnitDesc*>(smem_raw + b * F::BUF + F::DESC_OFF); };
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + NBUF * F::BUF);
+    TwT* const htw = reinterpret_cast<TwT*>(smem_raw + F::HTW_OFF);      // staged row twiddles (STAGE)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + F::HTW_OFF + F::HTW_BYTES);
     uint64_t* empty = full + NBUF;
+    uint64_t* htw_full = empty + NBUF;      // the staged row twiddles have landed
+    uint64_t* htw_empty = htw_full + 1;     // the compute threads have read them
 
     const u32 tid = threadIdx.x;
     if (tid == 0) {
@@ -188,6 +211,8 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], NT);
         }
+        mbar_init(htw_full, 1);
+        mbar_init(htw_empty, NT);
         fence_mbar_init();
     }
     __syncthreads();
@@ -252,6 +277,44 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 qn = 0;
             }
         };
+        // first table entry of stage sl's run for rows [u0, u0 + CR)
+        auto run_start = [&](int sl, u32 u0) -> u32 {
+            return FWD ? (1u << (P1 + sl)) + (u0 << sl) : (2u << (P1 + sl)) - ((u0 + (u32)F::CR) << sl);
+        };
+        // row tiles loaded whose staged twiddles are still to be copied into
+        // htw (unit numbers, in load order), and the copies issued so far
+        u32 hq[NBUF > 1 ? NBUF : 1];
+        u32 hq_head = 0, hq_tail = 0, fills = 0;
+        (void)hq;
+        auto fill_htw = [&]() -> bool {
+            if constexpr (STAGE) {
+                if (hq_head == hq_tail) return false;
+                if (fills && !mbar_test(htw_empty, (fills - 1) & 1u)) return false;
+                const volatile UnitDesc* d = buf_desc((int)(hq[hq_head % NBUF] % NBUF));
+                const u32 j = MAXJ > 1 ? d->job : 0u, pi = d->prime, u0 = d->tile * (u32)F::CR;
+                const FusedJobT<W>& J = a.job[j];
+                const TwT* base = J.tw + (size_t)pi * J.tw_len;
+                mbar_arrive_expect_tx(htw_full, (u32)RS::NH * (u32)sizeof(TwT));
+#pragma unroll
+                for (int sl = RS::SSB; sl < P2 - OTS; ++sl)
+                    bulk_load(htw + F::CR * ((1 << sl) - (1 << RS::SSB)), base + run_start(sl, u0),
+                              ((u32)F::CR << sl) * (u32)sizeof(TwT), htw_full);
+                if constexpr (OTS > 0) {
+                    bulk_load(htw + RS::A_OFF, J.ota + (size_t)pi * F::R2 + (1u << (P2 - OTS)),
+                              (u32)RS::NA * (u32)sizeof(TwT), htw_full);
+#pragma unroll
+                    for (int i = 0; i < OTS; ++i)
+                        bulk_load(htw + RS::B_OFF + i * F::CR,
+                                  J.otb + (size_t)pi * ((size_t)P2 << P1) + ((size_t)(P2 - OTS + i) << P1) + u0,
+                                  (u32)F::CR * (u32)sizeof(TwT), htw_full);
+                }
+                ++hq_head;
+                ++fills;
+                return true;
+            } else {
+                return false;
+            }
+        };
         auto load = [&](u32 kind, u32 limb, u32 tile) {
             const int b = (int)(issued % NBUF);
             const u32 j = job_of(limb);
@@ -276,18 +339,28 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 tma_load_2d(dst, &a.mapC[j], (int)(tile * F::COLW), (int)(local * F::R1), &full[b]);
                 bulk_load(buf_tw(b), J.tw + (size_t)pi * J.tw_len, F::R1 * (u32)sizeof(TwT), &full[b]);
             } else {
-                mbar_arrive_expect_tx(&full[b], F::TILE_R * (u32)sizeof(W) + (u32)sizeof(PrimeT));
+                mbar_arrive_expect_tx(&full[b], F::TILE_R * (u32)sizeof(W) + (u32)sizeof(PrimeT) +
+                                                    (u32)RS::N0 * (u32)sizeof(TwT));
                 tma_load_2d(dst, &a.mapR[j], 0,
                             (int)(local * (F::R1 * F::R2 / F::COLW) + tile * (F::TILE_R / F::COLW)), &full[b]);
-                // table runs of the row pass, into L2: stage sl of rows [u0, u0 + CR)
+                // table runs of the row pass: stage sl of rows [u0, u0 + CR)
                 // reads CR << sl consecutive entries (mirrored for the inverse)
                 const TwT* base = J.tw + (size_t)pi * J.tw_len;
                 const u32 u0 = tile * (u32)F::CR;
+                if constexpr (STAGE == 1) {
+                    // round 0's runs into the tile buffer, with the tile
 #pragma unroll
-                for (int sl = 0; sl < P2 - OTS; ++sl) {
-                    const u32 start = FWD ? (1u << (P1 + sl)) + (u0 << sl)
-                                          : (2u << (P1 + sl)) - ((u0 + (u32)F::CR) << sl);
-                    bulk_prefetch_l2(base + start, ((u32)F::CR << sl) * (u32)sizeof(TwT));
+                    for (int sl = 0; sl < RS::KR0; ++sl)
+                        bulk_load(buf_tw(b) + F::CR * ((1 << sl) - 1), base + run_start(sl, u0),
+                                  ((u32)F::CR << sl) * (u32)sizeof(TwT), &full[b]);
+                }
+                if constexpr (STAGE) {
+                    hq[hq_tail++ % NBUF] = issued;      // the later rounds' runs: when the buffer is free
+                } else {
+                    // into L2, for the compute threads' loads
+#pragma unroll
+                    for (int sl = 0; sl < P2 - OTS; ++sl)
+                        bulk_prefetch_l2(base + run_start(sl, u0), ((u32)F::CR << sl) * (u32)sizeof(TwT));
                 }
                 // the other factor of a fused element-wise product (the inverse's
                 // first pass multiplies the tile by it), into L2
@@ -322,7 +395,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             prefetch_tensormap(&a.mapR[j]);
         }
         for (;;) {
-            bool progress = false;
+            bool progress = fill_htw();
             // store computed tiles, in order
             while (stored < issued && mbar_test(&empty[stored % NBUF], (stored / NBUF) & 1u)) {
                 const int b = (int)(stored % NBUF);
@@ -397,7 +470,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 failed = true;
                 break;
             }
-            if (stored < issued && (held == NONE || issued - stored >= 2u)) {
+            if (stored < issued && (held == NONE || issued - stored >= 2u) && hq_head == hq_tail) {
                 // the only event that can come is the oldest unit's compute
                 // finishing: suspend on its barrier (a bounded try_wait)
                 // instead of polling, which would take issue slots from the
@@ -408,6 +481,12 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             }
         }
         publish_all();
+        // every copy this producer issued into shared memory has landed (a
+        // bounded wait) before the CTA may exit: the last NBUF tile loads and
+        // the last staged-twiddle copy
+        for (u32 k = issued > (u32)NBUF ? issued - (u32)NBUF : 0u; k < issued; ++k)
+            mbar_wait(&full[k % NBUF], (k / NBUF) & 1u, a.max_polls);
+        if (STAGE && fills) mbar_wait(htw_full, (fills - 1) & 1u, a.max_polls);
         if (failed) {
             atomicOr(a.status, held != NONE ? STATUS_DEP_TIMEOUT : STATUS_TMA_TIMEOUT);
             if (!stopped && issued - stored < (u32)NBUF) {
@@ -426,10 +505,12 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
     }
 
     // ===================================================== compute ======
+    u32 rt = 0;                  // row tiles computed (phase of the staged-twiddle barriers)
+    bool htw_lost = false;       // a wait for staged twiddles ran out
     for (u32 k = 0;; ++k) {
         const int b = (int)(k % NBUF);
         const bool got = mbar_wait(&full[b], (k / NBUF) & 1u, a.max_polls);
-        if (compute_any<NT>(!got)) {
+        if (compute_any<NT>(!got || htw_lost)) {
             if (tid == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
             break;
         }
@@ -469,12 +550,33 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                     round_barrier<NT, true>();
                 }
             }
-            if constexpr (FWD)
-                compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
-                    sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
-            else
-                compute_tile<P2, LOGC_R, KMAX, true, false, 1, false, false, OTS, false, NT, NoHook, true, sizeof(W) == 8>(
-                    sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
+            if constexpr (STAGE) {
+                // all twiddles from shared memory: round 0's runs in the tile
+                // buffer (STAGE 1), the rest in htw once the producer's copy
+                // has landed; htw is released after the last round reading it
+                const u32 ph = rt & 1u;
+                auto hw = [&]() {
+                    if (!mbar_wait(htw_full, ph, a.max_polls)) htw_lost = true;
+                };
+                auto ha = [&]() { mbar_arrive(htw_empty); };
+                const TwT* tw0 = STAGE == 1 ? buf_tw(b) : htw;
+                if constexpr (FWD)
+                    compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true, false, W,
+                                 STAGE, F::ROW_WARPX>(sm, pr, tw0, nullptr, nullptr, tile * F::CR, (u32)P1, tid,
+                                                      NoHook(), htw, hw, ha);
+                else
+                    compute_tile<P2, LOGC_R, KMAX, true, false, 1, false, false, OTS, false, NT, NoHook, true, false, W,
+                                 STAGE, F::ROW_WARPX>(sm, pr, tw0, nullptr, nullptr, tile * F::CR, (u32)P1, tid,
+                                                      NoHook(), htw, hw, ha);
+                ++rt;
+            } else {
+                if constexpr (FWD)
+                    compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
+                        sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
+                else
+                    compute_tile<P2, LOGC_R, KMAX, true, false, 1, false, false, OTS, false, NT, NoHook, true,
+                                 sizeof(W) == 8>(sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
+            }
         }
         // make this thread's shared-memory writes visible to the TMA store
         fence_proxy_async_shared();

@@ -87,6 +87,7 @@ struct ItemCtxT {
     W q, q4;
     u32 rc, rsh;         // final reduction constants
     u32 u;               // upper index bits (which 2^{n-s0} block)
+    u32 ubase;           // first block of the tile (staged twiddle runs are per tile)
     u32 hi;              // bits of v above the round digit
     u32 s0;              // first stage of the pass
     TwT ninv, w1ninv;
@@ -122,8 +123,54 @@ struct PairVec<u32> {
     using T = uint2;
 };
 
+// ------------------------------------------------------- twiddle sources --
+// Where a round reads the table twiddle of stage sl (of the pass), slot jlo:
+//   TW_PASS   : the pass's own table Psi[0, 2^P) in shared memory (a pass that
+//               holds stage 0, where that is all it needs);
+//   TW_GLOBAL : the prime's full table in global memory;
+//   TW_STAGED : runs of the full table copied into shared memory for the
+//               tile's SCR consecutive blocks u0 .. u0 + SCR - 1: stage sl's
+//               run holds entries [2^(s0+sl) + (u0 << sl), + (SCR << sl)) (the
+//               forward) or the mirrored run the inverse reads, at offset
+//               SCR (2^sl - 2^SSB) of the buffer (SSB: its first stage).
+// The inverse reads Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j].
+enum : int { TW_PASS = 0, TW_GLOBAL = 1, TW_STAGED = 2 };
+
+template <int TWM, int SCR, int SSB, int sl, bool FWDDIR, class W>
+__device__ __forceinline__ u32 tw_index(const ItemCtxT<W>& c, const u32 jlo)
+{
+    if constexpr (TWM == TW_PASS) {
+        return FWDDIR ? (1u << sl) + jlo : (2u << sl) - 1u - jlo;
+    } else if constexpr (TWM == TW_GLOBAL) {
+        const u32 j = (c.u << sl) + jlo;
+        return FWDDIR ? (1u << (c.s0 + sl)) + j : (2u << (c.s0 + sl)) - 1u - j;
+    } else {
+        static_assert(sl >= SSB, "stage below the buffer's first stage");
+        constexpr u32 off = (u32)SCR * ((1u << sl) - (1u << SSB));
+        const u32 r = c.u - c.ubase;
+        return FWDDIR ? off + (r << sl) + jlo : off + (((u32)SCR - r) << sl) - 1u - jlo;
+    }
+}
+
+// OT factors of stage sl (one of the last OTS stages): the per-row factor
+// B[sl][u] and the per-position factor A[2^sl + j].  SOT: both are staged in
+// shared memory with the tile (A from entry 2^(P-OTS), B as OTS runs of SCR
+// rows), else read from the prime's global tables.
+template <int P, int OTS, int SOT, int SCR, int sl, class W>
+__device__ __forceinline__ void ot_factors(const ItemCtxT<W>& c, const u32 jlo, typename WordTypes<W>::Tw& f1,
+                                           typename WordTypes<W>::Tw& f2)
+{
+    if constexpr (SOT) {
+        f1 = c.otb[(u32)(sl - (P - OTS)) * SCR + (c.u - c.ubase)];
+        f2 = c.ota[(1u << sl) + jlo - (1u << (P - OTS))];
+    } else {
+        f1 = c.otb[((u32)sl << c.s0) + c.u];
+        f2 = c.ota[(1u << sl) + jlo];
+    }
+}
+
 // ---------------------------------------------------------------- forward --
-template <int P, int KR, int K0, int k, int X, int OTS, bool TWG, int E, class W>
+template <int P, int KR, int K0, int k, int X, int OTS, int TWM, int SCR, int SSB, int SOT, int E, class W>
 __device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
 {
     if constexpr (k < KR) {
@@ -134,46 +181,37 @@ __device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
         for (int pre = 0; pre < (1 << k); ++pre) {
             const u32 jlo = ((u32)pre << K0) | c.hi;      // twiddle slot, see tw_slot
             if constexpr (ot) {
-                const auto f1 = c.otb[((u32)sl << c.s0) + c.u];
-                const auto f2 = c.ota[(1u << sl) + jlo];
+                typename WordTypes<W>::Tw f1, f2;
+                ot_factors<P, OTS, SOT, SCR, sl>(c, jlo, f1, f2);
 #pragma unroll
                 for (int i = 0; i < half; ++i)
                     ct_bfly_ot<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q, c.q4);
             } else {
-                const u32 idx = TWG ? (1u << (c.s0 + sl)) + (c.u << sl) + jlo : (1u << sl) + jlo;
-                const auto t = c.tw[idx];
+                const auto t = c.tw[tw_index<TWM, SCR, SSB, sl, true>(c, jlo)];
 #pragma unroll
                 for (int i = 0; i < half; ++i)
                     ct_bfly<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.q4);
             }
         }
-        fwd_stages<P, KR, K0, k + 1, ct_next(X), OTS, TWG, E>(x, c);
+        fwd_stages<P, KR, K0, k + 1, ct_next(X), OTS, TWM, SCR, SSB, SOT, E>(x, c);
     }
 }
 
 // ---------------------------------------------------------------- inverse --
-// Global table index of the inverse twiddle for stage sl of the pass, slot
-// jlo: Psi^{-1}[2^s + j] = -Psi[2^{s+1} - 1 - j].
-template <bool TWG, class W>
-__device__ __forceinline__ u32 inv_tw_index(const ItemCtxT<W>& c, const int sl, const u32 jlo)
-{
-    const u32 j = TWG ? (c.u << sl) + jlo : jlo;
-    return TWG ? (2u << (c.s0 + sl)) - 1u - j : (2u << sl) - 1u - j;
-}
-
 // Whether the first stage an inverse round runs (its largest, 2^{KR-1}
 // twiddles per item) reads table twiddles from global memory; those are then
 // loaded before the round's shared-memory reads, to overlap their latency.
-template <int P, int KR, int K0, int OTS, bool HAS_S0, bool TWG>
+template <int P, int KR, int K0, int OTS, bool HAS_S0, int TWM>
 __host__ __device__ constexpr bool inv_preloads()
 {
-    return TWG && K0 + KR - 1 < P - OTS && !(HAS_S0 && K0 == 0 && KR == 1);
+    return TWM == TW_GLOBAL && K0 + KR - 1 < P - OTS && !(HAS_S0 && K0 == 0 && KR == 1);
 }
 
 // Stages run from KR-1 down to 0.  HAS_S0: this round holds global stage 0
 // (K0 == 0 and s0 == 0), whose butterfly also applies N^{-1}.  t0: the
 // twiddles of stage KR-1 when inv_preloads().
-template <int P, int KR, int K0, int k, int X, int OTS, bool HAS_S0, bool TWG, bool PRE, int E, class W>
+template <int P, int KR, int K0, int k, int X, int OTS, bool HAS_S0, int TWM, int SCR, int SSB, int SOT, bool PRE,
+          int E, class W>
 __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c,
                                            const typename WordTypes<W>::Tw (&t0)[(E >> 1) > 0 ? (E >> 1) : 1])
 {
@@ -192,21 +230,21 @@ __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c,
             for (int pre = 0; pre < (1 << k); ++pre) {
                 const u32 jlo = ((u32)pre << K0) | c.hi;  // twiddle slot, see tw_slot
                 if constexpr (ot) {
-                    const auto f1 = c.otb[((u32)sl << c.s0) + c.u];
-                    const auto f2 = c.ota[(1u << sl) + jlo];
+                    typename WordTypes<W>::Tw f1, f2;
+                    ot_factors<P, OTS, SOT, SCR, sl>(c, jlo, f1, f2);
 #pragma unroll
                     for (int i = 0; i < half; ++i)
                         gs_bfly_ot<X, false>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q);
                 } else {
-                    constexpr bool pre_loaded = PRE && k == KR - 1 && inv_preloads<P, KR, K0, OTS, HAS_S0, TWG>();
-                    const auto t = pre_loaded ? t0[pre] : c.tw[inv_tw_index<TWG>(c, sl, jlo)];
+                    constexpr bool pre_loaded = PRE && k == KR - 1 && inv_preloads<P, KR, K0, OTS, HAS_S0, TWM>();
+                    const auto t = pre_loaded ? t0[pre] : c.tw[tw_index<TWM, SCR, SSB, sl, false>(c, jlo)];
 #pragma unroll
                     for (int i = 0; i < half; ++i)
                         gs_bfly<X, true>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q);
                 }
             }
         }
-        inv_stages<P, KR, K0, k - 1, gs_next(X), OTS, HAS_S0, TWG, PRE, E>(x, c, t0);
+        inv_stages<P, KR, K0, k - 1, gs_next(X), OTS, HAS_S0, TWM, SCR, SSB, SOT, PRE, E>(x, c, t0);
     }
 }
 
@@ -215,8 +253,8 @@ __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c,
 // memory, runs KR stages in registers and writes them back.
 // PRE: an inverse round loads the global twiddles of its first stage before
 // its shared-memory reads (see inv_preloads).
-template <int P, int LOGC, int KMAX, int r, bool ROWS, bool FWD, int XR, int OTS,
-          bool HAS_S0, int CANON, bool TWG, int NT, bool PRE, class W>
+template <int P, int LOGC, int KMAX, int r, bool ROWS, bool FWD, int XR, int OTS, bool HAS_S0, int CANON, int TWM,
+          int SCR, int SSB, int SOT, int NT, bool PRE, class W>
 __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base, const u32 tid)
 {
     constexpr int KR = rsize(P, KMAX, r);
@@ -242,10 +280,10 @@ __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base
         if constexpr (ROWS) c.u = u_base + cc;
         const u32 vbase = (hi << (P - K0)) | lo;
         typename WordTypes<W>::Tw t0[(E >> 1) > 0 ? (E >> 1) : 1];
-        if constexpr (!FWD && PRE && inv_preloads<P, KR, K0, OTS, HAS_S0, TWG>()) {
+        if constexpr (!FWD && PRE && inv_preloads<P, KR, K0, OTS, HAS_S0, TWM>()) {
 #pragma unroll
             for (int pre = 0; pre < (E >> 1); ++pre)
-                t0[pre] = c.tw[inv_tw_index<TWG>(c, K0 + KR - 1, ((u32)pre << K0) | hi)];
+                t0[pre] = c.tw[tw_index<TWM, SCR, SSB, K0 + KR - 1, false>(c, ((u32)pre << K0) | hi)];
         }
         W x[E];
         if constexpr (PAIRS) {
@@ -263,9 +301,9 @@ __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base
             }
         }
         if constexpr (FWD)
-            fwd_stages<P, KR, K0, 0, XR, OTS, TWG, E>(x, c);
+            fwd_stages<P, KR, K0, 0, XR, OTS, TWM, SCR, SSB, SOT, E>(x, c);
         else
-            inv_stages<P, KR, K0, KR - 1, XR, OTS, HAS_S0, TWG, PRE, E>(x, c, t0);
+            inv_stages<P, KR, K0, KR - 1, XR, OTS, HAS_S0, TWM, SCR, SSB, SOT, PRE, E>(x, c, t0);
         if constexpr (CANON > 0) {
 #pragma unroll
             for (int i = 0; i < E; ++i) x[i] = canon<CANON>(x[i], c.q, c.rc, c.rsh);
@@ -301,43 +339,102 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
+// Whether the items of a row tile stay in one warp across the rounds: every
+// round has the same radix, each thread holds one item per round, and a
+// row's items fit one warp.  The rounds of such a tile exchange data within
+// warps only, so a warp barrier separates them instead of a block barrier.
+template <int P, int LOGC, int KMAX, int NT>
+__host__ __device__ constexpr bool rows_stay_in_warp()
+{
+    constexpr int nr = nrounds(P, KMAX);
+    bool same = true;
+    for (int r = 1; r < nr; ++r) same = same && rsize(P, KMAX, r) == rsize(P, KMAX, 0);
+    constexpr int per_row = 1 << (P - rsize(P, KMAX, 0));
+    return same && per_row <= 32 && (32 % per_row) == 0 && ((1 << LOGC) * per_row) == NT;
+}
+
 // Barrier between rounds: the whole block, or (NAMED) named barrier 1 over
-// the NT compute threads only (when other warps of the block do not take part).
-template <int NT, bool NAMED>
+// the NT compute threads only (when other warps of the block do not take
+// part), or (WARPX) the warp alone.
+template <int NT, bool NAMED, bool WARPX = false>
 __device__ __forceinline__ void round_barrier()
 {
-    if constexpr (NAMED)
+    if constexpr (WARPX)
+        __syncwarp();
+    else if constexpr (NAMED)
         asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
     else
         __syncthreads();
 }
 
+// Twiddle staging of a row tile of the fused kernel (STAGE > 0): the table
+// runs of the tile's SCR rows in shared memory.  STAGE 1: round 0's runs in
+// `tw` (the tile buffer's own twiddle area), the later rounds' runs and the
+// OT factors in `htw`; STAGE 2: all of them in `htw`.  Layout of htw: the
+// runs of stages [SSB, P - OTS) (SSB = 0 for STAGE 2, the first stage of
+// round 1 for STAGE 1), then the A factors A[2^(P-OTS), 2^P), then the B
+// factors, OTS runs of SCR rows.
+template <int P, int CR, int KMAX, int OTS, int STAGE>
+struct RowStaging {
+    static constexpr int KR0 = rsize(P, KMAX, 0);
+    static constexpr int SSB = STAGE == 1 ? KR0 : 0;                   // first stage in htw
+    static constexpr int N0 = STAGE == 1 ? CR * ((1 << KR0) - 1) : 0;  // entries in the tile buffer
+    static constexpr int NT_H = CR * ((1 << (P - OTS)) - (1 << SSB)); // table entries in htw
+    static constexpr int NA = OTS ? (1 << P) - (1 << (P - OTS)) : 0;
+    static constexpr int NB = OTS * CR;
+    static constexpr int A_OFF = NT_H, B_OFF = NT_H + NA;
+    static constexpr int NH = NT_H + NA + NB;                          // entries in htw
+};
+
 // `mid` runs (in every thread) after the first round executed, before the
-// barrier that follows it.
+// barrier that follows it.  With row staging, `hw` runs before the first
+// round that reads htw and `ha` after the last one (wait for the buffer to be
+// filled, report it read).
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
-          bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false, bool PRELOAD_TW = false, class W = u64>
+          bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false, bool PRELOAD_TW = false, class W = u64,
+          int STAGE = 0, bool WARPX = false, class HW = NoHook, class HA = NoHook>
 __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>::Prime& pr,
                                              const typename WordTypes<W>::Tw* tw,
                                              const typename WordTypes<W>::Tw* ota,
                                              const typename WordTypes<W>::Tw* otb, const u32 u_base, const u32 s0,
-                                             const u32 tid, Hook mid = Hook())
+                                             const u32 tid, Hook mid = Hook(),
+                                             const typename WordTypes<W>::Tw* htw = nullptr, HW hw = HW(),
+                                             HA ha = HA())
 {
     constexpr int NR = nrounds(P, KMAX);
     static_assert(NR <= 4, "at most four rounds per pass");
     static_assert(FWD ? ct_range_max(XIN, P) <= 16 : gs_range_max(XIN, P) <= 8, "lazy range");
+    static_assert(STAGE == 0 || (ROWS && NR >= 2), "row staging needs a row pass of two rounds or more");
+    using RS = RowStaging<P, 1 << LOGC, KMAX, OTS, STAGE>;
+    constexpr int CRS = 1 << LOGC;
     ItemCtxT<W> c;
     c.q = pr.q;
     c.q4 = pr.q << 2;
     c.rc = pr.rc;
     c.rsh = pr.rsh;
     c.u = u_base;
+    c.ubase = u_base;
     c.hi = 0;
     c.s0 = s0;
     c.ninv = pr.ninv;
     c.w1ninv = pr.w1ninv;
     c.tw = tw;
-    c.ota = ota;
-    c.otb = otb;
+    c.ota = STAGE ? htw + RS::A_OFF : ota;
+    c.otb = STAGE ? htw + RS::B_OFF : otb;
+    (void)CRS;
+
+    // per round: where its table twiddles come from
+    constexpr int TWM_PLAIN = TW_SMEM ? TW_PASS : TW_GLOBAL;
+    constexpr int TWM0 = STAGE ? TW_STAGED : TWM_PLAIN;
+    constexpr int TWM1 = STAGE ? TW_STAGED : TWM_PLAIN;
+    constexpr int SB0 = 0, SB1 = RS::SSB;
+    constexpr int SOT = STAGE ? 1 : 0;
+    constexpr bool PRE = PRELOAD_TW && !STAGE;
+    ItemCtxT<W> c1 = c;
+    if constexpr (STAGE) {
+        c1.tw = htw;
+        if constexpr (STAGE == 2) c.tw = htw;
+    }
 
     // canonical output written by the last round executed
     constexpr int FWD_OUT = ct_range_after(XIN, P);
@@ -345,45 +442,53 @@ __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>:
     constexpr int CANON_INV = FINAL ? (HAS_S0 ? 4 : gs_range_after(XIN, P)) : 0;
 
     if constexpr (FWD) {
+        if constexpr (STAGE == 2) hw();
         run_round<P, LOGC, KMAX, 0, ROWS, true, round_in_range<P, KMAX, true, XIN, 0>(), OTS, false,
-                  (NR == 1 ? CANON_FWD : 0), !TW_SMEM, NT, false>(sm, c, u_base, tid);
+                  (NR == 1 ? CANON_FWD : 0), TWM0, CRS, SB0, SOT, NT, false>(sm, c, u_base, tid);
         mid();
         if constexpr (NR > 1) {
-            round_barrier<NT, NAMED>();
+            round_barrier<NT, NAMED, WARPX>();
+            if constexpr (STAGE == 1) hw();
             run_round<P, LOGC, KMAX, 1, ROWS, true, round_in_range<P, KMAX, true, XIN, 1>(), OTS, false,
-                      (NR == 2 ? CANON_FWD : 0), !TW_SMEM, NT, false>(sm, c, u_base, tid);
+                      (NR == 2 ? CANON_FWD : 0), TWM1, CRS, SB1, SOT, NT, false>(sm, c1, u_base, tid);
+            if constexpr (STAGE && NR == 2) ha();
         }
         if constexpr (NR > 2) {
-            round_barrier<NT, NAMED>();
+            round_barrier<NT, NAMED, WARPX>();
             run_round<P, LOGC, KMAX, 2, ROWS, true, round_in_range<P, KMAX, true, XIN, 2>(), OTS, false,
-                      (NR == 3 ? CANON_FWD : 0), !TW_SMEM, NT, false>(sm, c, u_base, tid);
+                      (NR == 3 ? CANON_FWD : 0), TWM1, CRS, SB1, SOT, NT, false>(sm, c1, u_base, tid);
+            if constexpr (STAGE && NR == 3) ha();
         }
         if constexpr (NR > 3) {
-            round_barrier<NT, NAMED>();
+            round_barrier<NT, NAMED, WARPX>();
             run_round<P, LOGC, KMAX, 3, ROWS, true, round_in_range<P, KMAX, true, XIN, 3>(), OTS, false,
-                      CANON_FWD, !TW_SMEM, NT, false>(sm, c, u_base, tid);
+                      CANON_FWD, TWM1, CRS, SB1, SOT, NT, false>(sm, c1, u_base, tid);
+            if constexpr (STAGE) ha();
         }
     } else {
+        if constexpr (STAGE) hw();
         if constexpr (NR > 3) {
-            run_round<P, LOGC, KMAX, 3, ROWS, false, round_in_range<P, KMAX, false, XIN, 3>(), OTS, false, 0, !TW_SMEM, NT, PRELOAD_TW>(
-                sm, c, u_base, tid);
+            run_round<P, LOGC, KMAX, 3, ROWS, false, round_in_range<P, KMAX, false, XIN, 3>(), OTS, false, 0, TWM1,
+                      CRS, SB1, SOT, NT, PRE>(sm, c1, u_base, tid);
             if constexpr (NR == 4) mid();
-            round_barrier<NT, NAMED>();
+            round_barrier<NT, NAMED, WARPX>();
         }
         if constexpr (NR > 2) {
-            run_round<P, LOGC, KMAX, 2, ROWS, false, round_in_range<P, KMAX, false, XIN, 2>(), OTS, false, 0, !TW_SMEM, NT, PRELOAD_TW>(
-                sm, c, u_base, tid);
+            run_round<P, LOGC, KMAX, 2, ROWS, false, round_in_range<P, KMAX, false, XIN, 2>(), OTS, false, 0, TWM1,
+                      CRS, SB1, SOT, NT, PRE>(sm, c1, u_base, tid);
             if constexpr (NR == 3) mid();
-            round_barrier<NT, NAMED>();
+            round_barrier<NT, NAMED, WARPX>();
         }
         if constexpr (NR > 1) {
-            run_round<P, LOGC, KMAX, 1, ROWS, false, round_in_range<P, KMAX, false, XIN, 1>(), OTS, false, 0, !TW_SMEM, NT, PRELOAD_TW>(
-                sm, c, u_base, tid);
+            run_round<P, LOGC, KMAX, 1, ROWS, false, round_in_range<P, KMAX, false, XIN, 1>(), OTS, false, 0, TWM1,
+                      CRS, SB1, SOT, NT, PRE>(sm, c1, u_base, tid);
+            if constexpr (STAGE == 1) ha();
             if constexpr (NR == 2) mid();
-            round_barrier<NT, NAMED>();
+            round_barrier<NT, NAMED, WARPX>();
         }
-        run_round<P, LOGC, KMAX, 0, ROWS, false, round_in_range<P, KMAX, false, XIN, 0>(), OTS, HAS_S0,
-                  CANON_INV, !TW_SMEM, NT, PRELOAD_TW>(sm, c, u_base, tid);
+        run_round<P, LOGC, KMAX, 0, ROWS, false, round_in_range<P, KMAX, false, XIN, 0>(), OTS, HAS_S0, CANON_INV,
+                  TWM0, CRS, SB0, SOT, NT, PRE>(sm, c, u_base, tid);
+        if constexpr (STAGE == 2) ha();
         if constexpr (NR == 1) mid();
     }
 }
