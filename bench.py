@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--launch-steps", type=int, default=500,
                     help="steps of the single-stream pass that times each launch")
+    ap.add_argument("--split-calls", action="store_true",
+                    help="each step as two calls (ntt_forward, ntt_inverse) instead of one ntt_execute")
     return ap.parse_args()
 
 
@@ -840,11 +842,17 @@ def main():
     lib = G.lib()
     handles = [p.handle for p in plans]
 
+    both = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+
     def step(i):
         j = i % S
         b = bufs[i % nbuf].data_ptr()
         sh = streams[j].cuda_stream
-        if lib.ntt_forward(handles[j], b, 1, sh) or lib.ntt_inverse(handles[j], b, 1, sh):
+        if args.split_calls:
+            bad = lib.ntt_forward(handles[j], b, 1, sh) or lib.ntt_inverse(handles[j], b, 1, sh)
+        else:
+            bad = lib.ntt_execute(handles[j], b, 1, both, sh)
+        if bad:
             raise RuntimeError("launch failed: " + G.ntt_last_cuda_error())
 
     for i in range(max(args.warmup, S)):
@@ -887,11 +895,13 @@ def main():
             raise RuntimeError("device status reports a failed bounded wait")
     value = whole_job_value(L, K, ws, total_ms)
 
-    # per-launch durations of the transform kernels, one stream, CUDA events
-    # around every call (launches do not overlap here)
+    # per-launch durations, one stream, CUDA events around every call
+    # (launches do not overlap here): the separate forward and inverse calls,
+    # and the one-launch forward + inverse call
     Kp = min(K, args.launch_steps)
     s0 = streams[0]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Kp + 1)]
+    evc = [torch.cuda.Event(enable_timing=True) for _ in range(Kp + 1)]
     torch.cuda.synchronize()
     with torch.cuda.stream(s0):
         ev[0].record(s0)
@@ -901,20 +911,33 @@ def main():
             ev[2 * i + 1].record(s0)
             _ok(G, lib.ntt_inverse(handles[0], b, 1, s0.cuda_stream), "inverse")
             ev[2 * i + 2].record(s0)
+        evc[0].record(s0)
+        for i in range(Kp):
+            _ok(G, lib.ntt_execute(handles[0], bufs[i % nbuf].data_ptr(), 1, both, s0.cuda_stream), "execute")
+            evc[i + 1].record(s0)
     torch.cuda.synchronize()
     fwd_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Kp)]
     inv_ms = [ev[2 * i + 1].elapsed_time(ev[2 * i + 2]) for i in range(Kp)]
+    chain_ms = [evc[i].elapsed_time(evc[i + 1]) for i in range(Kp)]
     single_ms = ev[0].elapsed_time(ev[2 * Kp]) / Kp
 
     peak, peak_src = measured_peak_hbm()
     fwd_avg = float(np.mean(fwd_ms))
     inv_avg = float(np.mean(inv_ms))
-    dom_name, dom_ms = ("ntt_forward", fwd_avg) if fwd_avg >= inv_avg else ("ntt_inverse", inv_avg)
-    alg_bytes = 2 * poly_bytes                       # one read + one write per transform
+    chain_avg = float(np.mean(chain_ms))
+    chained = info.kernel == G.NTT_KERNEL_FUSED and info.passes == 2
+    bfly_per_transform = L * (N // 2) * (N.bit_length() - 1)      # (N/2) log2 N butterflies per limb
+    if chained and not args.split_calls:
+        # the timed steps' launch: forward + inverse of the polynomial
+        dom_name, dom_ms, per_launch = "ntt_execute (forward + inverse, 1 fused launch)", chain_avg, 2
+    else:
+        dom_name, dom_ms = ("ntt_forward", fwd_avg) if fwd_avg >= inv_avg else ("ntt_inverse", inv_avg)
+        per_launch = 1
+    alg_bytes = 2 * poly_bytes * per_launch          # one read + one write per transform
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-    bfly_per_launch = L * (N // 2) * (N.bit_length() - 1)         # (N/2) log2 N butterflies per limb
+    bfly_per_launch = bfly_per_transform * per_launch
     bfly_achieved = bfly_per_launch / (dom_ms / 1e3) / 1e9
-    step_bytes = 2 * alg_bytes
+    step_bytes = 4 * poly_bytes                      # forward + inverse, each one read + one write
     frac_step = (step_bytes * K / (total_ms / 1e3) / 1e9) / peak
 
     # end to end through the host-buffer C ABI call (pinned host memory)
@@ -1005,9 +1028,10 @@ def main():
         cpu["single_thread"] = {"value": v1, "unit": unit, "cores": 1, "sample": s1}
         cpu["large_ring_c3"] = {"value": v3, "unit": unit, "cores": c3, "sample": s3}
     twname = "table" if info.twiddle_mode == G.NTT_TWIDDLE_TABLE else f"ot{int(info.ot_stages)}"
-    kname = f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})"
-    prof = profile_traffic(int(info.geometry), twname, "forward" if dom_name == "ntt_forward" else "inverse") \
-        if info.kernel == G.NTT_KERNEL_FUSED else None
+    kname = dom_name if per_launch == 2 else \
+        f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})"
+    direction = "forward+inverse" if per_launch == 2 else ("forward" if dom_name == "ntt_forward" else "inverse")
+    prof = profile_traffic(int(info.geometry), twname, direction) if info.kernel == G.NTT_KERNEL_FUSED else None
     traffic = prof["dram_bytes"] if prof else None
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": K,
@@ -1022,22 +1046,25 @@ def main():
                                               "twiddle_read_bytes", "how") if k in prof},
                      "kernel": kname,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
-                     "units_per_launch": f"{L} limb-NTTs of N={N} (16 N bytes each: one read, one write)",
-                     "launch_timing": f"CUDA events around each of {Kp} forward and inverse launches on one stream",
+                     "units_per_launch": f"{per_launch * L} limb-NTTs of N={N} (16 N bytes each: one read, one write)",
+                     "launch_timing": f"CUDA events around each of {Kp} launches on one stream",
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
         "roofline_alu": {"bound": "alu", "achieved": bfly_achieved, "peak": alu_peak_gbfly(),
                          "unit": "G butterfly/s", "frac": bfly_achieved / alu_peak_gbfly(),
                          "kernel": kname,
-                         "units_per_launch": f"{bfly_per_launch} butterflies ({L} limbs x (N/2) log2 N)",
+                         "units_per_launch": f"{bfly_per_launch} butterflies ({per_launch * L} limb-NTTs x (N/2) log2 N)",
                          "avg_launch_us": dom_ms * 1e3,
                          "peak_source": "152 SMs x 2070 MHz x 4.57 butterflies per SM-clock (FMA-heavy pipe: "
                                         "2 IMAD.HI + 3 IMAD.WIDE at 4 cycles and 4 IMAD at 2 cycles per warp butterfly)",
                          "peak_measured": None if args.no_peak_measure else G.ntt_measure_butterfly_rate(),
                          "peak_measured_source": "ntt_measure_butterfly_rate: register-only butterfly loop, live",
-                         "timed_region_frac": bfly_per_launch * 2 * K / (total_ms / 1e3) / 1e9 / alu_peak_gbfly()},
+                         "timed_region_frac": bfly_per_transform * 2 * K / (total_ms / 1e3) / 1e9 / alu_peak_gbfly()},
         "per_transform_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3,
+                             "forward_plus_inverse_one_launch": chain_avg * 1e3,
                              "timed_region_per_transform": total_ms * 1e3 / (2 * K),
-                             "single_stream_per_transform": single_ms * 1e3 / 2},
+                             "single_stream_per_transform": single_ms * 1e3 / 2,
+                             "single_stream_per_transform_one_launch": chain_avg * 1e3 / 2},
+        "step_call": "ntt_forward + ntt_inverse" if args.split_calls else "ntt_execute(FORWARD | INVERSE)",
         "plan": {"twiddle_mode": int(info.twiddle_mode), "ot_stages": int(info.ot_stages),
                  "passes": int(info.passes), "pass1_log2": int(info.pass1_log2),
                  "row_tile_log2": int(info.row_tile_log2), "geometry": int(info.geometry),
@@ -1053,7 +1080,8 @@ def main():
         "twiddle_modes_c2": modes,
         "single_limb_c1": c1,
         "word_size": words,
-        "gpu_launches": K * 2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes)),
+        "gpu_launches": K * (1 if chained and not args.split_calls else
+                             2 * (1 if info.kernel == G.NTT_KERNEL_FUSED else int(info.passes))),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

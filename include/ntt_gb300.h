@@ -187,11 +187,28 @@ ntt_status ntt_mul_pointwise(const ntt_plan* plan, const uint64_t* a, const uint
 ntt_status ntt_mul_negacyclic(const ntt_plan* plan, uint64_t* a, uint64_t* b, uint64_t* c, uint32_t batch,
                               void* stream);
 
-/* Operation flags for ntt_execute_host. */
+/* Operation flags for ntt_execute and ntt_execute_host. */
 enum {
     NTT_OP_FORWARD = 1,
     NTT_OP_INVERSE = 2          /* with NTT_OP_FORWARD: forward, then inverse */
 };
+
+/*
+ * The operations in `ops` on `batch` polynomials at device address `data`
+ * (as ntt_forward / ntt_inverse): NTT_OP_FORWARD, NTT_OP_INVERSE, or both
+ * (the forward transform, then the inverse of its result).  With both and a
+ * plan of the fused two-pass kernel (N >= 2^13), the two transforms run in one
+ * launch: the forward's column pass, its row pass, the inverse's row pass and
+ * its column pass of every limb in one persistent kernel, each pass of a limb
+ * starting when the previous pass of that limb has been written back (no
+ * launch boundary between the directions).  Results equal ntt_forward then
+ * ntt_inverse; the forward's result is written to `data` and read back by the
+ * inverse, as with two calls.  Other plans make one call per direction.
+ * The chained launch needs a work area for three times the limbs; the plan's
+ * grows on first use as for ntt_forward.  Errors as ntt_forward, and
+ * NTT_ERR_INVALID_ARG for bad `ops`.
+ */
+ntt_status ntt_execute(const ntt_plan* plan, uint64_t* data, uint32_t batch, uint32_t ops, void* stream);
 
 /*
  * Host-memory convenience call: copy `batch` polynomials from host_in to the

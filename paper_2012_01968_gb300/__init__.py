@@ -143,6 +143,8 @@ def _lib():
             L.ntt_mul_negacyclic.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
             L.ntt_mul_pointwise.restype = S
             L.ntt_mul_pointwise.argtypes = [_vp, _vp, _vp, _vp, _u32, _vp]
+            L.ntt_execute.restype = S
+            L.ntt_execute.argtypes = [_vp, _vp, _u32, _u32, _vp]
             for f in ("ntt_execute_host", "ntt_execute_host_async"):
                 getattr(L, f).restype = S
                 getattr(L, f).argtypes = [_vp, _vp, _vp, _u32, _u32, _vp]
@@ -304,6 +306,11 @@ def ntt_mul_negacyclic(plan: int, a, b, c, batch: int, stream=None) -> None:
     first pass applies the element-wise product."""
     _check(_lib().ntt_mul_negacyclic(plan, _addr(a), _addr(b), _addr(c), batch, _stream(stream, a)),
            "ntt_mul_negacyclic")
+
+
+def ntt_execute(plan: int, data, batch: int, ops: int, stream=None) -> None:
+    """Device data in place: forward, inverse, or both (one launch for fused plans)."""
+    _check(_lib().ntt_execute(plan, _addr(data), batch, ops, _stream(stream, data)), "ntt_execute")
 
 
 def _host_ptr(x) -> int:
@@ -480,6 +487,9 @@ class Plan:
 
     def inverse(self, data, batch: int = 1, stream=None):
         ntt_inverse(self.handle, data, batch, stream)
+
+    def execute(self, data, ops: int, batch: int = 1, stream=None):
+        ntt_execute(self.handle, data, batch, ops, stream)
 
     def info(self) -> PlanInfo:
         return ntt_plan_query(self.handle)

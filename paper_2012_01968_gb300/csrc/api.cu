@@ -98,6 +98,23 @@ ntt_status to_status(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? NTT_ERR_OOM : NTT_ERR_CUDA;
 }
 
+// Whether forward + inverse of a plan runs as one launch (fused two-pass plans).
+bool chains(const ntt_plan* p) { return p->passes == 2 && p->kernel == NTT_KERNEL_FUSED; }
+
+// The operations `ops` (NTT_OP_*) on one launch context: forward + inverse as
+// one chained launch where the plan allows it, else one call per direction.
+cudaError_t launch_ops(const ntt_plan* p, ntt::LaunchCtx c, uint32_t ops)
+{
+    if (ops == (NTT_OP_FORWARD | NTT_OP_INVERSE) && chains(p)) {
+        c.chain = 1;
+        return ntt::launch_transform(c, true);
+    }
+    cudaError_t e = cudaSuccess;
+    if (ops & NTT_OP_FORWARD) e = ntt::launch_transform(c, true);
+    if (e == cudaSuccess && (ops & NTT_OP_INVERSE)) e = ntt::launch_transform(c, false);
+    return e;
+}
+
 ntt_status transform(const ntt_plan* p, uint64_t* data, uint32_t batch, uint32_t levels, void* stream,
                      bool fwd)
 {
@@ -116,6 +133,24 @@ ntt_status transform(const ntt_plan* p, uint64_t* data, uint32_t batch, uint32_t
 }  // namespace
 
 extern "C" {
+
+ntt_status ntt_execute(const ntt_plan* p, uint64_t* data, uint32_t batch, uint32_t ops, void* stream)
+{
+    if (!p || !data || batch == 0) return NTT_ERR_INVALID_ARG;
+    if (ops == 0 || (ops & ~(uint32_t)(NTT_OP_FORWARD | NTT_OP_INVERSE))) return NTT_ERR_INVALID_ARG;
+    if (!aligned16(data)) return NTT_ERR_MISALIGNED;
+    const uint64_t limbs = (uint64_t)batch * p->L;
+    if (limbs > 0xFFFFFFFFull) return NTT_ERR_INVALID_ARG;
+    const bool chain = ops == (NTT_OP_FORWARD | NTT_OP_INVERSE) && chains(p);
+    const uint64_t need = chain ? ntt::chain_work_limbs(limbs) : limbs;
+    if (need > 0xFFFFFFFFull) return NTT_ERR_INVALID_ARG;
+    if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED && p->work_limbs < need) {
+        cudaError_t e = ntt_internal_grow_work(const_cast<ntt_plan*>(p), (uint32_t)need);
+        if (e != cudaSuccess) return to_status(e);
+    }
+    const ntt::LaunchCtx c = p->ctx(data, (uint32_t)limbs, p->L, (cudaStream_t)stream);
+    return to_status(launch_ops(p, c, ops));
+}
 
 ntt_status ntt_forward(const ntt_plan* p, uint64_t* data, uint32_t batch, void* stream)
 {
@@ -259,7 +294,10 @@ static ntt_status host_pipeline(const ntt_plan* cp, const uint64_t* host_in, uin
         const cudaError_t so = cudaStreamSynchronize(p->h_out);
         return se == cudaSuccess ? so : se;
     };
-    if (p->stage_bytes < bytes || p->hwork_limbs < seg_max) {
+    // a chained forward + inverse launch needs the larger work area
+    const uint32_t work_need = ops == (NTT_OP_FORWARD | NTT_OP_INVERSE) && chains(p)
+                                   ? (uint32_t)ntt::chain_work_limbs(seg_max) : seg_max;
+    if (p->stage_bytes < bytes || p->hwork_limbs < work_need) {
         // earlier asynchronous calls may still use the staging: drain first
         e = drain();
         if (e != cudaSuccess) return to_status(e);
@@ -270,7 +308,7 @@ static ntt_status host_pipeline(const ntt_plan* cp, const uint64_t* host_in, uin
         p->stage_bytes = 0;
         p->hwork_limbs = 0;
         for (int b = 0; b < ntt_plan::kHostBuffers; ++b) p->h_prev_segs[b] = 0;
-        const size_t wwords = ntt::fused_work_words(seg_max) * ntt_plan::kHostCompute;
+        const size_t wwords = ntt::fused_work_words(work_need) * ntt_plan::kHostCompute;
         e = cudaMalloc(&p->d_stage, bytes * ntt_plan::kHostBuffers);
         if (e == cudaSuccess) e = cudaMalloc(&p->d_hwork, wwords * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMemset(p->d_hwork, 0, wwords * sizeof(uint32_t));
@@ -279,7 +317,7 @@ static ntt_status host_pipeline(const ntt_plan* cp, const uint64_t* host_in, uin
             return to_status(e);
         }
         p->stage_bytes = bytes;
-        p->hwork_limbs = seg_max;
+        p->hwork_limbs = work_need;
     }
 
     // this call's staging buffer (alternate calls use alternate buffers)
@@ -311,8 +349,7 @@ static ntt_status host_pipeline(const ntt_plan* cp, const uint64_t* host_in, uin
         ntt::LaunchCtx c = p->ctx_range(stage + off, sg.count, sg.lview, sg.prime0, s);
         c.work = p->d_hwork + ntt::fused_work_words(p->hwork_limbs) * (size_t)k;
         c.work_limbs = p->hwork_limbs;
-        if (ops & NTT_OP_FORWARD) e = ntt::launch_transform(c, true);
-        if (e == cudaSuccess && (ops & NTT_OP_INVERSE)) e = ntt::launch_transform(c, false);
+        e = launch_ops(p, c, ops);
         if (e == cudaSuccess) e = cudaEventRecord(p->h_done[i], s);
     }
     for (size_t i = 0; i < segs.size() && e == cudaSuccess; ++i) {

@@ -93,15 +93,4 @@ const DevAttrs& attrs()
 
 int device_sm_count() { return attrs().sms.load(std::memory_order_acquire); }
 
-// Limbs whose first-pass results may wait in L2 for their second pass: the
-// window of the fused kernel's A queue, sized to 3/8 of the device's L2.
-u32 fused_window_limbs(size_t limb_bytes)
-{
-    const DevAttrs& a = attrs();
-    (void)a.sms.load(std::memory_order_acquire);
-    const size_t budget = (size_t)a.l2.load(std::memory_order_relaxed) / 8 * 3;
-    const size_t w = budget / (limb_bytes ? limb_bytes : 1);
-    return (u32)(w < 2 ? 2 : (w > 0xFFFFFFu ? 0xFFFFFFu : w));
-}
-
 }  // namespace ntt

@@ -164,19 +164,20 @@ struct Fused32Launch;
 cudaError_t launch_w32_fused(const Fused32Launch& c, bool fwd);
 
 // host helpers for the fused launch (fused_host.cu)
-u32 fused_window_limbs(size_t limb_bytes);
 cudaError_t encode_tile_maps(u64* data, u32 limbs, u32 n, int p1, int row_tile_words, CUtensorMap* mapC,
                              CUtensorMap* mapR);
 cudaError_t encode_tile_maps32(u32* data, u32 limbs, u32 n, int p1, int row_tile_words, CUtensorMap* mapC,
                                CUtensorMap* mapR);
 int device_sm_count();
 
-// One persistent launch over all limbs of all jobs, both passes.
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, bool MULB = false>
+// One persistent launch over all limbs of all jobs, both passes (CHAIN: the
+// forward and then the inverse transform, four passes).
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, bool MULB = false, bool CHAIN = false>
 cudaError_t launch_fused_dir(const JobsCtx& c)
 {
     using F = FusedCfg<P1, P2, LOGC_R, KMAX, u64, OTS>;
-    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS, MAXJ, u64, MULB>;
+    auto kern = ntt_fused_kernel<P1, P2, LOGC_R, KMAX, FWD, OTS, MAXJ, u64, MULB, CHAIN>;
+    constexpr u32 NP = fused_phases<FWD, CHAIN>();
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int occ = 0;
@@ -198,6 +199,8 @@ cudaError_t launch_fused_dir(const JobsCtx& c)
         a.job[j].tw = J.tw;
         a.job[j].ota = FWD ? J.ota_f : J.ota_i;
         a.job[j].otb = FWD ? J.otb_f : J.otb_i;
+        a.job[j].ota_inv = CHAIN ? J.ota_i : nullptr;
+        a.job[j].otb_inv = CHAIN ? J.otb_i : nullptr;
         // a product operand is only taken by the MULB instantiation
         if ((J.mulb != nullptr) != MULB || (J.mulb && ((uintptr_t)J.mulb & 15u))) return cudaErrorInvalidValue;
         a.job[j].mulb = J.mulb;
@@ -206,16 +209,19 @@ cudaError_t launch_fused_dir(const JobsCtx& c)
         a.job[j].limb0 = (u32)limbs;
         limbs += J.limbs;
     }
-    if (limbs == 0 || limbs > 0x7FFFFFFFull || !c.work || c.work_limbs < limbs) return cudaErrorInvalidValue;
+    // limbs are numbered in 28 bits by the publication entries; the work area
+    // must hold the launch's counters (fused_ctl_words)
+    if (limbs == 0 || limbs >= (1ull << 28) || !c.work ||
+        fused_work_words(c.work_limbs) < fused_ctl_words(NP, (size_t)limbs))
+        return cudaErrorInvalidValue;
     constexpr u32 UC = F::R2 / 16, UR = F::R1 / F::CR;
-    const u64 units = limbs * (UC + UR);
+    const u64 units = limbs * (UC + UR) * (CHAIN ? 2 : 1);
     const u64 slots = (u64)device_sm_count() * (u64)occ;
     const u32 grid = (u32)(units < slots ? units : slots);
     a.ctl = c.work;
     a.status = c.status;
     a.njobs = c.njobs;
     a.limbs = (u32)limbs;
-    a.a_window = fused_window_limbs(sizeof(u64) << (P1 + P2));
     a.max_polls = c.max_polls ? c.max_polls : 1u << 22;
     return launch_windowed(kern, dim3(grid), dim3(F::THREADS), F::SMEM, c.stream, c.l2_base, c.l2_bytes, c.l2_hit,
                            a);
@@ -225,6 +231,16 @@ template <int P1, int P2, int LOGC_R, int KMAX, int MAXJ>
 cudaError_t launch_fused(const JobsCtx& c, bool fwd)
 {
     if constexpr (MAXJ == 1) {
+        // forward, then inverse, in one launch (one job)
+        if (c.chain) {
+            if (!fwd || c.njobs != 1 || c.jobs[0].mulb) return cudaErrorInvalidValue;
+            switch (c.ots) {
+            case 0: return launch_fused_dir<P1, P2, LOGC_R, KMAX, true, 0, 1, false, true>(c);
+            case 1: return launch_fused_dir<P1, P2, LOGC_R, KMAX, true, 1, 1, false, true>(c);
+            case 2: return launch_fused_dir<P1, P2, LOGC_R, KMAX, true, 2, 1, false, true>(c);
+            default: return cudaErrorInvalidValue;
+            }
+        }
         // the inverse of an in-place negacyclic product (one job)
         if (!fwd && c.njobs == 1 && c.jobs[0].mulb) {
             switch (c.ots) {
@@ -296,7 +312,6 @@ cudaError_t launch_fused32_dir(const Fused32Launch& c)
     a.status = c.status;
     a.njobs = 1;
     a.limbs = c.limbs;
-    a.a_window = fused_window_limbs(sizeof(u32) << (P1 + P2));
     a.max_polls = 1u << 22;
     kern<<<grid, F::THREADS, F::SMEM, c.stream>>>(a);
     return cudaGetLastError();
@@ -327,8 +342,9 @@ cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
         }
     }
     const JobCtx job{c.data, c.limbs, c.L, c.primes, c.tw, c.tw_len, c.ota_f, c.otb_f, c.ota_i, c.otb_i, c.mulb};
-    const JobsCtx jc{&job,   1u,         c.n,      c.ots,        c.status,  c.work,   c.work_limbs,
-                     c.stream, c.max_polls, c.geom, c.l2_base, c.l2_bytes, c.l2_hit};
+    JobsCtx jc{&job,   1u,         c.n,      c.ots,        c.status,  c.work,   c.work_limbs,
+               c.stream, c.max_polls, c.geom, c.l2_base, c.l2_bytes, c.l2_hit};
+    jc.chain = c.chain;
     return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(jc, fwd);
 }
 

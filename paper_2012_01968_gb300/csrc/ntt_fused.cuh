@@ -1,57 +1,62 @@
-// Both passes of a two-pass transform in one persistent launch.
+// Both passes of a two-pass transform in one persistent launch (or the four
+// passes of a forward and the inverse of its result).
 //
-// Work unit = one tile of one pass of one limb.  The first-executed pass (A)
-// of a limb has no dependencies; a tile of the second pass (B) may start only
-// after every A tile of its limb has been written back (per-limb counters), so
-// limbs cross the pass boundary through L2 without a grid-wide barrier and
-// without a kernel boundary.  A limb whose A tiles are all written back is
-// "published": appended to a list in publication order, and B tickets are
-// handed out in that order, so a B tile waits only while no further limb has
-// been published, never for one particular slow limb.
+// Work unit = one tile of one pass ("phase") of one limb.  Phase 0 of a limb
+// has no dependencies; a tile of phase p > 0 may start only after every tile
+// of phase p - 1 of its limb has been written back (per-limb counters), so
+// limbs cross the pass boundaries through L2 without a grid-wide barrier and
+// without a kernel boundary.  A limb whose phase-p tiles are all written back
+// is "published" by phase p: appended to that phase's list in publication
+// order, and phase-(p+1) tickets are handed out in that order, so a tile waits
+// only while no further limb has been published, never for one particular
+// slow limb.  One transform has two phases (the forward: column pass, then
+// row pass; the inverse: row pass, then column pass); a forward + inverse
+// launch has four (forward column, forward row, inverse row, inverse column).
 //
 // Each CTA is warp-specialised:
-//   * NT compute threads transform tiles held in a ring of three shared-memory
+//   * NT compute threads transform tiles held in a ring of shared-memory
 //     buffers; they only wait for a buffer to be filled ("full" mbarrier) and
 //     report it computed ("empty" mbarrier).
-//   * one producer thread (its own warp) runs an event loop: it claims units
-//     from two global queues, at most one unit ahead of the one being
-//     computed (so the last units spread over the CTAs instead of queueing
-//     behind a few), preferring a B tile whose limb is already published and
-//     otherwise taking an A tile, so a CTA never idles on a dependency while
-//     other work is left; it loads tiles by TMA (2-D tensor
-//     maps with the 128-byte swizzle the compute rounds expect), together
-//     with the prime's constants and, for column tiles, the twiddles Psi[0,R1)
-//     of the column pass; it stores computed tiles by TMA and, once a store
-//     of an A tile has completed, publishes it on the limb's counter.
+//   * one producer thread (its own warp) runs an event loop: it claims units,
+//     at most one ahead of the unit being computed (so the last units spread
+//     over the CTAs instead of queueing behind a few); it loads tiles by TMA
+//     (2-D tensor maps with the 128-byte swizzle the compute rounds expect),
+//     together with the prime's constants and, for column tiles, the
+//     twiddles Psi[0, R1) of the column pass; it stores computed tiles by TMA
+//     and, once a store has completed, publishes it on its limb's counter.
 //
-// Order: A tiles are taken first while the A queue is less than a_window
-// limbs ahead of the B queue (the host sizes the window so that the
-// intermediate results of that many limbs stay in L2); beyond it a B tile
-// whose limb is published goes first.  Taking A tiles early keeps the
-// dependency waits off the end of the launch.
+// Claims: (1) a ticket of the latest phase whose limb is already published,
+// taken by compare-and-swap so that the ticket taken is the one checked
+// (later phases first: limbs finish, and leave L2, before new ones start);
+// (2) else a phase-0 ticket, which never waits; (3) else, once every ticket
+// of the phases below p is taken, a phase-p ticket, held until its limb is
+// published.  Deadlock freedom: a held ticket waits only for tiles of the
+// phase below, all of which are then claimed by CTAs that either compute them
+// or hold a ticket of a still lower phase, and phase 0 never waits; a CTA that
+// holds a ticket keeps storing and publishing its own finished tiles.  Every
+// wait is bounded; a wait that runs out sets the plan's status word and the
+// CTA stops.  (A CPU simulation of this protocol under random interleavings
+// checks these claims.)
 //
-// Row tiles read the twiddles of their second pass from the global table; the
-// producer prefetches the runs a row tile will read into L2 when it loads the
-// tile, so the compute warps' loads of them hit L2.
-//
-// Deadlock freedom: A tiles never wait.  A producer holds at most one B tile
-// whose limb is not yet published, and while it polls for that limb it keeps
-// storing and publishing its own finished tiles, so every A tile that any B
-// tile waits for is eventually published.  Every wait is bounded; a wait that
-// runs out sets the plan's status word and the CTA stops.
+// Twiddles of row tiles (64-bit words): where they fit, the producer stages
+// them in shared memory - round 0's table runs in the tile buffer with the
+// tile, the later rounds' runs and the OT factors in a per-CTA buffer filled
+// by bulk copies once the previous row tile has released it - so the compute
+// threads read no twiddle from global memory.  Otherwise row tiles read the
+// global table, which the producer prefetches into L2 with the tile.
 //
 // Jobs: one launch may transform several independent arrays ("jobs", up to
 // MAXJ), each with its own tensor maps and its own plan tables, all of the
 // same size and direction.  Limbs are numbered over the launch (job j owns
 // limbs [limb0_j, limb0_j + limbs_j)); tickets, counters and the publication
-// order use that numbering, and the producer finds a limb's job by binary
+// orders use that numbering, and the producer finds a limb's job by binary
 // search over limb0.
 //
-// Work area (owned by the caller, zero between launches; 4 + 2 * limbs
-// words): [0] next A ticket, [1] next B ticket, [2] CTAs finished, [3] limbs
-// published, [4 + limb] A tiles of the limb written back, [4 + limbs + i] the
-// i-th published limb plus one (0 while not yet published).  The last CTA to
-// finish zeroes it again.
+// Work area (owned by the caller, zero between launches; fused_ctl_words
+// words for NP phases): [p] next ticket of phase p, [NP + p] limbs published
+// by phase p (p < NP - 1), [2 NP - 1] CTAs finished, then for each phase
+// p < NP - 1 the tiles of each limb written back and the published limbs + 1
+// in publication order.  The last CTA to finish zeroes it again.
 #pragma once
 #include "ntt_pass.cuh"
 #include "tma.cuh"
@@ -76,6 +81,8 @@ struct FusedJobT {
     const typename WordTypes<W>::Tw* tw;         // [L][tw_len]
     const typename WordTypes<W>::Tw* ota;        // [L][2^p2]      OT A factors, this direction
     const typename WordTypes<W>::Tw* otb;        // [L][p2 << p1]  OT B factors, this direction
+    const typename WordTypes<W>::Tw* ota_inv;    // chained launches: the inverse's OT A factors
+    const typename WordTypes<W>::Tw* otb_inv;    // chained launches: the inverse's OT B factors
     const W* mulb;           // inverse, 64-bit words: data *= mulb element-wise
                              // before the first pass (null: no product)
     u32 tw_len;
@@ -96,8 +103,8 @@ struct FusedParams {
     u32* status;             // persistent error word
     u32 njobs;
     u32 limbs;               // all jobs
-    u32 a_window;            // limbs the A queue may run ahead before ready B tiles are preferred
     u32 max_polls;           // bound of every wait loop
+    u32 reserved;
 };
 
 template <int P1, int P2, int LOGC_R, int KMAX, class W = u64, int OTS = 0>
@@ -148,7 +155,7 @@ struct FusedCfg {
 
 // unit descriptor written by the producer into the buffer it fills
 struct __align__(16) UnitDesc {
-    u32 kind;    // KIND_A, KIND_B or KIND_STOP
+    u32 kind;    // the unit's phase, or KIND_STOP
     u32 limb;    // in the launch's numbering
     u32 tile;
     u32 prime;   // local limb % L of its job
@@ -156,7 +163,26 @@ struct __align__(16) UnitDesc {
     u32 local;   // limb within its job
     u32 pad[2];
 };
-enum : u32 { KIND_A = 0u, KIND_B = 1u, KIND_STOP = 2u };
+enum : u32 { KIND_STOP = 15u };
+
+// Phases of a launch.  One transform (CHAIN false): phase 0 is the pass
+// executed first (the column pass of the forward transform, the row pass of
+// the inverse), phase 1 the other.  CHAIN: the forward then the inverse
+// transform of the same data in one launch: the forward's column pass, its
+// row pass, the inverse's row pass, the inverse's column pass.  A tile of
+// phase p > 0 may start once every tile of phase p - 1 of its limb has been
+// written back.
+template <bool FWD, bool CHAIN>
+__host__ __device__ constexpr u32 fused_phases() { return CHAIN ? 4u : 2u; }
+template <bool FWD, bool CHAIN>
+__host__ __device__ constexpr bool phase_is_col(u32 p) { return CHAIN ? (p == 0 || p == 3) : (FWD ? p == 0 : p == 1); }
+template <bool FWD, bool CHAIN>
+__host__ __device__ constexpr bool phase_is_fwd(u32 p) { return CHAIN ? p < 2 : FWD; }
+// 32-bit words of the work area of a launch of `phases` phases over `limbs` limbs
+__host__ __device__ constexpr size_t fused_ctl_words(u32 phases, size_t limbs)
+{
+    return 2 * (size_t)phases + 2 * (size_t)(phases - 1) * limbs;
+}
 
 // all compute threads agree on a flag (named barrier 1 with reduction)
 template <int NT>
@@ -175,12 +201,15 @@ __device__ __forceinline__ bool compute_any(bool flag)
 }
 
 // MULB: an inverse whose first pass applies an element-wise product
-// (FusedJobT::mulb; 64-bit words only)
-template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, class W = u64, bool MULB = false>
+// (FusedJobT::mulb; 64-bit words only).  CHAIN: the forward then the inverse
+// transform in one launch (FWD true; see fused_phases).
+template <int P1, int P2, int LOGC_R, int KMAX, bool FWD, int OTS, int MAXJ, class W = u64, bool MULB = false,
+          bool CHAIN = false>
 __global__ void __launch_bounds__(FusedCfg<P1, P2, LOGC_R, KMAX, W>::THREADS,
                                   FusedCfg<P1, P2, LOGC_R, KMAX, W>::MIN_CTAS)
 ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
 {
+    static_assert(!CHAIN || (FWD && !MULB), "a chained launch runs the forward, then the inverse, without a product");
     using F = FusedCfg<P1, P2, LOGC_R, KMAX, W, OTS>;
     using TwT = typename F::TwT;
     using PrimeT = typename F::PrimeT;
@@ -188,11 +217,15 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
     constexpr int NT = F::NT;
     constexpr int NBUF = F::NBUF;
     constexpr int STAGE = F::STAGE;
+    constexpr u32 NP = fused_phases<FWD, CHAIN>();
     constexpr u32 UC = F::R2 / F::COLW;     // column tiles per limb
     constexpr u32 UR = F::R1 / F::CR;       // row tiles per limb
-    constexpr u32 UA = FWD ? UC : UR, UB = FWD ? UR : UC;
-    constexpr int X_B = FWD ? ct_range_after(1, P1) : gs_range_after(1, P2);
+    constexpr int X_RF = ct_range_after(1, P1);     // entering the forward's row pass
+    constexpr int X_CI = gs_range_after(1, P2);     // entering the inverse's column pass
     constexpr u32 NONE = 0xFFFFFFFFu;
+    auto is_col = [](u32 kind) { return phase_is_col<FWD, CHAIN>(kind); };
+    auto is_fwd = [](u32 kind) { return phase_is_fwd<FWD, CHAIN>(kind); };
+    auto units = [](u32 p) -> u32 { return phase_is_col<FWD, CHAIN>(p) ? UC : UR; };
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     auto buf_tile = [&](int b) { return reinterpret_cast<W*>(smem_raw + b * F::BUF); };
@@ -217,20 +250,21 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
     }
     __syncthreads();
 
-    // an A (first-executed pass) tile is a column tile for the forward
-    // transform and a row tile for the inverse
-    auto is_col = [](u32 kind) { return FWD ? kind == KIND_A : kind == KIND_B; };
-
     if (tid >= (u32)NT) {
         if (tid != (u32)NT) return;
         // =================================================== producer ====
-        u32* const done = a.ctl + 4;
-        u32* const order = a.ctl + 4 + a.limbs;  // published limbs + 1, in publication order
-        const u32 totalA = a.limbs * UA, totalB = a.limbs * UB;
+        // work area: [p] next ticket of phase p; [NP + p] limbs published by
+        // phase p (p < NP - 1); [2 NP - 1] CTAs finished; then per phase
+        // p < NP - 1 the tiles of each limb written back and the published
+        // limbs + 1 in publication order
+        u32* const ctl = a.ctl;
+        auto done_of = [&](u32 p) { return ctl + 2 * NP + 2 * p * a.limbs; };
+        auto list_of = [&](u32 p) { return ctl + 2 * NP + (2 * p + 1) * a.limbs; };
         u32 issued = 0, stored = 0;             // units loaded / stored by this CTA
         u32 q0 = 0, q1 = 0, q2 = 0, qn = 0;      // committed stores not yet published (FIFO)
-        bool a_left = true, b_left = true, stopped = false, failed = false;
-        u32 held = NONE;                         // claimed B ticket waiting for its limb
+        u32 left = (1u << NP) - 1u;              // phases that may still have tickets
+        bool stopped = false, failed = false;
+        u32 held = NONE, held_p = 0;             // claimed ticket waiting for its limb
         u32 idle = 0;
 
         // job of a limb of the launch (binary search over limb0)
@@ -246,15 +280,20 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             }
             return lo;
         };
-
+        // the i-th limb published by phase p, NONE while unpublished
+        auto pub_limb = [&](u32 p, u32 i) -> u32 {
+            const u32 v = ld_acquire(&list_of(p)[i]);
+            return v ? v - 1u : NONE;
+        };
+        // a completed store of a tile of phase p < NP - 1 counts for its limb
         auto publish_entry = [&](u32 e) {
-            if (e & 0x80000000u) {
-                const u32 limb = e & 0x7FFFFFFFu;
+            if (e) {
+                const u32 p = (e >> 28) - 1u, limb = e & 0x0FFFFFFFu;
                 fence_proxy_async_global();
-                if (atom_acq_rel_add(&done[limb], 1u) == UA - 1u) {
+                if (atom_acq_rel_add(&done_of(p)[limb], 1u) == units(p) - 1u) {
                     // this tile completed the limb: append it to the publication order
-                    const u32 pos = atomicAdd(&a.ctl[3], 1u);
-                    st_release(&order[pos], limb + 1u);
+                    const u32 pos = atomicAdd(&ctl[NP + p], 1u);
+                    st_release(&list_of(p)[pos], limb + 1u);
                 }
             }
         };
@@ -277,9 +316,10 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 qn = 0;
             }
         };
-        // first table entry of stage sl's run for rows [u0, u0 + CR)
-        auto run_start = [&](int sl, u32 u0) -> u32 {
-            return FWD ? (1u << (P1 + sl)) + (u0 << sl) : (2u << (P1 + sl)) - ((u0 + (u32)F::CR) << sl);
+        // first table entry of stage sl's run for rows [u0, u0 + CR), read by
+        // the forward (or, mirrored, by the inverse)
+        auto run_start = [&](int sl, u32 u0, bool fwd) -> u32 {
+            return fwd ? (1u << (P1 + sl)) + (u0 << sl) : (2u << (P1 + sl)) - ((u0 + (u32)F::CR) << sl);
         };
         // row tiles loaded whose staged twiddles are still to be copied into
         // htw (unit numbers, in load order), and the copies issued so far
@@ -292,20 +332,23 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 if (fills && !mbar_test(htw_empty, (fills - 1) & 1u)) return false;
                 const volatile UnitDesc* d = buf_desc((int)(hq[hq_head % NBUF] % NBUF));
                 const u32 j = MAXJ > 1 ? d->job : 0u, pi = d->prime, u0 = d->tile * (u32)F::CR;
+                const bool fwd = is_fwd(d->kind);
                 const FusedJobT<W>& J = a.job[j];
                 const TwT* base = J.tw + (size_t)pi * J.tw_len;
                 mbar_arrive_expect_tx(htw_full, (u32)RS::NH * (u32)sizeof(TwT));
 #pragma unroll
                 for (int sl = RS::SSB; sl < P2 - OTS; ++sl)
-                    bulk_load(htw + F::CR * ((1 << sl) - (1 << RS::SSB)), base + run_start(sl, u0),
+                    bulk_load(htw + F::CR * ((1 << sl) - (1 << RS::SSB)), base + run_start(sl, u0, fwd),
                               ((u32)F::CR << sl) * (u32)sizeof(TwT), htw_full);
                 if constexpr (OTS > 0) {
-                    bulk_load(htw + RS::A_OFF, J.ota + (size_t)pi * F::R2 + (1u << (P2 - OTS)),
+                    const TwT* ota = CHAIN && !fwd ? J.ota_inv : J.ota;
+                    const TwT* otb = CHAIN && !fwd ? J.otb_inv : J.otb;
+                    bulk_load(htw + RS::A_OFF, ota + (size_t)pi * F::R2 + (1u << (P2 - OTS)),
                               (u32)RS::NA * (u32)sizeof(TwT), htw_full);
 #pragma unroll
                     for (int i = 0; i < OTS; ++i)
                         bulk_load(htw + RS::B_OFF + i * F::CR,
-                                  J.otb + (size_t)pi * ((size_t)P2 << P1) + ((size_t)(P2 - OTS + i) << P1) + u0,
+                                  otb + (size_t)pi * ((size_t)P2 << P1) + ((size_t)(P2 - OTS + i) << P1) + u0,
                                   (u32)F::CR * (u32)sizeof(TwT), htw_full);
                 }
                 ++hq_head;
@@ -331,7 +374,8 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             // unstored when a unit is claimed, so at most two stores were
             // committed after that one; waiting for all but the newest suffices
             bulk_wait_read<1>();
-            if (kind == KIND_B) fence_proxy_async_global();
+            // a tile of a later phase reads what other CTAs' stores wrote
+            if (kind > 0) fence_proxy_async_global();
             W* dst = buf_tile(b);
             if (is_col(kind)) {
                 mbar_arrive_expect_tx(&full[b], F::TILE_C * (u32)sizeof(W) + F::R1 * (u32)sizeof(TwT) +
@@ -339,6 +383,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 tma_load_2d(dst, &a.mapC[j], (int)(tile * F::COLW), (int)(local * F::R1), &full[b]);
                 bulk_load(buf_tw(b), J.tw + (size_t)pi * J.tw_len, F::R1 * (u32)sizeof(TwT), &full[b]);
             } else {
+                const bool fwd = is_fwd(kind);
                 mbar_arrive_expect_tx(&full[b], F::TILE_R * (u32)sizeof(W) + (u32)sizeof(PrimeT) +
                                                     (u32)RS::N0 * (u32)sizeof(TwT));
                 tma_load_2d(dst, &a.mapR[j], 0,
@@ -351,7 +396,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                     // round 0's runs into the tile buffer, with the tile
 #pragma unroll
                     for (int sl = 0; sl < RS::KR0; ++sl)
-                        bulk_load(buf_tw(b) + F::CR * ((1 << sl) - 1), base + run_start(sl, u0),
+                        bulk_load(buf_tw(b) + F::CR * ((1 << sl) - 1), base + run_start(sl, u0, fwd),
                                   ((u32)F::CR << sl) * (u32)sizeof(TwT), &full[b]);
                 }
                 if constexpr (STAGE) {
@@ -360,7 +405,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                     // into L2, for the compute threads' loads
 #pragma unroll
                     for (int sl = 0; sl < P2 - OTS; ++sl)
-                        bulk_prefetch_l2(base + run_start(sl, u0), ((u32)F::CR << sl) * (u32)sizeof(TwT));
+                        bulk_prefetch_l2(base + run_start(sl, u0, fwd), ((u32)F::CR << sl) * (u32)sizeof(TwT));
                 }
                 // the other factor of a fused element-wise product (the inverse's
                 // first pass multiplies the tile by it), into L2
@@ -373,21 +418,55 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             bulk_load(buf_pr(b), J.primes + pi, (u32)sizeof(PrimeT), &full[b]);
             ++issued;
         };
-        // limb of B ticket t: the (t / UB)-th published limb, NONE while unpublished
-        auto b_limb = [&](u32 t) -> u32 {
-            const u32 v = ld_acquire(&order[t / UB]);
-            return v ? v - 1u : NONE;
-        };
-        auto claim_b = [&](bool& claimed) {
-            const u32 t = atomicAdd(&a.ctl[1], 1u);
-            if (t < totalB) {
-                const u32 limb = b_limb(t);
-                if (limb != NONE) load(KIND_B, limb, t % UB);
-                else held = t;
-                claimed = true;
-            } else {
-                b_left = false;
+        // Claim the next unit.  (1) A ticket of the latest phase whose limb is
+        // published, taken by compare-and-swap so that the ticket taken is the
+        // one checked (later phases first: limbs finish, and their data leaves
+        // L2, before new limbs start).  (2) A ticket of phase 0, which never
+        // waits.  (3) Once every ticket of the phases below p has been taken,
+        // a ticket of phase p, held until its limb is published: the tiles it
+        // waits for are then all claimed by CTAs that do not wait for it, so
+        // holding cannot deadlock.
+        auto claim = [&]() -> bool {
+            for (u32 p = NP - 1; p >= 1; --p) {
+                if (!((left >> p) & 1u)) continue;
+                const u32 tot = a.limbs * units(p);
+                const u32 t = ld_relaxed(&ctl[p]);
+                if (t >= tot) {
+                    left &= ~(1u << p);
+                    continue;
+                }
+                const u32 limb = pub_limb(p - 1, t / units(p));
+                if (limb != NONE && atomicCAS(&ctl[p], t, t + 1u) == t) {
+                    load(p, limb, t % units(p));
+                    return true;
+                }
             }
+            if (left & 1u) {
+                const u32 t = atomicAdd(&ctl[0], 1u);
+                if (t < a.limbs * units(0)) {
+                    load(0, t / units(0), t % units(0));
+                    return true;
+                }
+                left &= ~1u;
+            }
+            for (u32 p = 1; p < NP; ++p) {
+                if (left & ((1u << p) - 1u)) break;        // a lower phase may still have tickets
+                if (!((left >> p) & 1u)) continue;
+                const u32 t = atomicAdd(&ctl[p], 1u);
+                if (t >= a.limbs * units(p)) {
+                    left &= ~(1u << p);
+                    continue;
+                }
+                const u32 limb = pub_limb(p - 1, t / units(p));
+                if (limb != NONE) {
+                    load(p, limb, t % units(p));
+                } else {
+                    held = t;
+                    held_p = p;
+                }
+                return true;
+            }
+            return false;
         };
 
         for (u32 j = 0; j < a.njobs && j < (u32)MAXJ; ++j) {
@@ -409,7 +488,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                     tma_store_2d(&a.mapR[j], 0, (int)(local * (F::R1 * F::R2 / F::COLW) + tile * (F::TILE_R / F::COLW)),
                                  src);
                 bulk_commit();
-                const u32 e = kind == KIND_A ? (0x80000000u | limb) : 0u;
+                const u32 e = kind + 1u < NP ? ((kind + 1u) << 28) | limb : 0u;
                 if (qn == 0) q0 = e;
                 else if (qn == 1) q1 = e;
                 else q2 = e;
@@ -423,33 +502,15 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             } else if (issued - stored < 2u) {
                 // nothing but the unit in compute is pending: pick the next unit
                 if (held != NONE) {
-                    const u32 limb = b_limb(held);
+                    const u32 limb = pub_limb(held_p - 1, held / units(held_p));
                     if (limb != NONE) {
-                        load(KIND_B, limb, held % UB);
+                        load(held_p, limb, held % units(held_p));
                         held = NONE;
                         progress = true;
                     }
                 } else {
-                    bool claimed = false;
-                    if (b_left && a_left) {
-                        // A queue a_window limbs ahead: prefer a published B tile
-                        const u32 peek = ld_relaxed(&a.ctl[1]);
-                        if (peek >= totalB) b_left = false;
-                        else if (ld_relaxed(&a.ctl[0]) / UA >= peek / UB + a.a_window && b_limb(peek) != NONE)
-                            claim_b(claimed);
-                    }
-                    if (!claimed && a_left) {
-                        const u32 t = atomicAdd(&a.ctl[0], 1u);
-                        if (t < totalA) {
-                            load(KIND_A, t / UA, t % UA);
-                            claimed = true;
-                        } else {
-                            a_left = false;
-                        }
-                    }
-                    if (!claimed && b_left) claim_b(claimed);
-                    if (claimed) progress = true;
-                    if (!a_left && !b_left && held == NONE) {
+                    if (claim()) progress = true;
+                    if (left == 0 && held == NONE) {
                         // no work left: a stop descriptor in the next buffer
                         const int b = (int)(issued % NBUF);
                         buf_desc(b)->kind = KIND_STOP;
@@ -497,8 +558,9 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
         }
         // the last CTA to finish zeroes the work area for the next launch
         __threadfence();
-        if (atomicAdd(&a.ctl[2], 1u) == gridDim.x - 1) {
-            for (u32 i = 0; i < 2 * a.limbs + 4; ++i) a.ctl[i] = 0u;
+        if (atomicAdd(&ctl[2 * NP - 1], 1u) == gridDim.x - 1) {
+            const size_t words = fused_ctl_words(NP, a.limbs);
+            for (size_t i = 0; i < words; ++i) ctl[i] = 0u;
             __threadfence();
         }
         return;
@@ -521,18 +583,18 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
         W* sm = buf_tile(b);
         const PrimeT& pr = *buf_pr(b);
         if (is_col(kind)) {
-            // column pass: twiddles Psi[0, R1) staged with the tile
-            if constexpr (FWD)
+            // column pass: twiddles Psi[0, R1) staged with the tile; the
+            // forward's first pass, or the inverse's last (canonical output)
+            if (is_fwd(kind))
                 compute_tile<P1, F::LOGC_COL, KMAX, false, true, 1, false, true, 0, true, NT, NoHook, true>(
                     sm, pr, buf_tw(b), nullptr, nullptr, 0u, 0u, tid);
             else
-                compute_tile<P1, F::LOGC_COL, KMAX, false, false, X_B, true, true, 0, true, NT, NoHook, true>(
+                compute_tile<P1, F::LOGC_COL, KMAX, false, false, X_CI, true, true, 0, true, NT, NoHook, true>(
                     sm, pr, buf_tw(b), nullptr, nullptr, 0u, 0u, tid);
         } else {
+            // row pass: the forward's last (canonical output), or the inverse's first
+            const bool fwd = is_fwd(kind);
             const FusedJobT<W>& J = a.job[MAXJ > 1 ? buf_desc(b)->job : 0u];
-            const TwT* tw = J.tw + (size_t)pi * J.tw_len;
-            const TwT* ota = J.ota ? J.ota + (size_t)pi * F::R2 : nullptr;
-            const TwT* otb = J.otb ? J.otb + (size_t)pi * ((size_t)P2 << P1) : nullptr;
             if constexpr (MULB && !FWD && sizeof(W) == 8) {
                 // fused element-wise product (Sec. III-A): the tile of the first
                 // factor's transform times the second's, canonical, before the
@@ -560,8 +622,8 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                 };
                 auto ha = [&]() { mbar_arrive(htw_empty); };
                 const TwT* tw0 = STAGE == 1 ? buf_tw(b) : htw;
-                if constexpr (FWD)
-                    compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true, false, W,
+                if (fwd)
+                    compute_tile<P2, LOGC_R, KMAX, true, true, X_RF, true, false, OTS, false, NT, NoHook, true, false, W,
                                  STAGE, F::ROW_WARPX>(sm, pr, tw0, nullptr, nullptr, tile * F::CR, (u32)P1, tid,
                                                       NoHook(), htw, hw, ha);
                 else
@@ -570,8 +632,13 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
                                                       NoHook(), htw, hw, ha);
                 ++rt;
             } else {
-                if constexpr (FWD)
-                    compute_tile<P2, LOGC_R, KMAX, true, true, X_B, true, false, OTS, false, NT, NoHook, true>(
+                const TwT* tw = J.tw + (size_t)pi * J.tw_len;
+                const TwT* ota_t = CHAIN && !fwd ? J.ota_inv : J.ota;
+                const TwT* otb_t = CHAIN && !fwd ? J.otb_inv : J.otb;
+                const TwT* ota = ota_t ? ota_t + (size_t)pi * F::R2 : nullptr;
+                const TwT* otb = otb_t ? otb_t + (size_t)pi * ((size_t)P2 << P1) : nullptr;
+                if (fwd)
+                    compute_tile<P2, LOGC_R, KMAX, true, true, X_RF, true, false, OTS, false, NT, NoHook, true>(
                         sm, pr, tw, ota, otb, tile * F::CR, (u32)P1, tid);
                 else
                     compute_tile<P2, LOGC_R, KMAX, true, false, 1, false, false, OTS, false, NT, NoHook, true,

@@ -43,9 +43,13 @@ constexpr Geometry geometry_of(int n, int g) { return kGeometryTable[n - 13][g];
 #define NTT_KMAX 4      // stages per thread per round (per-thread radix 2^NTT_KMAX)
 #endif
 constexpr int KMAX_ALL = NTT_KMAX;
-// 32-bit words of the fused kernel's work area for `limbs` limbs: four
-// counters, a published-tile count per limb and the publication order.
+// 32-bit words of the fused kernel's work area for `limbs` limbs of one
+// transform: four counters, a published-tile count per limb and the
+// publication order.  A forward + inverse launch over `limbs` limbs needs
+// the area of chain_work_limbs(limbs) limbs (four phases: eight counters and
+// three of each per-limb array).
 constexpr size_t fused_work_words(size_t limbs) { return 4 + 2 * limbs; }
+constexpr size_t chain_work_limbs(size_t limbs) { return 3 * limbs + 2; }
 
 struct StageSlot {
     int sl, K0, k;
@@ -95,6 +99,9 @@ struct LaunchCtx {
     // inverse through the fused kernel only: the other factor of an
     // element-wise product that the first pass applies (see JobCtx::mulb)
     const u64* mulb = nullptr;
+    // fused two-pass plans, with fwd: the forward and then the inverse
+    // transform in one launch (work area of chain_work_limbs(limbs) limbs)
+    u32 chain = 0;
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
@@ -134,6 +141,7 @@ struct JobsCtx {
     const void* l2_base = nullptr;   // L2 access-policy window (l2_bytes 0: none)
     size_t l2_bytes = 0;
     float l2_hit = 0.f;
+    u32 chain = 0;                   // one job: forward, then inverse, in one launch
 };
 cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
 cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a, const u64* b,

@@ -1,40 +1,47 @@
 """The fused kernel's scheduling protocol, simulated on the CPU.
 
-Each CTA of ntt_fused_kernel has compute warps (a consumer of a ring of three
-tile buffers) and one producer thread (an event loop that claims units from
-two queues, at most one ahead of the unit in compute, loads tiles, stores
-computed tiles and publishes first-pass tiles on per-limb counters; the
-producer whose tile completes a limb appends the limb to the publication
-order, and second-pass tickets map to limbs in that order).  Here both sides of every CTA are generators mirroring
-that control flow; a random scheduler interleaves them and completes the
-asynchronous copies after random delays.  Checked for many seeds and shapes:
-  * a second-pass tile is loaded only after every first-pass tile of its limb
-    has been stored completely;
+Each CTA of ntt_fused_kernel has compute warps (a consumer of a ring of tile
+buffers) and one producer thread (an event loop that claims units from one
+queue per phase, at most one ahead of the unit in compute, loads tiles,
+stores computed tiles and publishes the tiles of every phase but the last on
+per-limb counters; the producer whose tile completes a limb appends the limb
+to that phase's publication order, and the next phase's tickets map to limbs
+in that order).  A launch has two phases (one transform: column then row
+pass, or row then column) or four (forward then inverse).  Claims: a
+published ticket of the latest phase by compare-and-swap, else a phase-0
+ticket, else, once every ticket of the phases below p is taken, a phase-p
+ticket held until its limb is published.  With staged row twiddles, each
+CTA's producer copies a row tile's later-round twiddles into one per-CTA
+buffer once the previous row tile has released it, and the compute warps
+wait for that copy before reading it.
+
+Here both sides of every CTA are generators mirroring that control flow; a
+random scheduler interleaves them and completes the asynchronous copies
+after random delays.  Checked for many seeds and shapes:
+  * a tile of phase p > 0 is loaded only after every tile of phase p - 1 of
+    its limb has been stored completely;
   * a buffer is refilled only after the store that last used it has read it;
   * a limb counter is raised only for stores that completed;
-  * every unit is computed exactly once, the run finishes (no deadlock), and
-    every CTA reaches the finished count;
-for B-first ordering (window 0), a small look-ahead window and A-first.
+  * the staged-twiddle buffer is refilled only after the previous row tile
+    released it, and read only after its copy landed, in row-tile order;
+  * every tile of every phase is computed exactly once, the run finishes (no
+    deadlock), and every CTA reaches the finished count.
 """
 import random
 
 import pytest
 
-import kernel_model as KM
-
-NBUF = 3
-
 
 class Sim:
-    def __init__(self, limbs, UA, UB, rng):
-        self.limbs, self.UA, self.UB = limbs, UA, UB
-        self.totalA, self.totalB = limbs * UA, limbs * UB
-        self.ctl = [0, 0, 0]            # next A ticket, next B ticket, CTAs finished
-        self.done = [0] * limbs
-        self.order = []                 # published limbs, in publication order
-        self.a_stored = [set() for _ in range(limbs)]
-        self.computedA = [0] * self.totalA
-        self.computedB = [0] * self.totalB
+    def __init__(self, limbs, units, rows, rng):
+        self.limbs, self.units, self.rows = limbs, units, rows      # units[p]; rows[p]: row-tile phase
+        self.NP = len(units)
+        self.tickets = [0] * self.NP
+        self.done = [[0] * limbs for _ in range(self.NP)]
+        self.order = [[] for _ in range(self.NP)]                  # published limbs per phase
+        self.stored = [[set() for _ in range(limbs)] for _ in range(self.NP)]
+        self.computed = [[[0] * units[p] for _ in range(limbs)] for p in range(self.NP)]
+        self.finished = 0
         self.rng = rng
         self.now = 0
         self.events = []
@@ -44,25 +51,29 @@ class Sim:
 
 
 class Cta:
-    def __init__(self, sim, peek=True, window=0):
+    def __init__(self, sim, nbuf, stage):
         self.s = sim
-        self.peek = peek
-        self.window = window
-        self.full = [0] * NBUF          # completed phases per buffer
-        self.empty = [0] * NBUF
-        self.desc = [None] * NBUF
+        self.NBUF = nbuf
+        self.stage = stage
+        self.full = [0] * nbuf          # completed phases per buffer
+        self.empty = [0] * nbuf
+        self.desc = [None] * nbuf
         self.stores = []                # committed stores in order
         self.bufstore = {}
+        self.htw_full = 0               # staged-twiddle copies landed
+        self.htw_empty = 0              # row tiles that released the buffer
+        self.htw_tile = []              # (phase, limb, tile) of each fill, in order
 
     # async copies ------------------------------------------------------
-    def load(self, kind, limb, tile, t, issued):
+    def load(self, p, limb, tile, issued):
         s = self.s
-        b = issued % NBUF
-        if kind == "B":
-            assert len(s.a_stored[limb]) == s.UA, "B tile loaded before its limb's A tiles were stored"
+        b = issued % self.NBUF
+        if p > 0:
+            assert len(s.stored[p - 1][limb]) == s.units[p - 1], \
+                "tile loaded before every tile of the previous phase of its limb was stored"
         st = self.bufstore.get(b)
         assert st is None or st["read"], "buffer refilled before its store read it"
-        self.desc[b] = (kind, limb, tile, t)
+        self.desc[b] = (p, limb, tile)
 
         def fin():
             self.full[b] += 1
@@ -70,7 +81,7 @@ class Cta:
 
     def store(self, b):
         s = self.s
-        kind, limb, tile, t = self.desc[b]
+        p, limb, tile = self.desc[b]
         st = {"read": False, "done": False}
 
         def rd():
@@ -78,8 +89,7 @@ class Cta:
 
         def fin():
             st["done"] = True
-            if kind == "A":
-                s.a_stored[limb].add(tile)
+            s.stored[p][limb].add(tile)
         s.later(rd, 1, 10)
         s.later(fin, 11, 60)
         self.stores.append(st)
@@ -89,17 +99,21 @@ class Cta:
     # producer ------------------------------------------------------------
     def producer(self):
         s = self.s
+        NP, NBUF = s.NP, self.NBUF
         issued = stored = 0
-        fifo = []                       # (store, limb or None)
-        a_left = b_left = True
+        fifo = []                       # (store, (phase, limb) or None)
+        left = (1 << NP) - 1
         stopped = False
-        held = None
+        held = None                     # (phase, ticket)
+        hq = []                         # row units loaded, staged twiddles not yet copied
+        fills = 0
 
-        def publish(limb):
-            if limb is not None:
-                s.done[limb] += 1
-                if s.done[limb] == s.UA:
-                    s.order.append(limb)
+        def publish(e):
+            if e is not None:
+                p, limb = e
+                s.done[p][limb] += 1
+                if s.done[p][limb] == s.units[p]:
+                    s.order[p].append(limb)
 
         def wait_all_but(n):
             while not all(x["done"] for x in (self.stores[:-n] if n else self.stores)):
@@ -109,41 +123,98 @@ class Cta:
             nonlocal fifo
             if len(fifo) >= 2:
                 yield from wait_all_but(1)
-                for st, limb in fifo[:-1]:
+                for st, e in fifo[:-1]:
                     assert st["done"], "limb counter raised before the store completed"
-                    publish(limb)
+                    publish(e)
                 fifo = fifo[-1:]
 
         def publish_all():
             nonlocal fifo
             if fifo:
                 yield from wait_all_but(0)
-                for st, limb in fifo:
+                for st, e in fifo:
                     assert st["done"]
-                    publish(limb)
+                    publish(e)
                 fifo = []
 
         def wait_read_all():
             while not all(x["read"] for x in self.stores):
                 yield
 
-        def b_limb(t):
-            pos = t // s.UB
-            return s.order[pos] if pos < len(s.order) else None
+        def pub_limb(p, i):
+            return s.order[p][i] if i < len(s.order[p]) else None
 
-        def do_load(kind, limb, tile, t):
+        def do_load(p, limb, tile):
             nonlocal issued
             yield from wait_read_all()
-            self.load(kind, limb, tile, t, issued)
+            self.load(p, limb, tile, issued)
+            if self.stage and s.rows[p]:
+                hq.append(issued)
             issued += 1
 
+        def fill_htw():
+            nonlocal fills
+            if not self.stage or not hq:
+                return False
+            if fills and self.htw_empty < fills:
+                return False
+            assert self.htw_empty == fills, "staged twiddles copied before the previous row tile released them"
+            u = hq.pop(0)
+            self.htw_tile.append(self.desc[u % NBUF])
+
+            def fin():
+                self.htw_full += 1
+            s.later(fin)
+            fills += 1
+            return True
+
+        def claim():
+            nonlocal left, held
+            for p in range(NP - 1, 0, -1):
+                if not (left >> p) & 1:
+                    continue
+                tot = s.limbs * s.units[p]
+                t = s.tickets[p]
+                if t >= tot:
+                    left &= ~(1 << p)
+                    continue
+                limb = pub_limb(p - 1, t // s.units[p])
+                if limb is not None and s.tickets[p] == t:       # compare-and-swap
+                    s.tickets[p] = t + 1
+                    yield from do_load(p, limb, t % s.units[p])
+                    return True
+            if left & 1:
+                t = s.tickets[0]
+                s.tickets[0] += 1
+                if t < s.limbs * s.units[0]:
+                    yield from do_load(0, t // s.units[0], t % s.units[0])
+                    return True
+                left &= ~1
+            for p in range(1, NP):
+                if left & ((1 << p) - 1):
+                    break
+                if not (left >> p) & 1:
+                    continue
+                t = s.tickets[p]
+                s.tickets[p] += 1
+                if t >= s.limbs * s.units[p]:
+                    left &= ~(1 << p)
+                    continue
+                limb = pub_limb(p - 1, t // s.units[p])
+                if limb is not None:
+                    yield from do_load(p, limb, t % s.units[p])
+                else:
+                    held = (p, t)
+                return True
+            return False
+
         while True:
-            progress = False
+            progress = fill_htw()
             while stored < issued and self.empty[stored % NBUF] > stored // NBUF:
                 b = stored % NBUF
-                kind, limb, tile, t = self.desc[b]
+                p, limb, tile = self.desc[b]
                 st = self.store(b)
-                fifo.append((st, limb if kind == "A" else None))
+                fifo.append((st, (p, limb) if p + 1 < NP else None))
                 stored += 1
                 yield from publish_older()
                 progress = True
@@ -152,51 +223,18 @@ class Cta:
                     break
             elif issued - stored < 2:
                 if held is not None:
-                    if b_limb(held) is not None:
-                        yield from do_load("B", b_limb(held), held % s.UB, held)
+                    p, t = held
+                    limb = pub_limb(p - 1, t // s.units[p])
+                    if limb is not None:
+                        yield from do_load(p, limb, t % s.units[p])
                         held = None
                         progress = True
                 else:
-                    claimed = False
-                    if b_left and a_left and self.peek:
-                        pk = s.ctl[1]
-                        if pk >= s.totalB:
-                            b_left = False
-                        elif s.ctl[0] // s.UA >= pk // s.UB + self.window and b_limb(pk) is not None:
-                            t = s.ctl[1]
-                            s.ctl[1] += 1
-                            if t < s.totalB:
-                                if b_limb(t) is not None:
-                                    yield from do_load("B", b_limb(t), t % s.UB, t)
-                                else:
-                                    held = t
-                                claimed = True
-                            else:
-                                b_left = False
-                    if not claimed and a_left:
-                        t = s.ctl[0]
-                        s.ctl[0] += 1
-                        if t < s.totalA:
-                            yield from do_load("A", t // s.UA, t % s.UA, t)
-                            claimed = True
-                        else:
-                            a_left = False
-                    if not claimed and b_left:
-                        t = s.ctl[1]
-                        s.ctl[1] += 1
-                        if t < s.totalB:
-                            if b_limb(t) is not None:
-                                yield from do_load("B", b_limb(t), t % s.UB, t)
-                            else:
-                                held = t
-                            claimed = True
-                        else:
-                            b_left = False
-                    if claimed:
+                    if (yield from claim()):
                         progress = True
-                    if not a_left and not b_left and held is None:
+                    if left == 0 and held is None:
                         b = issued % NBUF
-                        self.desc[b] = ("STOP", 0, 0, 0)
+                        self.desc[b] = ("STOP", 0, 0)
                         self.full[b] += 1
                         issued += 1
                         stopped = True
@@ -207,35 +245,40 @@ class Cta:
             yield from publish_all()
             yield
         yield from publish_all()
-        s.ctl[2] += 1
+        s.finished += 1
 
     # compute warps ----------------------------------------------------------
     def compute(self):
         s = self.s
-        k = 0
+        NBUF = self.NBUF
+        k = rt = 0
         while True:
             b = k % NBUF
             while self.full[b] <= k // NBUF:
                 yield
-            kind, limb, tile, t = self.desc[b]
-            if kind == "STOP":
+            p, limb, tile = self.desc[b]
+            if p == "STOP":
                 return
+            if self.stage and s.rows[p]:
+                while self.htw_full <= rt:
+                    yield
+                assert self.htw_tile[rt] == (p, limb, tile), "staged twiddles of another row tile"
             for _ in range(s.rng.randint(1, 6)):
                 yield
-            if kind == "A":
-                s.computedA[t] += 1
-            else:
-                s.computedB[limb * s.UB + tile] += 1     # every (limb, tile), not every ticket
+            if self.stage and s.rows[p]:
+                self.htw_empty += 1
+                rt += 1
+            s.computed[p][limb][tile] += 1
             self.empty[b] += 1
             k += 1
 
 
-def simulate(limbs, UA, UB, ctas, seed, peek=True, window=0, max_steps=3_000_000):
+def simulate(limbs, units, rows, ctas, seed, nbuf, stage, max_steps=4_000_000):
     rng = random.Random(seed)
-    sim = Sim(limbs, UA, UB, rng)
+    sim = Sim(limbs, units, rows, rng)
     gens = []
     for _ in range(ctas):
-        c = Cta(sim, peek, window)
+        c = Cta(sim, nbuf, stage)
         gens += [c.producer(), c.compute()]
     alive = list(range(len(gens)))
     steps = 0
@@ -254,24 +297,30 @@ def simulate(limbs, UA, UB, ctas, seed, peek=True, window=0, max_steps=3_000_000
             alive.remove(i)
     for _, fn in sorted(sim.events, key=lambda e: e[0]):
         fn()
-    assert all(c == 1 for c in sim.computedA) and all(c == 1 for c in sim.computedB)
-    assert sim.done == [UA] * limbs
-    assert sorted(sim.order) == list(range(limbs))
-    assert sim.ctl[2] == ctas
+    for p in range(sim.NP):
+        assert all(c == 1 for row in sim.computed[p] for c in row), f"phase {p}: a tile computed twice or never"
+    for p in range(sim.NP - 1):
+        assert sim.done[p] == [units[p]] * limbs
+        assert sorted(sim.order[p]) == list(range(limbs))
+    assert sim.finished == ctas
 
 
-@pytest.mark.parametrize("limbs,UA,UB,ctas", [(6, 8, 2, 60), (3, 16, 16, 96), (45, 16, 16, 40),
-                                               (45, 16, 16, 304), (1, 4, 4, 8), (20, 2, 8, 7),
-                                               (120, 32, 32, 64)])
-@pytest.mark.parametrize("seed", range(3))
-@pytest.mark.parametrize("peek,window", [(True, 0), (False, 0), (True, 2), (True, 1 << 24)])
-def test_protocol_random_interleavings(limbs, UA, UB, ctas, seed, peek, window):
-    simulate(limbs, UA, UB, ctas, seed, peek, window)
+# (units per phase, row-tile phases): forward (column, row), inverse (row,
+# column), forward then inverse (column, row, row, column)
+SHAPES = {"fwd": ((16, 16), (False, True)), "inv": ((16, 16), (True, False)),
+          "chain": ((16, 16, 16, 16), (False, True, True, False)),
+          "fwd_uneven": ((8, 32), (False, True)), "chain_uneven": ((8, 4, 4, 8), (False, True, True, False))}
 
 
-@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
-def test_fused_tile_counts_cover_limb(n):
-    UC, UR = KM.fused_geometry(n)
-    p1, p2 = KM.split(n)
-    assert UC * 16 * (1 << p1) == 1 << n          # column tiles: 16 columns x R1 rows
-    assert UR * (1 << KM.logc_rows(p2)) * (1 << p2) == 1 << n
+@pytest.mark.parametrize("shape", sorted(SHAPES))
+@pytest.mark.parametrize("nbuf,stage", [(3, False), (2, True)])
+@pytest.mark.parametrize("limbs,ctas", [(1, 1), (1, 7), (3, 2), (6, 9), (12, 24)])
+def test_protocol(shape, nbuf, stage, limbs, ctas):
+    units, rows = SHAPES[shape]
+    for seed in range(3):
+        simulate(limbs, units, rows, ctas, seed * 7919 + limbs * 31 + ctas, nbuf, stage)
+
+
+def test_protocol_many_ctas_few_limbs():
+    """More CTAs than tiles of a phase: most producers hold tickets."""
+    simulate(2, (4, 4, 4, 4), (False, True, True, False), 40, 5, 2, True)

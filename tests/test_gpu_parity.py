@@ -513,3 +513,79 @@ def test_monomial_product_is_signed_shift_full_size(shape):
             torch.cuda.synchronize()
             assert np.array_equal(host(dc)[0], want), f"k={k}"
         assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("n", [13, 14, 15, 16, 17])
+@pytest.mark.parametrize("mode,ots", [(G.NTT_TWIDDLE_TABLE, 0), (G.NTT_TWIDDLE_OT, 1), (G.NTT_TWIDDLE_OT, 2)])
+def test_execute_forward_then_inverse_one_launch(orc, n, mode, ots):
+    """ntt_execute with both operations (one chained launch for fused plans):
+    the round trip restores the input, and each single operation through the
+    same call equals the oracle."""
+    N = 1 << n
+    L = 3 if n < 17 else 2
+    primes = I.prime_chain(L, 2 * N)
+    data = I.batch_uniform(40 + n, 2, primes, N)
+    both = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+    with G.Plan(N, primes, mode, ots) as p:
+        d = dev(data)
+        p.execute(d, both, 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), data)
+        p.execute(d, G.NTT_OP_FORWARD, 2)
+        torch.cuda.synchronize()
+        want = oracle_fwd(orc, data, primes)
+        assert np.array_equal(host(d).reshape(data.shape), want)
+        # the inverse through the call, on forward output and on arbitrary NTT-domain input
+        p.execute(d, G.NTT_OP_INVERSE, 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), data)
+        d = dev(data)
+        p.execute(d, G.NTT_OP_INVERSE, 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), oracle_inv(orc, data, primes))
+        assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("geometry", [G.NTT_GEOMETRY_DEFAULT, G.NTT_GEOMETRY_SMALL_ROW_TILE, G.NTT_GEOMETRY_ALT_SPLIT])
+@pytest.mark.parametrize("n", [16, 17])
+def test_execute_chain_many_limbs_every_geometry(n, geometry):
+    """The chained launch at the C2 / C3 shapes in every geometry, with
+    queued calls and no synchronisation between them: equal to separate
+    forward and inverse calls on the same data (a forward, then a chained
+    call, then an inverse, leaves the forward's result of the input)."""
+    N = 1 << n
+    L = 45 if n == 16 else 60
+    primes = I.prime_chain(L, 2 * N)
+    data = I.batch_uniform(70 + n, 2 if n == 17 else 1, primes, N)
+    b = data.shape[0]
+    both = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+    with G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_FUSED, geometry) as p:
+        d = dev(data)
+        ref = dev(data)
+        for _ in range(3):
+            p.execute(d, both, b)
+        p.forward(ref, b)
+        p.execute(d, G.NTT_OP_FORWARD, b)
+        p.execute(d, both, b)
+        p.execute(ref, both, b)
+        torch.cuda.synchronize()
+        assert torch.equal(d, ref)
+        p.inverse(d, b)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), data)
+        assert p.device_status() == 0
+
+
+@pytest.mark.parametrize("kernel", [G.NTT_KERNEL_PER_PASS, G.NTT_KERNEL_RADIX2])
+def test_execute_other_organisations(kernel):
+    """Plans that do not chain run the two operations as two calls."""
+    N = 1 << 14
+    primes = I.prime_chain(2, 2 * N)
+    data = I.batch_uniform(90, 1, primes, N)
+    with G.Plan(N, primes, G.NTT_TWIDDLE_TABLE, 0, kernel) as p:
+        d = dev(data)
+        p.execute(d, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE, 1)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), data)
+        with pytest.raises(G.NttError):
+            p.execute(d, 4, 1)
