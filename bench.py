@@ -66,6 +66,17 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--launch-steps", type=int, default=500,
                     help="steps of the single-stream pass that times each launch")
+    ap.add_argument("--l2-twiddles", action="store_true",
+                    help="plans with NTT_PLAN_L2_TWIDDLES (twiddle tables kept in L2 by a persisting window)")
+    ap.add_argument("--traffic-json", default=None,
+                    help="write the DRAM-traffic summary of the C2 kernels from ncu CSV files (--traffic-csv) "
+                         "to this JSON file and exit")
+    ap.add_argument("--traffic-csv", nargs="*", default=[],
+                    help="ncu --csv logs of dram__bytes_read.sum, dram__bytes_write.sum, gpu__time_duration.sum")
+    ap.add_argument("--traffic-command", default="",
+                    help="the command line that produced the CSV files (recorded in the JSON)")
+    ap.add_argument("--int8-probe", action="store_true",
+                    help="time the library int8 GEMM (torch._int_mm) against bf16 and print it (tensor-core check)")
     ap.add_argument("--split-calls", action="store_true",
                     help="each step as two calls (ntt_forward, ntt_inverse) instead of one ntt_execute")
     return ap.parse_args()
@@ -79,7 +90,7 @@ def dist_env():
 
 
 KERNEL_SOURCES = ("arith.cuh", "device_types.cuh", "ntt_pass.cuh", "tma.cuh", "ntt_fused.cuh",
-                  "launch.cuh", "fused_host.cu", "plan.h", "k_n16.cu")
+                  "launch.cuh", "k_n16.cu")
 
 
 def max_over_ranks(value: float, dist, device) -> float:
@@ -130,6 +141,88 @@ def profile_traffic(geometry: int, twiddle: str, direction: str):
                 (geometry, twiddle, direction, h):
             return e
     return None
+
+
+def int8_probe(torch):
+    """Dense int8 GEMM rate of the library path (torch._int_mm, cuBLASLt)
+    against bf16 (torch.matmul) on square-ish shapes: whether an exact
+    integer tensor-core pass could pay on this GPU."""
+    out = {"unit": "TOPS (int8) / TFLOP/s (bf16)", "shapes": []}
+    for m, k, n in ((8192, 8192, 8192), (16384, 8192, 8192)):
+        a8 = torch.randint(-128, 127, (m, k), dtype=torch.int8, device="cuda")
+        b8 = torch.randint(-128, 127, (k, n), dtype=torch.int8, device="cuda")
+        ab = a8.to(torch.bfloat16)
+        bb = b8.to(torch.bfloat16)
+        res = {"m": m, "k": k, "n": n}
+        for name, fn in (("int8", lambda: torch._int_mm(a8, b8)), ("bf16", lambda: ab @ bb)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 20
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = 2.0 * m * k * n * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+        out["shapes"].append(res)
+    return out
+
+
+def write_traffic_json(out, csvs, command):
+    """Mean DRAM traffic per launch of each C2 fused kernel in ncu CSV logs
+    (steady-state launches taken with --cache-control none, so a launch's
+    writes include the write-back of dirty lines it evicts), keyed by
+    geometry, twiddle supply, direction and the current kernel source hash."""
+    import csv as _csv
+    import re
+    N, L = 1 << 16, 45
+    geoms = {(8, 4): 0, (8, 3): 1, (7, 3): 2}
+    per = {}
+    for path in csvs:
+        hdr = None
+        for r in _csv.reader(open(path)):
+            if r and r[0] == "ID":
+                hdr = r
+                continue
+            if not hdr or len(r) != len(hdr):
+                continue
+            d = dict(zip(hdr, r))
+            name = d["Kernel Name"]
+            if "ntt_fused_kernel" not in name:
+                continue
+            args = [x.strip() for x in re.search(r"ntt_fused_kernel<([^>]*)>", name).group(1).split(",")]
+            p1, p2, lc, fwd, ots = int(args[0]), int(args[1]), int(args[2]), int(args[4]), int(args[5])
+            chain = len(args) >= 10 and int(args[9]) == 1
+            if p1 + p2 != 16:
+                continue
+            key = (geoms.get((p1, lc), -1), "table" if ots == 0 else f"ot{ots}",
+                   "forward+inverse" if chain else ("forward" if fwd else "inverse"))
+            v = float(d["Metric Value"].replace(",", ""))
+            e = per.setdefault(key, {"kernel": name.split("(")[0].replace("void ", ""), "read": [], "write": [], "t": []})
+            e[{"dram__bytes_read.sum": "read", "dram__bytes_write.sum": "write",
+               "gpu__time_duration.sum": "t"}[d["Metric Name"]]].append(v)
+    entries = []
+    h = kernel_source_hash()
+    for (g, tw, direction), e in sorted(per.items()):
+        rd, wr = float(np.mean(e["read"])), float(np.mean(e["write"]))
+        transforms = 2 if direction == "forward+inverse" else 1
+        data = 8 * N * L                    # one read of the array
+        entries.append({"kernel": e["kernel"], "geometry": g, "twiddle": tw, "direction": direction,
+                        "source_hash": h, "launches": len(e["read"]),
+                        "dram_read_bytes": rd, "dram_write_bytes": wr, "dram_bytes": rd + wr,
+                        "alg_bytes": 16 * N * L * transforms,
+                        "data_read_bytes": min(rd, data), "twiddle_read_bytes": max(0.0, rd - data),
+                        "duration_us_mean_under_ncu": float(np.mean(e["t"])) / 1e3,
+                        "how": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                               "--cache-control none on steady-state launches of the bench's timed loop; writes "
+                               "include write-back of lines evicted during the launch; data_read_bytes = one read "
+                               "of the array (8 N L), the rest of the reads counted as twiddle reads"})
+    with open(out, "w") as f:
+        json.dump({"workload": "c2_n65536_l45", "command": command, "entries": entries}, f, indent=1)
+        f.write("\n")
+    print(json.dumps({"traffic_json": out, "entries": len(entries)}))
 
 
 class ClockSampler:
@@ -777,7 +870,8 @@ def config_dict(w, args, ws):
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
             "twiddle": args.twiddle, "parallelism": f"replicas{ws}",
             "streams": args.streams,
-            "overlap": "step i runs on stream i mod streams with its own plan; steps are independent polynomials",
+            "overlap": "step i runs on stream i mod streams with its own plan (clones sharing one set of tables); "
+                       "steps are independent polynomials",
             "l2": "inputs rotate over buffers totalling > 2x L2 (129 MB)"}
 
 
@@ -789,6 +883,9 @@ def main():
     metric = "limb-NTT/s, N=2^16 L=45 forward+inverse (bit-exact)"
     unit = "limb-NTT/s"
     w = I.workload_c2()
+    if args.traffic_json:
+        write_traffic_json(args.traffic_json, args.traffic_csv, args.traffic_command)
+        return
     if args.impl == "reference":
         run_reference(args, metric, unit, w)
         return
@@ -806,6 +903,12 @@ def main():
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
     G.lib()
+    if args.int8_probe:
+        if rank == 0:
+            print(json.dumps({"int8_probe": int8_probe(torch)}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.ablation_only or args.word_size_only:
         if rank == 0:
             if args.ablation_only:
@@ -826,11 +929,14 @@ def main():
     # one plan (tables + work area) per stream: steps on different streams are
     # independent polynomials and may overlap on the device
     c2_tune = None
+    l2f = G.NTT_PLAN_L2_TWIDDLES if args.l2_twiddles else 0
     if not args.no_tune and args.twiddle == "auto" and args.kernel == "auto":
         best, c2_tune = autotune(G, N, primes, 1, reps=20)
-        plans = [G.Plan.from_opts(N, primes, best) for _ in range(S)]
+        plans = [G.Plan.from_opts(N, primes, best, flags=l2f or None)]
     else:
-        plans = [G.Plan(N, primes, *mode, kern) for _ in range(S)]
+        plans = [G.Plan(N, primes, *mode, kern, flags=l2f)]
+    # the other streams' plans share the first plan's tables (ntt_plan_clone)
+    plans += [plans[0].clone() for _ in range(S - 1)]
     plan = plans[0]
     info = plan.info()
     poly_bytes = N * L * 8

@@ -138,6 +138,17 @@ ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t* primes, u
 void ntt_plan_destroy(ntt_plan* plan);
 
 /*
+ * A second plan for the same transform that shares `plan`'s device tables
+ * (twiddles, OT factors, prime constants: no new 16 N L bytes) but has its own
+ * work area, status word and staging, so that calls on the two plans may
+ * overlap in time (e.g. one plan per stream).  Sharing one table also keeps
+ * it in L2 for both.  The tables are freed with the last plan that shares
+ * them; the plans are destroyed independently.  Must run with the plan's
+ * device current.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_OOM, NTT_ERR_CUDA.
+ */
+ntt_status ntt_plan_clone(ntt_plan** out, const ntt_plan* plan);
+
+/*
  * In-place forward transform of `batch` polynomials at device address `data`
  * (layout [batch][L][N], 16-byte aligned, caller-owned).  Input in natural
  * coefficient order, output in bit-reversed order (Algorithm 1).  All
@@ -289,22 +300,33 @@ ntt_status ntt_transform_noalloc(const ntt_plan* plan, uint64_t* data, uint32_t 
  * at the different levels of an HE computation).
  *
  * A job transforms one array [batch][levels][N] of one plan in place, in one
- * direction.  ntt_batch_submit runs a list of jobs in few launches: jobs of
- * the same N >= 2^13, direction and OT setting (plans with the fused kernel)
- * share one launch of the fused two-pass kernel, up to 16 jobs per launch, and
- * these launches run concurrently on the batch object's internal streams,
- * forked from and joined back to `stream`; jobs of N <= 2^12 or of
- * NTT_KERNEL_PER_PASS plans are launched one by one on the same streams.  The
- * whole submission is ordered on `stream` like a single call.  Results equal
- * those of ntt_forward_levels / ntt_inverse_levels on each job.
+ * direction.  ntt_batch_submit runs a list of jobs in few launches:
+ *   - jobs of fused plans (N >= 2^13) with the default geometry go into one
+ *     launch per OT setting and 128 jobs, whatever their sizes and directions (a
+ *     persistent kernel in which each (size, direction) group runs its two
+ *     passes and CTAs move to another group when theirs has no work left);
+ *     with default plans a submission of any mix is one launch;
+ *   - jobs of fused plans with another geometry share launches of one size,
+ *     direction and OT setting, up to 16 jobs per launch;
+ *   - jobs of N <= 2^12 or of other kernel organisations run one by one.
+ * These launches run concurrently on the batch object's internal streams,
+ * forked from and joined back to `stream`; the whole submission is ordered
+ * on `stream` like a single call.  Results equal those of
+ * ntt_forward_levels / ntt_inverse_levels on each job.  The mixed launch's job
+ * descriptors (tensor maps and tables) are uploaded when they differ from the
+ * previous submission's; a submission repeated on the same arrays (or replayed
+ * from a captured graph) reuses them.
  *
  * Ownership and concurrency: the caller keeps its plans and arrays alive until
  * the work has finished; arrays of one submission must not overlap (rejected).
- * The batch object owns internal streams and a work area; calls on one batch
- * object must not overlap in time.  The work area grows when a submission
- * needs more (a device synchronisation and an allocation), so make one
- * submission of the largest shape before capturing submissions into a CUDA
- * graph.  Must run with the batch's device current.
+ * The batch object owns internal streams, a work area and the descriptor
+ * arrays; calls on one batch object must not overlap in time.  The work area
+ * grows when a submission needs more (a device synchronisation and an
+ * allocation), and a submission whose descriptors changed uploads them (it
+ * waits for the previous upload), so make one eager submission of the same
+ * jobs before capturing a submission into a CUDA graph, and submit no other
+ * jobs on that batch object while the graph is in use.  Must run with the
+ * batch's device current.
  */
 typedef struct ntt_batch ntt_batch;
 

@@ -133,6 +133,8 @@ def _lib():
             L.ntt_plan_create.argtypes = [ctypes.POINTER(_vp), _u32, _u64p, _u32, ctypes.POINTER(PlanOpts)]
             L.ntt_plan_destroy.restype = None
             L.ntt_plan_destroy.argtypes = [_vp]
+            L.ntt_plan_clone.restype = S
+            L.ntt_plan_clone.argtypes = [ctypes.POINTER(_vp), _vp]
             for f in ("ntt_forward", "ntt_inverse"):
                 getattr(L, f).restype = S
                 getattr(L, f).argtypes = [_vp, _vp, _u32, _vp]
@@ -481,6 +483,15 @@ class Plan:
         """A plan with the options an autotuner run returned (flags: override)."""
         return cls(N, primes, opts.twiddle_mode, opts.ot_stages, opts.kernel, opts.geometry,
                    opts.flags if flags is None else flags, opts.radix_log2)
+
+    def clone(self) -> "Plan":
+        """A plan sharing this one's device tables, with its own work area
+        (ntt_plan_clone): for calls that overlap on another stream."""
+        out = _vp()
+        _check(_lib().ntt_plan_clone(ctypes.byref(out), self.handle), "ntt_plan_clone")
+        c = object.__new__(type(self))
+        c.N, c.primes, c.L, c.handle = self.N, list(self.primes), self.L, out.value
+        return c
 
     def forward(self, data, batch: int = 1, stream=None):
         ntt_forward(self.handle, data, batch, stream)

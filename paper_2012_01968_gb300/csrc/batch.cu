@@ -7,6 +7,7 @@
 // the others.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -32,6 +33,12 @@ struct ntt_batch {
     size_t work_words = 0;
     uint32_t* d_status = nullptr;
     uint32_t test_stall_polls = 0;  // test hook: the next submission's fused launches stall (bounded)
+    // job descriptors of the mixed-size launches (device array and its
+    // page-locked host copy, equal at all times; both start zeroed)
+    void* d_mix = nullptr;
+    void* h_mix = nullptr;
+    size_t mix_cap = 0;             // jobs
+    uint32_t last_launches = 0;     // kernel launches of the latest submission
     std::mutex mu;
 };
 
@@ -47,6 +54,13 @@ ntt_status cuda_status(cudaError_t e)
 
 void release(ntt_batch* b)
 {
+    if (b->d_mix || b->h_mix) {
+        for (int k = 0; k < kStreams; ++k)
+            if (b->s[k]) cudaStreamSynchronize(b->s[k]);
+        cudaFree(b->d_mix);
+        cudaFreeHost(b->h_mix);
+        b->d_mix = b->h_mix = nullptr;
+    }
     for (int k = 0; k < kStreams; ++k) {
         if (b->s[k]) cudaStreamDestroy(b->s[k]);
         if (b->join[k]) cudaEventDestroy(b->join[k]);
@@ -90,6 +104,38 @@ cudaError_t grow_work(ntt_batch* b, size_t words, cudaStream_t caller)
     b->d_work = static_cast<uint32_t*>(mem);
     if (e == cudaSuccess) b->work_words = words;
     return e;
+}
+
+// Room for `jobs` mixed-launch descriptors (device and host copies, zeroed).
+// Growing drains the batch's streams first (an earlier launch may still read
+// the old arrays); not during graph capture.
+cudaError_t reserve_mix(ntt_batch* b, size_t jobs, cudaStream_t caller)
+{
+    if (jobs <= b->mix_cap) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(caller, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+    for (int k = 0; k < kStreams && e == cudaSuccess; ++k) e = cudaStreamSynchronize(b->s[k]);
+    if (e != cudaSuccess) return e;
+    cudaFree(b->d_mix);
+    cudaFreeHost(b->h_mix);
+    b->d_mix = b->h_mix = nullptr;
+    b->mix_cap = 0;
+    const size_t cap = std::max<size_t>(jobs, 128), bytes = cap * ntt::mixed_job_bytes();
+    e = cudaMalloc(&b->d_mix, bytes);
+    if (e == cudaSuccess) e = cudaMemset(b->d_mix, 0, bytes);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_mix, bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) std::memset(b->h_mix, 0, bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();     // the zeroing is done before any upload
+    if (e != cudaSuccess) {
+        cudaFree(b->d_mix);
+        if (b->h_mix) cudaFreeHost(b->h_mix);
+        b->d_mix = b->h_mix = nullptr;
+        return e;
+    }
+    b->mix_cap = cap;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -145,14 +191,22 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
     }
     if (ntt::host::any_overlap(ranges)) return NTT_ERR_INVALID_ARG;
 
-    // group the fused jobs by (size and geometry, direction, OT stages); the rest run alone
+    // Fused jobs of plans with the default geometry go into one mixed-size
+    // launch per OT setting (all sizes and both directions together); fused
+    // jobs of other geometries are grouped by (size and geometry, direction,
+    // OT stages) into launches of up to FUSED_MAX_JOBS jobs; the rest run alone.
     std::vector<uint32_t> fused, direct;
+    std::vector<std::vector<uint32_t>> mixed(3);          // by OT stages
     std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> keys;
     std::vector<uint64_t> limbs, sizes;
     for (uint32_t i = 0; i < njobs; ++i) {
         const ntt_plan* p = jobs[i].plan;
         if (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED) {
             const uint32_t ots = p->twiddle_mode == NTT_TWIDDLE_OT ? p->ot_stages : 0;
+            if (p->geom == 0 && ots <= 2) {
+                mixed[ots].push_back(i);
+                continue;
+            }
             fused.push_back(i);
             keys.emplace_back(p->n | (p->geom << 8), jobs[i].op, ots);
             limbs.push_back((uint64_t)jobs[i].batch * jobs[i].levels);
@@ -166,13 +220,38 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         if (c.limbs > 0x7FFFFFFFull) return NTT_ERR_INVALID_ARG;
         for (uint32_t& j : c.jobs) j = fused[j];          // indices into the submission
     }
+    auto job_in = [&](uint32_t i) {
+        const ntt_plan* p = jobs[i].plan;
+        return ntt::MixJobIn{ntt::JobCtx{reinterpret_cast<ntt::u64*>(jobs[i].data), jobs[i].batch * jobs[i].levels,
+                                         jobs[i].levels, p->d_primes, p->d_tw, p->tw_len, p->d_ota_f, p->d_otb_f,
+                                         p->d_ota_i, p->d_otb_i},
+                             p->n, jobs[i].op == NTT_OP_FORWARD ? 1u : 0u};
+    };
+    // the mixed launches: per OT setting, up to MIXED_MAX_JOBS jobs each
+    std::vector<std::vector<ntt::MixJobIn>> mixin;
+    std::vector<uint32_t> mix_ots;
+    size_t mix_jobs = 0;
+    for (int o = 0; o < 3; ++o) {
+        for (size_t k = 0; k < mixed[o].size(); k += ntt::MIXED_MAX_JOBS) {
+            mixin.emplace_back();
+            mix_ots.push_back((uint32_t)o);
+            for (size_t m = k; m < mixed[o].size() && m < k + ntt::MIXED_MAX_JOBS; ++m)
+                mixin.back().push_back(job_in(mixed[o][m]));
+            mix_jobs += mixin.back().size();
+        }
+    }
 
-    // one work area per fused launch, back to back; grown in stream order
+    // one work area per launch, back to back; grown in stream order
     const cudaStream_t caller = (cudaStream_t)stream;
     size_t words = 0;
+    for (const auto& m : mixin) words += ntt::mixed_work_words(m.data(), (uint32_t)m.size());
     for (const ntt::host::Chunk& c : chunks) words += ntt::fused_work_words(c.limbs);
     if (words > b->work_words) {
         cudaError_t e = grow_work(b, words, caller);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (mix_jobs > b->mix_cap) {
+        cudaError_t e = reserve_mix(b, mix_jobs, caller);
         if (e != cudaSuccess) return cuda_status(e);
     }
 
@@ -181,9 +260,11 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
     // test_stall_polls polls (the kernels then set the status word)
     const uint32_t stall = b->test_stall_polls;
     b->test_stall_polls = 0;
+    size_t mix_words = 0;
+    for (const auto& m : mixin) mix_words += ntt::mixed_work_words(m.data(), (uint32_t)m.size());
     if (stall) {
         static const uint32_t taken = 0x40000000u;
-        size_t o = 0;
+        size_t o = mix_words;
         for (const ntt::host::Chunk& c : chunks) {
             cudaError_t e = cudaMemcpyAsync(b->d_work + o, &taken, sizeof(taken), cudaMemcpyHostToDevice, caller);
             if (e != cudaSuccess) return cuda_status(e);
@@ -192,18 +273,36 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
     }
 
     // fork onto the internal streams
-    const int used = (int)std::min<size_t>(kStreams, chunks.size() + direct.size());
+    const size_t nmix = mixin.size();
+    const int used = (int)std::min<size_t>(kStreams, nmix + chunks.size() + direct.size());
     cudaError_t e = cudaEventRecord(b->fork, caller);
     for (int k = 0; k < used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->s[k], b->fork, 0);
     if (e != cudaSuccess) return cuda_status(e);
-    // longest first, each on the least loaded stream
+    // longest first, each on the least loaded stream: the mixed launches,
+    // the chunks, then the jobs that run alone
     std::vector<double> work;
+    for (const auto& mj : mixin) {
+        double w = 0;
+        for (const ntt::MixJobIn& m : mj) w += (double)m.job.limbs * (double)(1u << m.n);
+        work.push_back(w);
+    }
     for (const ntt::host::Chunk& c : chunks) work.push_back(c.work);
     for (uint32_t i : direct) work.push_back((double)jobs[i].batch * jobs[i].levels * jobs[i].plan->N);
     const std::vector<int> at = ntt::host::place_least_loaded(work, used);
-    size_t off = 0;
+    size_t off = 0, item = 0, desc = 0;
+    for (size_t mi = 0; mi < mixin.size() && e == cudaSuccess; ++mi) {
+        const size_t n = mixin[mi].size();
+        const size_t w = ntt::mixed_work_words(mixin[mi].data(), (uint32_t)n);
+        auto* d_desc = reinterpret_cast<ntt::MixJob*>(static_cast<char*>(b->d_mix) + desc * ntt::mixed_job_bytes());
+        auto* h_desc = reinterpret_cast<ntt::MixJob*>(static_cast<char*>(b->h_mix) + desc * ntt::mixed_job_bytes());
+        e = ntt::launch_mixed(mixin[mi].data(), (uint32_t)n, mix_ots[mi], d_desc, h_desc, b->d_work + off, w,
+                              b->d_status, stall, b->s[at[item]]);
+        off += w;
+        desc += n;
+        ++item;
+    }
     std::vector<ntt::JobCtx> jc;
-    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    for (size_t ci = 0; ci < chunks.size() && e == cudaSuccess; ++ci) {
         const ntt::host::Chunk& c = chunks[ci];
         jc.clear();
         for (uint32_t i : c.jobs) {
@@ -212,21 +311,21 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
                                      jobs[i].levels, p->d_primes, p->d_tw, p->tw_len, p->d_ota_f, p->d_otb_f,
                                      p->d_ota_i, p->d_otb_i});
         }
-        const int k = at[ci];
+        const int k = at[item++];
         const uint32_t n = std::get<0>(c.key) & 0xFFu, geom = std::get<0>(c.key) >> 8, ots = std::get<2>(c.key);
         const bool fwd = std::get<1>(c.key) == NTT_OP_FORWARD;
         const ntt::JobsCtx ctx{jc.data(), (uint32_t)jc.size(), n, ots, b->d_status, b->d_work + off,
                                (uint32_t)c.limbs, b->s[k], stall, geom};
         off += ntt::fused_work_words(c.limbs);
         e = ntt::launch_fused_jobs(ctx, fwd);
-        if (e != cudaSuccess) break;
     }
     for (size_t m = 0; m < direct.size() && e == cudaSuccess; ++m) {
         const ntt_job& j = jobs[direct[m]];
-        const int k = at[chunks.size() + m];
+        const int k = at[item++];
         const ntt::LaunchCtx c = j.plan->ctx(j.data, j.batch * j.levels, j.levels, b->s[k]);
         e = ntt::launch_transform(c, j.op == NTT_OP_FORWARD);
     }
+    b->last_launches = (uint32_t)item;
     // join back onto the caller's stream (also after a failed launch, so the
     // caller's stream stays ordered after whatever was enqueued)
     for (int k = 0; k < used; ++k) {
@@ -245,6 +344,16 @@ ntt_status ntt_internal_batch_test_stall(ntt_batch* b, uint32_t max_polls)
     if (!b || max_polls == 0) return NTT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> guard(b->mu);
     b->test_stall_polls = max_polls;
+    return NTT_OK;
+}
+
+// Test hook (not part of the public interface): kernel launches of the
+// latest submission (direct jobs count their own launches as one each).
+ntt_status ntt_internal_batch_last_launches(ntt_batch* b, uint32_t* count)
+{
+    if (!b || !count) return NTT_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(b->mu);
+    *count = b->last_launches;
     return NTT_OK;
 }
 

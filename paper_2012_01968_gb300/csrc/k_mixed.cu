@@ -1,0 +1,153 @@
+// Host side of the mixed-size launch (ntt_mixed.cuh): groups, job
+// descriptors, CTA shares, and the three instantiations (table, OT of one or
+// two stages).
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "launch.cuh"
+#include "ntt_mixed.cuh"
+
+namespace ntt {
+
+namespace {
+
+template <int OTS>
+cudaError_t launch_mixed_ots(const MixParams& prm, cudaStream_t s, u32 units_total, u32* grid_out)
+{
+    using LY = MixLayout<KMAX_ALL, OTS>;
+    auto kern = ntt_mixed_kernel<KMAX_ALL, OTS>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int occ = 0;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, LY::THREADS, LY::SMEM);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const u64 slots = (u64)device_sm_count() * (u64)occ;
+    const u32 grid = (u32)std::min<u64>(units_total, slots);
+    // SM shares of the groups (in 1/1024ths of the SMs), in proportion to
+    // their work (limbs x N log N)
+    MixParams a = prm;
+    double total = 0;
+    std::vector<double> w(a.ngroups);
+    for (u32 g = 0; g < a.ngroups; ++g) {
+        const u32 n = MIX_FIRST_N + a.group[g].cls;
+        w[g] = (double)a.group[g].limbs * (double)(1u << n) * n;
+        total += w[g];
+    }
+    double acc = 0;
+    for (u32 g = 0; g < a.ngroups; ++g) {
+        a.sm_start[g] = (u32)std::min<double>(1024.0, acc / total * 1024.0 + 0.5);
+        acc += w[g];
+    }
+    a.sm_start[a.ngroups] = 1024;
+    *grid_out = grid;
+    kern<<<grid, LY::THREADS, LY::SMEM, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t mixed_job_bytes() { return sizeof(MixJob); }
+
+size_t mixed_work_words(const MixJobIn* jobs, u32 njobs)
+{
+    std::vector<u64> limbs(MIX_MAX_GROUPS, 0);
+    for (u32 i = 0; i < njobs; ++i) limbs[(jobs[i].n - MIX_FIRST_N) * 2 + (jobs[i].fwd ? 1 : 0)] += jobs[i].job.limbs;
+    size_t w = 1;
+    for (u64 l : limbs)
+        if (l) w += mix_group_words(l);
+    return w;
+}
+
+cudaError_t launch_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixJob* d_jobs, MixJob* h_jobs, u32* work,
+                         size_t work_words, u32* status, u32 stall_polls, cudaStream_t s)
+{
+    if (njobs == 0 || njobs > (u32)MIX_MAX_JOBS || ots > 2) return cudaErrorInvalidValue;
+    // groups: one per (size class, direction), in that order
+    std::vector<std::vector<u32>> members(MIX_MAX_GROUPS);
+    for (u32 i = 0; i < njobs; ++i) {
+        if (jobs[i].n < (u32)MIX_FIRST_N || jobs[i].n >= (u32)(MIX_FIRST_N + MIX_CLASSES)) return cudaErrorInvalidValue;
+        members[(jobs[i].n - MIX_FIRST_N) * 2 + (jobs[i].fwd ? 1 : 0)].push_back(i);
+    }
+    MixParams a{};
+    std::vector<MixJob> hj(njobs);
+    u32 nj = 0, ctl = 0;
+    u64 units_total = 0;
+    for (u32 key = 0; key < (u32)MIX_MAX_GROUPS; ++key) {
+        if (members[key].empty()) continue;
+        MixGroup& g = a.group[a.ngroups];
+        g.cls = key / 2;
+        g.fwd = key & 1;
+        g.job0 = nj;
+        g.njobs = (u32)members[key].size();
+        const Geometry geo = geometry_of((int)(MIX_FIRST_N + g.cls), 0);
+        const int p1 = geo.p1, cr = 1 << geo.logc_r, n = MIX_FIRST_N + (int)g.cls;
+        const int row_tile = cr << (n - p1);
+        u64 limbs = 0;
+        for (u32 i : members[key]) {
+            const JobCtx& J = jobs[i].job;
+            MixJob& m = hj[nj];
+            MixJobInfo& info = a.info[nj++];
+            std::memset(&m, 0, sizeof(m));
+            cudaError_t e = encode_tile_maps(J.data, J.limbs, (u32)n, p1, row_tile, &m.mapC, &m.mapR);
+            if (e != cudaSuccess) return e;
+            info.primes = J.primes;
+            info.tw = J.tw;
+            info.ota = g.fwd ? J.ota_f : J.ota_i;
+            info.otb = g.fwd ? J.otb_f : J.otb_i;
+            info.tw_len = J.tw_len;
+            info.L = J.L;
+            info.limb0 = (u32)limbs;
+            limbs += J.limbs;
+        }
+        if (limbs >= (1ull << 28)) return cudaErrorInvalidValue;
+        g.limbs = (u32)limbs;
+        g.ctl = ctl;
+        ctl += (u32)mix_group_words(limbs);
+        units_total += limbs * (((1ull << n) >> p1 >> 4) + ((1ull << p1) / cr));
+        ++a.ngroups;
+    }
+    const size_t words = (size_t)ctl + 1;
+    if (!work || work_words < words) return cudaErrorInvalidValue;
+    // the descriptors go to the device only when they changed (a repeated
+    // submission, e.g. one replayed from a CUDA graph, reuses them)
+    const size_t bytes = sizeof(MixJob) * njobs;
+    if (std::memcmp(h_jobs, hj.data(), bytes) != 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(s, &cs);
+        if (e != cudaSuccess) return e;
+        if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+        // the host copy may still be the source of an earlier upload: wait for it
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        std::memcpy(h_jobs, hj.data(), bytes);
+        e = cudaMemcpyAsync(d_jobs, h_jobs, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (stall_polls) {
+        static const u32 taken = 0x40000000u;
+        for (u32 g = 0; g < a.ngroups; ++g) {
+            cudaError_t e = cudaMemcpyAsync(work + a.group[g].ctl, &taken, sizeof(taken), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    a.jobs = d_jobs;
+    a.ctl = work;
+    a.status = status;
+    a.ctl_words = (u32)words;
+    a.max_polls = stall_polls ? stall_polls : 1u << 22;
+    u32 grid = 0;
+    switch (ots) {
+    case 0: return launch_mixed_ots<0>(a, s, (u32)std::min<u64>(units_total, 0xFFFFFFFFull), &grid);
+    case 1: return launch_mixed_ots<1>(a, s, (u32)std::min<u64>(units_total, 0xFFFFFFFFull), &grid);
+    default: return launch_mixed_ots<2>(a, s, (u32)std::min<u64>(units_total, 0xFFFFFFFFull), &grid);
+    }
+}
+
+}  // namespace ntt

@@ -133,12 +133,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src, uint64_t& bytes)
 void free_plan(ntt_plan* p)
 {
     if (!p) return;
-    cudaFree(p->d_primes);
-    cudaFree(p->d_tw);
-    cudaFree(p->d_ota_f);
-    cudaFree(p->d_otb_f);
-    cudaFree(p->d_ota_i);
-    cudaFree(p->d_otb_i);
+    p->tables.reset();                  // frees the tables with the last plan sharing them
     cudaFree(p->d_stage);
     cudaFree(p->d_hwork);
     if (p->h_in) cudaStreamDestroy(p->h_in);
@@ -291,12 +286,20 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     ce = cudaMalloc(&p->d_status, sizeof(uint32_t));
     if (ce == cudaSuccess) ce = cudaMemset(p->d_status, 0, sizeof(uint32_t));
     if (ce == cudaSuccess) ce = ntt_internal_grow_work(p, L * 16u);
-    if (ce == cudaSuccess) ce = upload(&p->d_primes, h.pd, p->device_bytes);
-    if (ce == cudaSuccess) ce = upload(&p->d_tw, h.tw, p->device_bytes);
-    if (ce == cudaSuccess) ce = upload(&p->d_ota_f, h.ota_f, p->device_bytes);
-    if (ce == cudaSuccess) ce = upload(&p->d_otb_f, h.otb_f, p->device_bytes);
-    if (ce == cudaSuccess) ce = upload(&p->d_ota_i, h.ota_i, p->device_bytes);
-    if (ce == cudaSuccess) ce = upload(&p->d_otb_i, h.otb_i, p->device_bytes);
+    p->tables = std::make_shared<NttPlanTables>();
+    NttPlanTables& t = *p->tables;
+    if (ce == cudaSuccess) ce = upload(&t.primes, h.pd, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&t.tw, h.tw, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&t.ota_f, h.ota_f, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&t.otb_f, h.otb_f, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&t.ota_i, h.ota_i, p->device_bytes);
+    if (ce == cudaSuccess) ce = upload(&t.otb_i, h.otb_i, p->device_bytes);
+    p->d_primes = t.primes;
+    p->d_tw = t.tw;
+    p->d_ota_f = t.ota_f;
+    p->d_otb_f = t.otb_f;
+    p->d_ota_i = t.ota_i;
+    p->d_otb_i = t.otb_i;
     if (ce == cudaSuccess && (p->flags & NTT_PLAN_L2_TWIDDLES)) ce = reserve_l2(p);
     if (ce != cudaSuccess) {
         ntt_internal_set_cuda_error(ce);
@@ -309,6 +312,50 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
 }
 
 extern "C" void ntt_plan_destroy(ntt_plan* plan) { free_plan(plan); }
+
+extern "C" ntt_status ntt_plan_clone(ntt_plan** out, const ntt_plan* src)
+{
+    if (!out || !src) return NTT_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != src->device) return NTT_ERR_INVALID_ARG;
+    ntt_plan* p = new (std::nothrow) ntt_plan();
+    if (!p) return NTT_ERR_OOM;
+    p->N = src->N;
+    p->n = src->n;
+    p->L = src->L;
+    p->p1 = src->p1;
+    p->passes = src->passes;
+    p->twiddle_mode = src->twiddle_mode;
+    p->ot_stages = src->ot_stages;
+    p->device = src->device;
+    p->primes = src->primes;
+    p->psis = src->psis;
+    p->tables = src->tables;
+    p->d_primes = src->d_primes;
+    p->d_tw = src->d_tw;
+    p->tw_len = src->tw_len;
+    p->d_ota_f = src->d_ota_f;
+    p->d_otb_f = src->d_otb_f;
+    p->d_ota_i = src->d_ota_i;
+    p->d_otb_i = src->d_otb_i;
+    p->device_bytes = src->device_bytes;
+    p->kernel = src->kernel;
+    p->geom = src->geom;
+    p->flags = src->flags;
+    p->radix_log2 = src->radix_log2;
+    p->l2_hit = src->l2_hit;
+    cudaError_t ce = cudaMalloc(&p->d_status, sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = cudaMemset(p->d_status, 0, sizeof(uint32_t));
+    if (ce == cudaSuccess) ce = ntt_internal_grow_work(p, src->work_limbs ? src->work_limbs : src->L * 16u);
+    if (ce != cudaSuccess) {
+        ntt_internal_set_cuda_error(ce);
+        free_plan(p);
+        cudaGetLastError();
+        return ce == cudaErrorMemoryAllocation ? NTT_ERR_OOM : NTT_ERR_CUDA;
+    }
+    *out = p;
+    return NTT_OK;
+}
 
 extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
 {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -144,6 +145,25 @@ struct JobsCtx {
     u32 chain = 0;                   // one job: forward, then inverse, in one launch
 };
 cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
+
+// Jobs of different sizes (2^13 .. 2^17, plans of geometry 0) and directions
+// in one launch (ntt_mixed.cuh, k_mixed.cu), at most MIXED_MAX_JOBS jobs.  d_jobs / h_jobs: a device array
+// and its page-locked host copy of mixed_job_bytes() per job; the host copy
+// must equal what the device array holds (both start zeroed); descriptors are
+// uploaded only when they change, which a graph capture refuses.  The work
+// area holds mixed_work_words() zeroed words.  stall_polls > 0 (test hook):
+// every group's first-phase queue starts taken, waits bounded by it.
+struct MixJobIn {
+    JobCtx job;
+    u32 n;                   // log2 N
+    u32 fwd;                 // 1: forward
+};
+struct MixJob;
+constexpr u32 MIXED_MAX_JOBS = 128;
+size_t mixed_job_bytes();
+size_t mixed_work_words(const MixJobIn* jobs, u32 njobs);
+cudaError_t launch_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixJob* d_jobs, MixJob* h_jobs, u32* work,
+                         size_t work_words, u32* status, u32 stall_polls, cudaStream_t s);
 cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a, const u64* b,
                              u64* out, u32 limbs, cudaStream_t s);
 
@@ -164,6 +184,26 @@ cudaError_t launch_jobs_n17(const JobsCtx& c, bool fwd);
 
 }  // namespace ntt
 
+// Device tables of a plan, shared by the plan and its clones (ntt_plan_clone)
+// and freed with the last of them.
+struct NttPlanTables {
+    ntt::PrimeDev* primes = nullptr;
+    ntt::Tw* tw = nullptr;
+    ntt::Tw* ota_f = nullptr;
+    ntt::Tw* otb_f = nullptr;
+    ntt::Tw* ota_i = nullptr;
+    ntt::Tw* otb_i = nullptr;
+    ~NttPlanTables()
+    {
+        cudaFree(primes);
+        cudaFree(tw);
+        cudaFree(ota_f);
+        cudaFree(otb_f);
+        cudaFree(ota_i);
+        cudaFree(otb_i);
+    }
+};
+
 struct ntt_plan {
     uint32_t N = 0, n = 0, L = 0;
     uint32_t p1 = 0, passes = 0;
@@ -178,6 +218,7 @@ struct ntt_plan {
     ntt::Tw* d_ota_i = nullptr;
     ntt::Tw* d_otb_i = nullptr;
     uint64_t device_bytes = 0;
+    std::shared_ptr<NttPlanTables> tables;   // owner of d_primes .. d_otb_i
     uint32_t kernel = 0;                  // NTT_KERNEL_*
     uint32_t geom = 0;                    // geometry index (two-pass sizes)
     uint32_t flags = 0;                   // NTT_PLAN_* bits

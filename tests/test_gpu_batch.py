@@ -53,6 +53,8 @@ def test_uneven_batch_c4_against_oracle(orc, chain, options):
                       for i, j in enumerate(w.jobs)])
             torch.cuda.synchronize()
             assert b.device_status() == 0
+            if options == "default":
+                assert _last_launches(b) == 1          # all 96 jobs, four sizes, both directions
         for i, j in enumerate(w.jobs):
             want = (oracle_fwd if j.dir > 0 else oracle_inv)(orc, datas[i], chain[:j.L])
             assert np.array_equal(host(devs[i]), want), f"job {i}: N={j.N} L={j.L} dir={j.dir}"
@@ -89,9 +91,21 @@ def test_batch_equals_single_calls(chain):
             p.close()
 
 
-def test_many_jobs_one_group_are_chunked(chain):
-    """40 jobs of one size and direction: several launches of up to 16 jobs."""
-    p = G.Plan(1 << 13, chain)
+def _last_launches(b):
+    import ctypes
+    fn = G.lib().ntt_internal_batch_last_launches
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]
+    n = ctypes.c_uint32()
+    assert fn(b.handle, ctypes.byref(n)) == 0
+    return n.value
+
+
+@pytest.mark.parametrize("geometry", [G.NTT_GEOMETRY_DEFAULT, G.NTT_GEOMETRY_SMALL_ROW_TILE])
+def test_many_jobs_one_size(chain, geometry):
+    """40 jobs of one size and direction: one mixed launch with the default
+    geometry, launches of up to 16 jobs with another."""
+    p = G.Plan(1 << 13, chain, G.NTT_TWIDDLE_OT, 1, G.NTT_KERNEL_FUSED, geometry)
     try:
         datas = [I.batch_uniform(300 + i, 1, chain[:1 + i % 5], 1 << 13) for i in range(40)]
         got = [dev(d) for d in datas]
@@ -102,6 +116,7 @@ def test_many_jobs_one_group_are_chunked(chain):
             b.submit([(p.handle, t, 1, d.shape[1], FWD) for d, t in zip(datas, got)])
             torch.cuda.synchronize()
             assert b.device_status() == 0
+            assert _last_launches(b) == (1 if geometry == G.NTT_GEOMETRY_DEFAULT else 3)
         for a, c in zip(got, want):
             assert torch.equal(a, c)
     finally:

@@ -589,3 +589,31 @@ def test_execute_other_organisations(kernel):
         assert np.array_equal(host(d).reshape(data.shape), data)
         with pytest.raises(G.NttError):
             p.execute(d, 4, 1)
+
+
+def test_plan_clone_shares_tables_and_runs_concurrently(orc):
+    """A clone gives the same results, on another stream at the same time,
+    and outlives the plan it was cloned from."""
+    N = 1 << 15
+    primes = I.prime_chain(6, 2 * N)
+    data = I.batch_uniform(123, 2, primes, N)
+    p = G.Plan(N, primes)
+    c = p.clone()
+    assert c.info().device_bytes == p.info().device_bytes
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a, b = dev(data), dev(data)
+    for _ in range(4):
+        p.execute(a, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE, 2, s1)
+        c.execute(b, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE, 2, s2)
+    p.forward(a, 2, s1)
+    c.forward(b, 2, s2)
+    torch.cuda.synchronize()
+    want = oracle_fwd(orc, data, primes)
+    assert np.array_equal(host(a).reshape(data.shape), want)
+    assert np.array_equal(host(b).reshape(data.shape), want)
+    p.close()
+    c.inverse(b, 2)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(b).reshape(data.shape), data)
+    assert c.device_status() == 0
+    c.close()
