@@ -48,8 +48,11 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "per_pass"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
-    ap.add_argument("--streams", type=int, default=2,
+    ap.add_argument("--streams", type=int, default=3,
                     help="independent steps spread over this many streams (one plan each)")
+    ap.add_argument("--ctas-per-sm", type=int, default=1,
+                    help="persistent CTAs per SM of the timed steps' fused launches (0: as many as fit); "
+                         "with one, launches on different streams share every SM")
     ap.add_argument("--no-batch-compare", action="store_true",
                     help="skip the per-limb C2 path and the uneven 96-job batch")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
@@ -870,8 +873,10 @@ def config_dict(w, args, ws):
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
             "twiddle": args.twiddle, "parallelism": f"replicas{ws}",
             "streams": args.streams,
+            "ctas_per_sm": args.ctas_per_sm,
             "overlap": "step i runs on stream i mod streams with its own plan (clones sharing one set of tables); "
-                       "steps are independent polynomials",
+                       "steps are independent polynomials; with one persistent CTA per SM per launch, "
+                       "launches on different streams share the SMs",
             "l2": "inputs rotate over buffers totalling > 2x L2 (129 MB)"}
 
 
@@ -932,9 +937,9 @@ def main():
     l2f = G.NTT_PLAN_L2_TWIDDLES if args.l2_twiddles else 0
     if not args.no_tune and args.twiddle == "auto" and args.kernel == "auto":
         best, c2_tune = autotune(G, N, primes, 1, reps=20)
-        plans = [G.Plan.from_opts(N, primes, best, flags=l2f or None)]
+        plans = [G.Plan.from_opts(N, primes, best, flags=l2f or None, ctas_per_sm=args.ctas_per_sm)]
     else:
-        plans = [G.Plan(N, primes, *mode, kern, flags=l2f)]
+        plans = [G.Plan(N, primes, *mode, kern, flags=l2f, ctas_per_sm=args.ctas_per_sm)]
     # the other streams' plans share the first plan's tables (ntt_plan_clone)
     plans += [plans[0].clone() for _ in range(S - 1)]
     plan = plans[0]
@@ -1003,9 +1008,14 @@ def main():
 
     # per-launch durations, one stream, CUDA events around every call
     # (launches do not overlap here): the separate forward and inverse calls,
-    # and the one-launch forward + inverse call
+    # and the one-launch forward + inverse call.  A clone of the timed plan
+    # with as many CTAs per SM as fit: the launch configuration for a stream
+    # that runs alone (the same kernel as the timed steps)
     Kp = min(K, args.launch_steps)
     s0 = streams[0]
+    solo = plans[0].clone()
+    solo.set_ctas_per_sm(0)
+    handles = [solo.handle] + handles[1:]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Kp + 1)]
     evc = [torch.cuda.Event(enable_timing=True) for _ in range(Kp + 1)]
     torch.cuda.synchronize()
@@ -1153,7 +1163,7 @@ def main():
                      "kernel": kname,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
                      "units_per_launch": f"{per_launch * L} limb-NTTs of N={N} (16 N bytes each: one read, one write)",
-                     "launch_timing": f"CUDA events around each of {Kp} launches on one stream",
+                     "launch_timing": f"CUDA events around each of {Kp} launches on one stream (a clone of the timed plan with as many CTAs per SM as fit)",
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
         "roofline_alu": {"bound": "alu", "achieved": bfly_achieved, "peak": alu_peak_gbfly(),
                          "unit": "G butterfly/s", "frac": bfly_achieved / alu_peak_gbfly(),

@@ -106,8 +106,20 @@ typedef struct ntt_plan_opts {
     uint32_t geometry;        /* NTT_GEOMETRY_*; must be 0 for N <= 2^12 and for RADIX2 */
     uint32_t flags;           /* NTT_PLAN_* bits */
     uint32_t radix_log2;      /* HIGH_RADIX: stages per launch, 1..5 (0 = 4, radix 16); else 0 */
-    uint32_t reserved[2];     /* must be zero */
+    uint32_t ctas_per_sm;     /* FUSED two-pass sizes: persistent CTAs per SM of the plan's
+                               * launches, 1..8, capped by what fits (0 = as many as fit, 2).
+                               * 1 leaves room on every SM for a launch on another stream to
+                               * run beside it; see NTT_CTAS_PER_SM_NOTE below */
+    uint32_t reserved;        /* must be zero */
 } ntt_plan_opts;
+
+/* NTT_CTAS_PER_SM_NOTE: a fused launch ends in a tail where its last units
+ * run on few SMs, and its passes meet at limb boundaries where units wait for
+ * the previous pass of their limb.  With two persistent CTAs per SM (the
+ * default) a launch on a second stream can start only as the first launch's
+ * CTAs exit.  With one CTA per SM two launches on two streams run side by
+ * side, each filling the other's waits: measured faster when two or more
+ * streams issue transforms, slower for one stream alone. */
 
 /* Keep the plan's twiddle table resident in L2 across calls: plan creation
  * raises this CUDA context's persisting-L2 limit (cudaLimitPersistingL2CacheSize,
@@ -147,6 +159,16 @@ void ntt_plan_destroy(ntt_plan* plan);
  * device current.  Errors: NTT_ERR_INVALID_ARG, NTT_ERR_OOM, NTT_ERR_CUDA.
  */
 ntt_status ntt_plan_clone(ntt_plan** out, const ntt_plan* plan);
+
+/*
+ * Change the persistent CTAs per SM of the plan's fused launches (the
+ * ctas_per_sm plan option, 0..8, 0 = as many as fit), e.g. on a clone that
+ * runs alone on one stream while its source runs beside other streams.
+ * Takes effect for calls made after it returns; do not call it while another
+ * thread issues calls on the same plan.  Errors: NTT_ERR_INVALID_ARG (NULL,
+ * ctas_per_sm > 8).
+ */
+ntt_status ntt_plan_set_ctas_per_sm(ntt_plan* plan, uint32_t ctas_per_sm);
 
 /*
  * In-place forward transform of `batch` polynomials at device address `data`
@@ -554,7 +576,7 @@ typedef struct ntt_plan_info {
     uint32_t geometry;        /* NTT_GEOMETRY_* */
     uint32_t row_tile_log2;   /* rows per tile of the second pass (two-pass sizes), log2 */
     uint32_t radix_log2;      /* HIGH_RADIX: stages per launch; else 0 */
-    uint32_t reserved;
+    uint32_t ctas_per_sm;     /* the option the plan was created with (0: as many as fit) */
 } ntt_plan_info;
 
 ntt_status ntt_plan_query(const ntt_plan* plan, ntt_plan_info* info);

@@ -59,7 +59,7 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("twiddle_mode", _u32), ("ot_stages", _u32), ("kernel", _u32), ("geometry", _u32),
-                ("flags", _u32), ("radix_log2", _u32), ("reserved", _u32 * 2)]
+                ("flags", _u32), ("radix_log2", _u32), ("ctas_per_sm", _u32), ("reserved", _u32)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -71,7 +71,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("N", _u32), ("L", _u32), ("log2_N", _u32), ("passes", _u32),
                 ("pass1_log2", _u32), ("twiddle_mode", _u32), ("ot_stages", _u32),
                 ("device", _u32), ("kernel", _u32), ("device_bytes", _u64), ("geometry", _u32),
-                ("row_tile_log2", _u32), ("radix_log2", _u32), ("reserved", _u32)]
+                ("row_tile_log2", _u32), ("radix_log2", _u32), ("ctas_per_sm", _u32)]
 
 
 class Job(ctypes.Structure):
@@ -135,6 +135,8 @@ def _lib():
             L.ntt_plan_destroy.argtypes = [_vp]
             L.ntt_plan_clone.restype = S
             L.ntt_plan_clone.argtypes = [ctypes.POINTER(_vp), _vp]
+            L.ntt_plan_set_ctas_per_sm.restype = S
+            L.ntt_plan_set_ctas_per_sm.argtypes = [_vp, _u32]
             for f in ("ntt_forward", "ntt_inverse"):
                 getattr(L, f).restype = S
                 getattr(L, f).argtypes = [_vp, _vp, _u32, _vp]
@@ -249,11 +251,11 @@ def _check(st: int, where: str):
 # --------------------------------------------------------------------------
 def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
                     kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0,
-                    radix_log2: int = 0) -> int:
+                    radix_log2: int = 0, ctas_per_sm: int = 0) -> int:
     """Create a plan; returns the opaque handle (an int).  Raises NttError."""
     primes = [int(p) for p in primes]
     arr = (_u64 * len(primes))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2, ctas_per_sm)
     out = _vp()
     _check(_lib().ntt_plan_create(ctypes.byref(out), N, arr, len(primes), ctypes.byref(opts)),
            "ntt_plan_create")
@@ -261,14 +263,14 @@ def ntt_plan_create(N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_sta
 
 
 def ntt_plan_create_status(N: int, primes, twiddle_mode: int = 0, ot_stages: int = 0, reserved=None,
-                           kernel: int = 0, geometry: int = 0, flags: int = 0, radix_log2: int = 0):
+                           kernel: int = 0, geometry: int = 0, flags: int = 0, radix_log2: int = 0,
+                           ctas_per_sm: int = 0):
     """Like ntt_plan_create but returns (status, handle) without raising."""
     primes = [int(p) for p in primes]
     arr = (_u64 * max(1, len(primes)))(*primes)
-    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2)
+    opts = PlanOpts(twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2, ctas_per_sm)
     if reserved:
-        for i, v in enumerate(reserved):
-            opts.reserved[i] = v
+        opts.reserved = int(reserved[0])
     out = _vp()
     st = _lib().ntt_plan_create(ctypes.byref(out), N, arr if primes else None, len(primes),
                                 ctypes.byref(opts))
@@ -472,17 +474,19 @@ class Plan:
 
     def __init__(self, N: int, primes, twiddle_mode: int = NTT_TWIDDLE_AUTO, ot_stages: int = 0,
                  kernel: int = NTT_KERNEL_AUTO, geometry: int = NTT_GEOMETRY_DEFAULT, flags: int = 0,
-                 radix_log2: int = 0):
+                 radix_log2: int = 0, ctas_per_sm: int = 0):
         self.N = N
         self.primes = [int(p) for p in primes]
         self.L = len(self.primes)
-        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2)
+        self.handle = ntt_plan_create(N, self.primes, twiddle_mode, ot_stages, kernel, geometry, flags, radix_log2,
+                                      ctas_per_sm)
 
     @classmethod
-    def from_opts(cls, N: int, primes, opts: PlanOpts, flags: int | None = None):
-        """A plan with the options an autotuner run returned (flags: override)."""
+    def from_opts(cls, N: int, primes, opts: PlanOpts, flags: int | None = None, ctas_per_sm: int | None = None):
+        """A plan with the options an autotuner run returned (flags, ctas_per_sm: overrides)."""
         return cls(N, primes, opts.twiddle_mode, opts.ot_stages, opts.kernel, opts.geometry,
-                   opts.flags if flags is None else flags, opts.radix_log2)
+                   opts.flags if flags is None else flags, opts.radix_log2,
+                   opts.ctas_per_sm if ctas_per_sm is None else ctas_per_sm)
 
     def clone(self) -> "Plan":
         """A plan sharing this one's device tables, with its own work area
@@ -492,6 +496,10 @@ class Plan:
         c = object.__new__(type(self))
         c.N, c.primes, c.L, c.handle = self.N, list(self.primes), self.L, out.value
         return c
+
+    def set_ctas_per_sm(self, ctas_per_sm: int) -> None:
+        """Persistent CTAs per SM of this plan's fused launches (ntt_plan_set_ctas_per_sm)."""
+        _check(_lib().ntt_plan_set_ctas_per_sm(self.handle, ctas_per_sm), "ntt_plan_set_ctas_per_sm")
 
     def forward(self, data, batch: int = 1, stream=None):
         ntt_forward(self.handle, data, batch, stream)

@@ -216,7 +216,8 @@ cudaError_t launch_fused_dir(const JobsCtx& c)
         return cudaErrorInvalidValue;
     constexpr u32 UC = F::R2 / 16, UR = F::R1 / F::CR;
     const u64 units = limbs * (UC + UR) * (CHAIN ? 2 : 1);
-    const u64 slots = (u64)device_sm_count() * (u64)occ;
+    const u64 per_sm = c.ctas_per_sm && c.ctas_per_sm < (u32)occ ? c.ctas_per_sm : (u32)occ;
+    const u64 slots = (u64)device_sm_count() * per_sm;
     const u32 grid = (u32)(units < slots ? units : slots);
     a.ctl = c.work;
     a.status = c.status;
@@ -345,6 +346,7 @@ cudaError_t launch_two_pass(const LaunchCtx& c, bool fwd)
     JobsCtx jc{&job,   1u,         c.n,      c.ots,        c.status,  c.work,   c.work_limbs,
                c.stream, c.max_polls, c.geom, c.l2_base, c.l2_bytes, c.l2_hit};
     jc.chain = c.chain;
+    jc.ctas_per_sm = c.ctas_per_sm;
     return launch_fused<P1, P2, LOGC_R, KMAX_R, 1>(jc, fwd);
 }
 

@@ -370,10 +370,11 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
             d->prime = pi;
             d->job = j;
             d->local = local;
-            // the buffer's previous store has read it: at most one unit is
-            // unstored when a unit is claimed, so at most two stores were
-            // committed after that one; waiting for all but the newest suffices
-            bulk_wait_read<1>();
+            // the buffer's previous store has read it.  A unit is claimed with
+            // at most one unit unstored, right after a store: with three
+            // buffers the buffer's previous store is older than the newest
+            // one (wait for all but the newest); with two it is the newest
+            bulk_wait_read<NBUF == 2 ? 0 : 1>();
             // a tile of a later phase reads what other CTAs' stores wrote
             if (kind > 0) fence_proxy_async_global();
             W* dst = buf_tile(b);

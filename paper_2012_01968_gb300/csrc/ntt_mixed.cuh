@@ -312,7 +312,7 @@ ntt_mixed_kernel(const __grid_constant__ MixParams a)
             d->prime = pi;
             d->job = j;
             d->local = local;
-            bulk_wait_read<1>();
+            bulk_wait_read<NBUF == 2 ? 0 : 1>();   // the buffer's previous store has read it
             if (kind > 0) fence_proxy_async_global();
             u64* dst = buf_tile(b);
             if (is_col(fwd, kind)) {

@@ -190,14 +190,14 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     ntt_plan_opts o;
     std::memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    for (uint32_t r : o.reserved)
-        if (r) return NTT_ERR_INVALID_ARG;
+    if (o.reserved) return NTT_ERR_INVALID_ARG;
     if (o.flags & ~NTT_PLAN_L2_TWIDDLES) return NTT_ERR_INVALID_ARG;
     if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
     if (o.kernel > NTT_KERNEL_HIGH_RADIX) return NTT_ERR_INVALID_ARG;
     const bool high_radix = o.kernel == NTT_KERNEL_HIGH_RADIX;
     if (high_radix ? o.radix_log2 > 5 : o.radix_log2 != 0) return NTT_ERR_INVALID_ARG;
     if (o.geometry >= (uint32_t)ntt::kGeometries) return NTT_ERR_INVALID_ARG;
+    if (o.ctas_per_sm > 8) return NTT_ERR_INVALID_ARG;
     const uint32_t n = (uint32_t)__builtin_ctz(N);
     const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
     if (o.geometry && (!two_pass || o.kernel == NTT_KERNEL_RADIX2 || high_radix)) return NTT_ERR_INVALID_ARG;
@@ -240,6 +240,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     p->radix_log2 = high_radix ? (o.radix_log2 ? o.radix_log2 : 4u) : 0u;
     p->geom = o.geometry;
     p->flags = o.flags;
+    p->ctas_per_sm = o.ctas_per_sm;
     cudaError_t ce = cudaGetDevice(&p->device);
     if (ce != cudaSuccess) {
         ntt_internal_set_cuda_error(ce);
@@ -313,6 +314,13 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
 
 extern "C" void ntt_plan_destroy(ntt_plan* plan) { free_plan(plan); }
 
+extern "C" ntt_status ntt_plan_set_ctas_per_sm(ntt_plan* p, uint32_t ctas_per_sm)
+{
+    if (!p || ctas_per_sm > 8) return NTT_ERR_INVALID_ARG;
+    p->ctas_per_sm = ctas_per_sm;
+    return NTT_OK;
+}
+
 extern "C" ntt_status ntt_plan_clone(ntt_plan** out, const ntt_plan* src)
 {
     if (!out || !src) return NTT_ERR_INVALID_ARG;
@@ -343,6 +351,7 @@ extern "C" ntt_status ntt_plan_clone(ntt_plan** out, const ntt_plan* src)
     p->geom = src->geom;
     p->flags = src->flags;
     p->radix_log2 = src->radix_log2;
+    p->ctas_per_sm = src->ctas_per_sm;
     p->l2_hit = src->l2_hit;
     cudaError_t ce = cudaMalloc(&p->d_status, sizeof(uint32_t));
     if (ce == cudaSuccess) ce = cudaMemset(p->d_status, 0, sizeof(uint32_t));
@@ -374,6 +383,7 @@ extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
     info->geometry = p->geom;
     info->row_tile_log2 = p->passes == 2 ? (uint32_t)ntt::geometry_of((int)p->n, (int)p->geom).logc_r : 0;
     info->radix_log2 = p->radix_log2;
+    info->ctas_per_sm = p->ctas_per_sm;
     return NTT_OK;
 }
 

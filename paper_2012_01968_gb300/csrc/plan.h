@@ -103,6 +103,7 @@ struct LaunchCtx {
     // fused two-pass plans, with fwd: the forward and then the inverse
     // transform in one launch (work area of chain_work_limbs(limbs) limbs)
     u32 chain = 0;
+    u32 ctas_per_sm = 0;     // fused kernel: persistent CTAs per SM (0: as many as fit)
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
@@ -143,6 +144,7 @@ struct JobsCtx {
     size_t l2_bytes = 0;
     float l2_hit = 0.f;
     u32 chain = 0;                   // one job: forward, then inverse, in one launch
+    u32 ctas_per_sm = 0;             // persistent CTAs per SM (0: as many as fit)
 };
 cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
 
@@ -223,6 +225,7 @@ struct ntt_plan {
     uint32_t geom = 0;                    // geometry index (two-pass sizes)
     uint32_t flags = 0;                   // NTT_PLAN_* bits
     uint32_t radix_log2 = 0;              // HIGH_RADIX: stages per launch
+    uint32_t ctas_per_sm = 0;             // fused launches: persistent CTAs per SM (0: as many as fit)
     float l2_hit = 0.f;                   // persisting fraction of the twiddle window
     uint32_t* d_status = nullptr;         // device status word (kernel error bits)
     uint32_t* d_work = nullptr;           // fused kernel's work area: fused_work_words(work_limbs) words
@@ -276,6 +279,7 @@ struct ntt_plan {
         c.stream = s;
         c.max_polls = 0;
         c.geom = geom;
+        c.ctas_per_sm = ctas_per_sm;
         const bool win = (flags & NTT_PLAN_L2_TWIDDLES) && l2_hit > 0.f;
         c.l2_base = win ? (const void*)d_tw : nullptr;
         c.l2_bytes = win ? (size_t)L * tw_len * sizeof(ntt::Tw) : 0;

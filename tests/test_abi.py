@@ -59,6 +59,7 @@ BIG = I.prime_chain(3, 1 << 18)
     (1 << 16, BIG[:1], {"twiddle_mode": G.NTT_TWIDDLE_OT, "ot_stages": 3}, G.NTT_ERR_INVALID_ARG),
     (1 << 16, BIG[:1], {"twiddle_mode": G.NTT_TWIDDLE_TABLE, "ot_stages": 1}, G.NTT_ERR_INVALID_ARG),
     (1 << 12, BIG[:1], {"reserved": [1]}, G.NTT_ERR_INVALID_ARG),
+    (1 << 16, BIG[:1], {"ctas_per_sm": 9}, G.NTT_ERR_INVALID_ARG),             # more CTAs per SM than any fit
     (1 << 16, BIG[:1], {"geometry": 3}, G.NTT_ERR_INVALID_ARG),                # no such geometry
     (1 << 12, BIG[:1], {"geometry": 1}, G.NTT_ERR_INVALID_ARG),                # one-pass size
     (1 << 16, BIG[:1], {"geometry": 2, "kernel": G.NTT_KERNEL_RADIX2}, G.NTT_ERR_INVALID_ARG),

@@ -20,7 +20,9 @@ random scheduler interleaves them and completes the asynchronous copies
 after random delays.  Checked for many seeds and shapes:
   * a tile of phase p > 0 is loaded only after every tile of phase p - 1 of
     its limb has been stored completely;
-  * a buffer is refilled only after the store that last used it has read it;
+  * a buffer is refilled only after the store that last used it has read it
+    (the producer waits with the kernel's slack: all but the newest store
+    with three buffers, every store with two);
   * a limb counter is raised only for stores that completed;
   * the staged-twiddle buffer is refilled only after the previous row tile
     released it, and read only after its copy landed, in row-tile order;
@@ -50,10 +52,17 @@ class Sim:
         self.events.append((self.now + self.rng.randint(lo, hi), fn))
 
 
+def kernel_read_slack(nbuf):
+    """Stores the kernel lets still read their buffers when it refills one:
+    all but the newest with three buffers, none with two."""
+    return 0 if nbuf == 2 else 1
+
+
 class Cta:
-    def __init__(self, sim, nbuf, stage):
+    def __init__(self, sim, nbuf, stage, slack=None):
         self.s = sim
         self.NBUF = nbuf
+        self.slack = kernel_read_slack(nbuf) if slack is None else slack
         self.stage = stage
         self.full = [0] * nbuf          # completed phases per buffer
         self.empty = [0] * nbuf
@@ -137,8 +146,9 @@ class Cta:
                     publish(e)
                 fifo = []
 
-        def wait_read_all():
-            while not all(x["read"] for x in self.stores):
+        def wait_read(n):
+            # cp.async.bulk.wait_group.read n: all but the n newest stores have read
+            while not all(x["read"] for x in (self.stores[:-n] if n else self.stores)):
                 yield
 
         def pub_limb(p, i):
@@ -146,7 +156,7 @@ class Cta:
 
         def do_load(p, limb, tile):
             nonlocal issued
-            yield from wait_read_all()
+            yield from wait_read(self.slack)
             self.load(p, limb, tile, issued)
             if self.stage and s.rows[p]:
                 hq.append(issued)
@@ -273,12 +283,12 @@ class Cta:
             k += 1
 
 
-def simulate(limbs, units, rows, ctas, seed, nbuf, stage, max_steps=4_000_000):
+def simulate(limbs, units, rows, ctas, seed, nbuf, stage, max_steps=4_000_000, slack=None):
     rng = random.Random(seed)
     sim = Sim(limbs, units, rows, rng)
     gens = []
     for _ in range(ctas):
-        c = Cta(sim, nbuf, stage)
+        c = Cta(sim, nbuf, stage, slack)
         gens += [c.producer(), c.compute()]
     alive = list(range(len(gens)))
     steps = 0
@@ -324,3 +334,17 @@ def test_protocol(shape, nbuf, stage, limbs, ctas):
 def test_protocol_many_ctas_few_limbs():
     """More CTAs than tiles of a phase: most producers hold tickets."""
     simulate(2, (4, 4, 4, 4), (False, True, True, False), 40, 5, 2, True)
+
+
+def test_two_buffers_need_every_store_read():
+    """With two buffers the refilled buffer is the newest store's: waiting for
+    all but the newest store (the three-buffer rule) lets a load overwrite a
+    tile its store has not read yet, which the model catches."""
+    caught = 0
+    for seed in range(20):
+        try:
+            simulate(6, (16, 16), (False, True), 4, seed, 2, True, slack=1)
+        except AssertionError as e:
+            assert "before its store read it" in str(e)
+            caught += 1
+    assert caught > 0

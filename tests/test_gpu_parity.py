@@ -617,3 +617,45 @@ def test_plan_clone_shares_tables_and_runs_concurrently(orc):
     assert np.array_equal(host(b).reshape(data.shape), data)
     assert c.device_status() == 0
     c.close()
+
+
+@pytest.mark.parametrize("n", [13, 16, 17])
+@pytest.mark.parametrize("ctas", [1, 2, 8])
+def test_ctas_per_sm_option(orc, n, ctas):
+    """Plans with one or two persistent CTAs per SM (8: capped by what fits)
+    give the oracle's results, alone and with clones running side by side on
+    two streams; the plan reports the option."""
+    N = 1 << n
+    L = 5
+    primes = I.prime_chain(L, 2 * N)
+    data = [I.batch_uniform(70 + n + k, 1, primes, N) for k in range(4)]
+    want = [oracle_fwd(orc, x, primes) for x in data]
+    with G.Plan(N, primes, G.NTT_TWIDDLE_OT, 1, ctas_per_sm=ctas) as p:
+        assert p.info().ctas_per_sm == ctas
+        q = p.clone()
+        try:
+            assert q.info().ctas_per_sm == ctas
+            ss = [torch.cuda.Stream(), torch.cuda.Stream()]
+            ds = [dev(x) for x in data]
+            for k, d in enumerate(ds):
+                (p if k % 2 == 0 else q).forward(d, 1, ss[k % 2])
+            torch.cuda.synchronize()
+            for d, w in zip(ds, want):
+                assert np.array_equal(host(d).reshape(w.shape), w)
+            both = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+            for k, d in enumerate(ds):
+                (p if k % 2 == 0 else q).execute(d, both, 1, ss[k % 2])
+            torch.cuda.synchronize()
+            for d, w in zip(ds, want):
+                assert np.array_equal(host(d).reshape(w.shape), w)
+            # the clone switched back to as many CTAs as fit; the source keeps its own
+            q.set_ctas_per_sm(0)
+            assert q.info().ctas_per_sm == 0 and p.info().ctas_per_sm == ctas
+            for k, d in enumerate(ds):
+                (p if k % 2 == 0 else q).execute(d, G.NTT_OP_INVERSE, 1, ss[k % 2])
+            torch.cuda.synchronize()
+            for d, x in zip(ds, data):
+                assert np.array_equal(host(d).reshape(x.shape), x)
+            assert p.device_status() == 0 and q.device_status() == 0
+        finally:
+            q.close()
