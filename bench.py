@@ -840,18 +840,25 @@ def word_sizes(G, torch):
 
 
 def single_limb_c1(G, torch, reps=500):
-    """C1: one limb of N = 2^12, forward then inverse, one stream: the launch
-    latency of the one-pass kernel."""
+    """C1: one limb of N = 2^12, forward then inverse, one stream: the latency
+    of the default one-pass kernel (one CTA per limb) and of the cluster kernel
+    (one limb over a cluster of 8 CTAs), each as two calls and as one
+    ntt_execute call (forward + inverse in one launch for the cluster plan)."""
     w = I.workload_c1()
     host = I.batch_uniform(w.seed, 1, w.primes, w.N)
     d = torch.from_numpy(host.view(np.int64).copy()).cuda()
     ref = d.clone()
     lib = G.lib()
     s = torch.cuda.Stream()
-    with G.Plan(w.N, w.primes) as p:
+    both = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+
+    def timed(p, one_call):
         def step():
-            _ok(G, lib.ntt_forward(p.handle, d.data_ptr(), 1, s.cuda_stream), "C1 forward")
-            _ok(G, lib.ntt_inverse(p.handle, d.data_ptr(), 1, s.cuda_stream), "C1 inverse")
+            if one_call:
+                _ok(G, lib.ntt_execute(p.handle, d.data_ptr(), 1, both, s.cuda_stream), "C1 execute")
+            else:
+                _ok(G, lib.ntt_forward(p.handle, d.data_ptr(), 1, s.cuda_stream), "C1 forward")
+                _ok(G, lib.ntt_inverse(p.handle, d.data_ptr(), 1, s.cuda_stream), "C1 inverse")
         for _ in range(10):
             step()
         torch.cuda.synchronize()
@@ -861,11 +868,44 @@ def single_limb_c1(G, torch, reps=500):
             step()
         e1.record(s)
         torch.cuda.synchronize()
-    if not torch.equal(d, ref):
-        raise RuntimeError("C1 round trip mismatch")
-    us = e0.elapsed_time(e1) * 1e3 / reps
-    return {"workload": "N=2^12, L=1, forward + inverse, one stream", "us_per_step": us,
-            "value": 2 / (us / 1e6), "unit": "limb-NTT/s"}
+        if not torch.equal(d, ref):
+            raise RuntimeError("C1 round trip mismatch")
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    with G.Plan(w.N, w.primes) as p:
+        one_pass = timed(p, False)
+        one_pass_exec = timed(p, True)
+    with G.Plan(w.N, w.primes, G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_CLUSTER) as p:
+        clus = timed(p, False)
+        clus_exec = timed(p, True)
+        # the same one-launch steps replayed from a CUDA graph (no per-launch
+        # submission gaps on the device)
+        K = 100
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(K):
+                _ok(G, lib.ntt_execute(p.handle, d.data_ptr(), 1, both, s.cuda_stream), "C1 execute (capture)")
+        with torch.cuda.stream(s):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        with torch.cuda.stream(s):
+            for _ in range(10):
+                g.replay()
+        e1.record(s)
+        torch.cuda.synchronize()
+        clus_graph = e0.elapsed_time(e1) * 1e3 / (10 * K)
+        if not torch.equal(d, ref):
+            raise RuntimeError("C1 round trip mismatch (graph)")
+    return {"workload": "N=2^12, L=1, forward + inverse, one stream", "us_per_step": one_pass,
+            "value": 2 / (one_pass / 1e6), "unit": "limb-NTT/s",
+            "us_per_step_execute": one_pass_exec,
+            "cluster": {"kernel": "one limb per cluster of 8 CTAs (NTT_KERNEL_CLUSTER)",
+                        "us_per_step": clus, "us_per_step_execute_one_launch": clus_exec,
+                        "us_per_step_execute_graph": clus_graph,
+                        "value": 2 / (min(clus, clus_exec) / 1e6), "unit": "limb-NTT/s"},
+            "timing": f"CUDA events around {reps} back-to-back steps on one stream"}
 
 
 def config_dict(w, args, ws):

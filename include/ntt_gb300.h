@@ -85,8 +85,18 @@ enum {
     NTT_KERNEL_FUSED = 1,
     NTT_KERNEL_PER_PASS = 2,
     NTT_KERNEL_RADIX2 = 3,
-    NTT_KERNEL_HIGH_RADIX = 4
+    NTT_KERNEL_HIGH_RADIX = 4,
+    NTT_KERNEL_CLUSTER = 5
 };
+/* NTT_KERNEL_CLUSTER (N = 2^10 .. 2^12, table twiddles): each limb on a
+ * thread-block cluster of N / 512 CTAs on as many SMs, two passes (floor(n/2)
+ * column stages, then the rest, Sec. VI-C's decomposition) with the
+ * transposition between them through distributed shared memory: one global
+ * read and one write per limb per launch, for the latency of few-limb calls
+ * (a one-pass CTA runs all n stages of its limb on one SM).  ntt_execute with
+ * both operations runs forward and inverse in one launch.  The plan's table
+ * is laid out for these passes.  Results are identical to the other
+ * organisations. */
 
 /* Pass geometries of the two-pass sizes (N >= 2^13, FUSED and PER_PASS):
  * the radix split N = 2^p1 x 2^(n-p1) and the height of the second pass's row

@@ -41,6 +41,7 @@ NTT_KERNEL_FUSED = 1
 NTT_KERNEL_PER_PASS = 2
 NTT_KERNEL_RADIX2 = 3
 NTT_KERNEL_HIGH_RADIX = 4
+NTT_KERNEL_CLUSTER = 5
 
 NTT_GEOMETRY_DEFAULT = 0
 NTT_GEOMETRY_SMALL_ROW_TILE = 1

@@ -25,6 +25,7 @@ namespace ntt {
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd)
 {
     if (c.limbs == 0) return cudaSuccess;
+    if (c.cluster) return launch_cluster(c, fwd);
     if (c.radix2) return launch_radix2(c, fwd);
     if (c.high_radix) return launch_high_radix(c, fwd);
     if (c.n <= (u32)SINGLE_PASS_MAX) return launch_single(c, fwd);
@@ -98,8 +99,12 @@ ntt_status to_status(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? NTT_ERR_OOM : NTT_ERR_CUDA;
 }
 
-// Whether forward + inverse of a plan runs as one launch (fused two-pass plans).
-bool chains(const ntt_plan* p) { return p->passes == 2 && p->kernel == NTT_KERNEL_FUSED; }
+// Whether forward + inverse of a plan runs as one launch (fused two-pass
+// plans and cluster plans).
+bool chains(const ntt_plan* p)
+{
+    return (p->passes == 2 && p->kernel == NTT_KERNEL_FUSED) || p->kernel == NTT_KERNEL_CLUSTER;
+}
 
 // The operations `ops` (NTT_OP_*) on one launch context: forward + inverse as
 // one chained launch where the plan allows it, else one call per direction.

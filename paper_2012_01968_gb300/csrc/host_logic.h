@@ -161,7 +161,8 @@ private:
 // TABLE, 2 OT with ot_stages 1 or 2; geometry 0 .. geometries-1).  Two-pass
 // sizes (n >= 13): every geometry x {FUSED, PER_PASS} x {TABLE, OT1, OT2},
 // then RADIX2 and HIGH_RADIX with table twiddles.  One-pass sizes: the
-// one-pass kernel (kernel 0 = AUTO), RADIX2 and HIGH_RADIX.
+// one-pass kernel (kernel 0 = AUTO), RADIX2 and HIGH_RADIX, and for
+// n = 10 .. 12 the cluster kernel (kernel 5 CLUSTER).
 struct TuneCandidate {
     uint32_t kernel, twiddle_mode, ot_stages, geometry;
 };
@@ -172,6 +173,7 @@ inline std::vector<TuneCandidate> tune_candidates(uint32_t n, uint32_t geometrie
         out.push_back(TuneCandidate{0, 1, 0, 0});
         out.push_back(TuneCandidate{3, 1, 0, 0});
         out.push_back(TuneCandidate{4, 1, 0, 0});
+        if (n >= 10 && n <= 12) out.push_back(TuneCandidate{5, 1, 0, 0});   // the cluster kernel's sizes
         return out;
     }
     for (uint32_t g = 0; g < geometries; ++g)

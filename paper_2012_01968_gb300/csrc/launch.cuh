@@ -101,13 +101,15 @@ cudaError_t launch_pass(const LaunchCtx& c, u32 s0, const Tw* ota, const Tw* otb
     return launch_pass_w<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, u64>(pl, s0, ota, otb);
 }
 
-// Single pass over all n stages (n <= 12): one CTA per limb.
+// Single pass over all n stages (n <= 12): one CTA per limb, with the limb's
+// whole table Psi[0, N) staged in shared memory beside the data (one batched
+// copy before the first round instead of a global read in every stage).
 template <int N_LOG>
 cudaError_t launch_single_n(const LaunchCtx& c, bool fwd)
 {
     if (fwd)
-        return launch_pass<N_LOG, 0, KMAX_ALL, true, true, 1, true, true, 0, false>(c, 0, nullptr, nullptr);
-    return launch_pass<N_LOG, 0, KMAX_ALL, true, false, 1, true, true, 0, false>(c, 0, nullptr, nullptr);
+        return launch_pass<N_LOG, 0, KMAX_ALL, true, true, 1, true, true, 0, true>(c, 0, nullptr, nullptr);
+    return launch_pass<N_LOG, 0, KMAX_ALL, true, false, 1, true, true, 0, true>(c, 0, nullptr, nullptr);
 }
 
 // Two passes: P1 column-like stages [0, P1), then P2 row-like stages.

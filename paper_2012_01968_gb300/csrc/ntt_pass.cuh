@@ -529,6 +529,30 @@ __device__ __forceinline__ uint4 vec_from_smem(const W* sm, u32 w)
     }
 }
 
+// COUNT elements copied by T threads (element i by thread i % T): each thread
+// issues up to 8 loads before the stores that consume them, so a thread's
+// copies cost one memory latency per 8 elements rather than one each.
+template <int T, int COUNT, class V, class LD, class ST>
+__device__ __forceinline__ void batched_copy(const u32 tid, LD ld, ST st)
+{
+    constexpr int PER = (COUNT + T - 1) / T;
+    constexpr int B = PER < 8 ? PER : 8;
+#pragma unroll
+    for (int k0 = 0; k0 < PER; k0 += B) {
+        V v[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const u32 i = tid + (u32)(k0 + k) * T;
+            if (k0 + k < PER && (COUNT % T == 0 || i < (u32)COUNT)) v[k] = ld(i);
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const u32 i = tid + (u32)(k0 + k) * T;
+            if (k0 + k < PER && (COUNT % T == 0 || i < (u32)COUNT)) st(i, v[k]);
+        }
+    }
+}
+
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0,
           int OTS, bool TW_SMEM, class W = u64>
 __global__ void __launch_bounds__(pass_threads(P, LOGC, KMAX))
@@ -572,29 +596,32 @@ ntt_pass_kernel(const PassArgsT<W> a)
         l0 = (tile % per_u) * C;
     }
 
+    // global -> shared, every copy batched (loads in flight before their stores)
     if constexpr (TW_SMEM) {
         const TwT* g = a.tw + (size_t)pi * a.tw_len;
-        for (u32 i = tid; i < (u32)R; i += T) sm_tw[i] = g[i];
+        batched_copy<T, R, TwT>(tid, [&](u32 i) { return g[i]; }, [&](u32 i, const TwT& v) { sm_tw[i] = v; });
     }
     if constexpr (OTS > 0) {
         const TwT* g = a.ota + (size_t)pi * R;
-        for (u32 i = tid; i < (u32)R; i += T) sm_ota[i] = g[i];
+        batched_copy<T, R, TwT>(tid, [&](u32 i) { return g[i]; }, [&](u32 i, const TwT& v) { sm_ota[i] = v; });
     }
-
-    // global -> shared
     if constexpr (VW == 1) {
         const W* src = base + ((size_t)u_base << P);
-        for (u32 i = tid; i < (u32)TILE; i += T) sm[swzw<W>(i)] = src[i];
+        batched_copy<T, TILE, W>(tid, [&](u32 i) { return src[i]; }, [&](u32 i, const W& v) { sm[swzw<W>(i)] = v; });
     } else if constexpr (ROWS) {
         const uint4* src = reinterpret_cast<const uint4*>(base + ((size_t)u_base << P));
-        for (u32 i = tid; i < TILE / VW; i += T) vec_to_smem(sm, VW * i, src[i]);
+        batched_copy<T, TILE / VW, uint4>(tid, [&](u32 i) { return src[i]; },
+                                         [&](u32 i, const uint4& v) { vec_to_smem(sm, VW * i, v); });
     } else {
         constexpr int VPR = C / VW;                   // vectors per row
         const W* blk = base + ((size_t)u_base << nb) + l0;
-        for (u32 i = tid; i < TILE / VW; i += T) {
-            const u32 v = i / VPR, cv = i % VPR;
-            vec_to_smem(sm, v * C + VW * cv, *reinterpret_cast<const uint4*>(blk + ((size_t)v << a.b) + VW * cv));
-        }
+        batched_copy<T, TILE / VW, uint4>(
+            tid,
+            [&](u32 i) {
+                const u32 v = i / VPR, cv = i % VPR;
+                return *reinterpret_cast<const uint4*>(blk + ((size_t)v << a.b) + VW * cv);
+            },
+            [&](u32 i, const uint4& x) { vec_to_smem(sm, (i / VPR) * C + VW * (i % VPR), x); });
     }
     __syncthreads();
 

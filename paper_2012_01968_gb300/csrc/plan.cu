@@ -72,8 +72,10 @@ void build_prime(const ntt_plan& p, uint32_t l, HostTables& h)
     // (natural order, slot 2^s + j, for the radix-2 organisation)
     Tw* tw = h.tw.data() + (size_t)l * p.tw_len;
     tw[0] = make_tw(1, q);
+    const bool cluster = p.kernel == NTT_KERNEL_CLUSTER;
     for (uint32_t s = 0; (1u << s) < p.tw_len; ++s) {
-        const ntt::StageSlot g = ntt::stage_slot_params(n, p.p1, s);
+        const ntt::StageSlot g = cluster ? ntt::stage_slot_params(n, p.p1, s, true, ntt::CLUSTER_TABLE_KMAX)
+                                         : ntt::stage_slot_params(n, p.p1, s);
         for (uint32_t j = 0; j < (1u << s); ++j) {
             const bool natural = p.kernel == NTT_KERNEL_RADIX2 || p.kernel == NTT_KERNEL_HIGH_RADIX;
             const uint32_t slot = natural ? j : ntt::tw_slot(j, g.sl, g.K0, g.k);
@@ -193,7 +195,7 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     if (o.reserved) return NTT_ERR_INVALID_ARG;
     if (o.flags & ~NTT_PLAN_L2_TWIDDLES) return NTT_ERR_INVALID_ARG;
     if (o.twiddle_mode > NTT_TWIDDLE_OT) return NTT_ERR_INVALID_ARG;
-    if (o.kernel > NTT_KERNEL_HIGH_RADIX) return NTT_ERR_INVALID_ARG;
+    if (o.kernel > NTT_KERNEL_CLUSTER) return NTT_ERR_INVALID_ARG;
     const bool high_radix = o.kernel == NTT_KERNEL_HIGH_RADIX;
     if (high_radix ? o.radix_log2 > 5 : o.radix_log2 != 0) return NTT_ERR_INVALID_ARG;
     if (o.geometry >= (uint32_t)ntt::kGeometries) return NTT_ERR_INVALID_ARG;
@@ -201,8 +203,13 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     const uint32_t n = (uint32_t)__builtin_ctz(N);
     const bool two_pass = n > (uint32_t)ntt::SINGLE_PASS_MAX;
     if (o.geometry && (!two_pass || o.kernel == NTT_KERNEL_RADIX2 || high_radix)) return NTT_ERR_INVALID_ARG;
-    const uint32_t p1 = two_pass ? (uint32_t)ntt::geometry_of((int)n, (int)o.geometry).p1
-                                 : (uint32_t)ntt::split_p1((int)n);
+    const bool cluster = o.kernel == NTT_KERNEL_CLUSTER;
+    if (cluster && (n < (uint32_t)ntt::CLUSTER_N_MIN || n > (uint32_t)ntt::CLUSTER_N_MAX ||
+                    o.twiddle_mode == NTT_TWIDDLE_OT || o.ot_stages))
+        return NTT_ERR_INVALID_ARG;
+    const uint32_t p1 = cluster    ? n / 2u
+                        : two_pass ? (uint32_t)ntt::geometry_of((int)n, (int)o.geometry).p1
+                                   : (uint32_t)ntt::split_p1((int)n);
     // AUTO: OT on the last stage for two-pass sizes (measured faster than the
     // table there, and half the last stage's twiddle traffic), table below
     const bool radix2 = o.kernel == NTT_KERNEL_RADIX2 || high_radix;   // global-memory organisations
@@ -233,7 +240,8 @@ extern "C" ntt_status ntt_plan_create(ntt_plan** out, uint32_t N, const uint64_t
     p->passes = two_pass ? 2 : 1;
     p->twiddle_mode = mode;
     p->ot_stages = ots;
-    p->kernel = high_radix                         ? NTT_KERNEL_HIGH_RADIX
+    p->kernel = cluster                            ? NTT_KERNEL_CLUSTER
+                : high_radix                       ? NTT_KERNEL_HIGH_RADIX
                 : radix2                           ? NTT_KERNEL_RADIX2
                 : o.kernel == NTT_KERNEL_PER_PASS ? NTT_KERNEL_PER_PASS
                                                    : NTT_KERNEL_FUSED;
@@ -373,7 +381,7 @@ extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
     info->N = p->N;
     info->L = p->L;
     info->log2_N = p->n;
-    info->passes = p->passes;
+    info->passes = p->kernel == NTT_KERNEL_CLUSTER ? 2u : p->passes;
     info->pass1_log2 = p->p1;
     info->twiddle_mode = p->twiddle_mode;
     info->ot_stages = p->ot_stages;
@@ -381,7 +389,10 @@ extern "C" ntt_status ntt_plan_query(const ntt_plan* p, ntt_plan_info* info)
     info->kernel = p->kernel;
     info->device_bytes = p->device_bytes;
     info->geometry = p->geom;
-    info->row_tile_log2 = p->passes == 2 ? (uint32_t)ntt::geometry_of((int)p->n, (int)p->geom).logc_r : 0;
+    info->row_tile_log2 = p->passes == 2 ? (uint32_t)ntt::geometry_of((int)p->n, (int)p->geom).logc_r
+                          : p->kernel == NTT_KERNEL_CLUSTER
+                              ? p->p1 - (p->n - 9u)      // rows per CTA: 2^p1 rows over N / 512 CTAs
+                              : 0;
     info->radix_log2 = p->radix_log2;
     info->ctas_per_sm = p->ctas_per_sm;
     return NTT_OK;

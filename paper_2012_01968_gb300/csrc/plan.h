@@ -55,12 +55,14 @@ constexpr size_t chain_work_limbs(size_t limbs) { return 3 * limbs + 2; }
 struct StageSlot {
     int sl, K0, k;
 };
-inline StageSlot stage_slot_params(int n, int p1, int s)
+// two_pass: stages [0, p1) form one pass and [p1, n) another (else one pass
+// of n stages); kmax: stages per thread per round of those passes.
+inline StageSlot stage_slot_params(int n, int p1, int s, bool two_pass, int kmax)
 {
-    const int s0 = (n <= SINGLE_PASS_MAX || s < p1) ? 0 : p1;
-    const int P = (n <= SINGLE_PASS_MAX) ? n : (s < p1 ? p1 : n - p1);
+    const int s0 = (!two_pass || s < p1) ? 0 : p1;
+    const int P = !two_pass ? n : (s < p1 ? p1 : n - p1);
     const int sl = s - s0;
-    const int nr = (P + KMAX_ALL - 1) / KMAX_ALL;
+    const int nr = (P + kmax - 1) / kmax;
     int K0 = 0;
     for (int r = 0; r < nr; ++r) {
         const int sz = P / nr + (r < P % nr ? 1 : 0);
@@ -68,6 +70,12 @@ inline StageSlot stage_slot_params(int n, int p1, int s)
         K0 += sz;
     }
     return StageSlot{sl, 0, sl};
+}
+// The layout of the plans' kernels: one pass up to 2^SINGLE_PASS_MAX, else
+// two, with KMAX_ALL stages per round.
+inline StageSlot stage_slot_params(int n, int p1, int s)
+{
+    return stage_slot_params(n, p1, s, n > SINGLE_PASS_MAX, KMAX_ALL);
 }
 
 // Everything a launch needs (device pointers are the plan's).
@@ -104,9 +112,17 @@ struct LaunchCtx {
     // transform in one launch (work area of chain_work_limbs(limbs) limbs)
     u32 chain = 0;
     u32 ctas_per_sm = 0;     // fused kernel: persistent CTAs per SM (0: as many as fit)
+    u32 cluster = 0;         // 1: the cluster kernel (N = 2^10 .. 2^12; its own table layout)
 };
 
 cudaError_t launch_transform(const LaunchCtx& c, bool fwd);
+// One limb per thread-block cluster (ntt_cluster.cuh, k_cluster.cu); with
+// c.chain, forward and then inverse in one launch.
+cudaError_t launch_cluster(const LaunchCtx& c, bool fwd);
+// Table layout and sizes of the cluster kernel: two passes of floor(n/2) and
+// ceil(n/2) stages, 3 stages per thread per round.
+constexpr int CLUSTER_TABLE_KMAX = 3;
+constexpr int CLUSTER_N_MIN = 10, CLUSTER_N_MAX = 12;
 
 // One job of a multi-job fused launch: an array [batch][L][N] and the tables
 // of its plan.
@@ -280,6 +296,7 @@ struct ntt_plan {
         c.max_polls = 0;
         c.geom = geom;
         c.ctas_per_sm = ctas_per_sm;
+        c.cluster = kernel == NTT_KERNEL_CLUSTER ? 1u : 0u;
         const bool win = (flags & NTT_PLAN_L2_TWIDDLES) && l2_hit > 0.f;
         c.l2_base = win ? (const void*)d_tw : nullptr;
         c.l2_bytes = win ? (size_t)L * tw_len * sizeof(ntt::Tw) : 0;

@@ -16,7 +16,7 @@
 extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
 
 static_assert(NTT_KERNEL_AUTO == 0 && NTT_KERNEL_FUSED == 1 && NTT_KERNEL_PER_PASS == 2 && NTT_KERNEL_RADIX2 == 3 &&
-                  NTT_KERNEL_HIGH_RADIX == 4,
+                  NTT_KERNEL_HIGH_RADIX == 4 && NTT_KERNEL_CLUSTER == 5,
               "tune_candidates uses these codes");
 static_assert(NTT_TWIDDLE_TABLE == 1 && NTT_TWIDDLE_OT == 2, "tune_candidates uses these codes");
 

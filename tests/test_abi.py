@@ -60,11 +60,15 @@ BIG = I.prime_chain(3, 1 << 18)
     (1 << 16, BIG[:1], {"twiddle_mode": G.NTT_TWIDDLE_TABLE, "ot_stages": 1}, G.NTT_ERR_INVALID_ARG),
     (1 << 12, BIG[:1], {"reserved": [1]}, G.NTT_ERR_INVALID_ARG),
     (1 << 16, BIG[:1], {"ctas_per_sm": 9}, G.NTT_ERR_INVALID_ARG),             # more CTAs per SM than any fit
+    (1 << 9, BIG[:1], {"kernel": G.NTT_KERNEL_CLUSTER}, G.NTT_ERR_INVALID_ARG),   # below the cluster sizes
+    (1 << 13, BIG[:1], {"kernel": G.NTT_KERNEL_CLUSTER}, G.NTT_ERR_INVALID_ARG),  # above them
+    (1 << 12, BIG[:1], {"kernel": G.NTT_KERNEL_CLUSTER, "twiddle_mode": G.NTT_TWIDDLE_OT},
+     G.NTT_ERR_INVALID_ARG),                                                     # table twiddles only
+    (1 << 12, BIG[:1], {"kernel": 6}, G.NTT_ERR_INVALID_ARG),                  # no such organisation
     (1 << 16, BIG[:1], {"geometry": 3}, G.NTT_ERR_INVALID_ARG),                # no such geometry
     (1 << 12, BIG[:1], {"geometry": 1}, G.NTT_ERR_INVALID_ARG),                # one-pass size
     (1 << 16, BIG[:1], {"geometry": 2, "kernel": G.NTT_KERNEL_RADIX2}, G.NTT_ERR_INVALID_ARG),
     (1 << 16, BIG[:1], {"flags": 2}, G.NTT_ERR_INVALID_ARG),                   # unknown flag bit
-    (1 << 16, BIG[:1], {"kernel": 5}, G.NTT_ERR_INVALID_ARG),                  # no such organisation
     (1 << 16, BIG[:1], {"kernel": G.NTT_KERNEL_HIGH_RADIX, "radix_log2": 6}, G.NTT_ERR_INVALID_ARG),
     (1 << 16, BIG[:1], {"radix_log2": 4}, G.NTT_ERR_INVALID_ARG),              # radix only for HIGH_RADIX
     (1 << 16, BIG[:1], {"kernel": G.NTT_KERNEL_HIGH_RADIX, "twiddle_mode": G.NTT_TWIDDLE_OT}, G.NTT_ERR_INVALID_ARG),

@@ -659,3 +659,55 @@ def test_ctas_per_sm_option(orc, n, ctas):
             assert p.device_status() == 0 and q.device_status() == 0
         finally:
             q.close()
+
+
+@pytest.mark.parametrize("n", [10, 11, 12])
+def test_cluster_organisation(orc, n):
+    """The cluster kernel (one limb per cluster of N / 512 CTAs, the passes'
+    exchange through distributed shared memory): forward and inverse equal the
+    oracle, forward + inverse in one launch restores the input, on several
+    limbs of several primes (prime l % L per limb) and through the levels
+    call (tables viewed from prime 0, fewer limbs per polynomial)."""
+    N = 1 << n
+    primes = I.prime_chain(3, 2 * N)
+    got = _roundtrip_case(orc, N, primes, 4, 300 + n, kernel=G.NTT_KERNEL_CLUSTER)
+    assert np.array_equal(got, _roundtrip_case(orc, N, primes, 4, 300 + n))   # the one-pass kernel agrees
+    data = I.batch_uniform(320 + n, 3, primes, N)
+    with G.Plan(N, primes, G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_CLUSTER) as p:
+        info = p.info()
+        assert info.kernel == G.NTT_KERNEL_CLUSTER and info.passes == 2 and info.pass1_log2 == n // 2
+        d = dev(data)
+        p.execute(d, G.NTT_OP_FORWARD | G.NTT_OP_INVERSE, 3)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), data)
+        p.execute(d, G.NTT_OP_FORWARD, 3)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), oracle_fwd(orc, data, primes))
+        lv = I.batch_uniform(340 + n, 5, primes[:2], N)
+        dl = dev(lv)
+        G.ntt_forward_levels(p.handle, dl, 5, 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(dl).reshape(lv.shape), oracle_fwd(orc, lv, primes[:2]))
+        G.ntt_inverse_levels(p.handle, dl, 5, 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(dl).reshape(lv.shape), lv)
+        assert p.device_status() == 0
+
+
+def test_cluster_many_limbs_and_edges(orc):
+    """More clusters than fit on the GPU at once (several waves), and the edge
+    values 0, 1 and q - 1 in every position."""
+    N = 1 << 12
+    primes = I.prime_chain(2, 2 * N)
+    data = I.batch_uniform(360, 200, primes, N)
+    data[0, 0, :] = 0
+    data[0, 1, :] = primes[1] - 1
+    data[1, 0, ::2] = 1
+    with G.Plan(N, primes, G.NTT_TWIDDLE_TABLE, 0, G.NTT_KERNEL_CLUSTER) as p:
+        d = dev(data)
+        p.forward(d, 200)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), oracle_fwd(orc, data, primes))
+        p.inverse(d, 200)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(d).reshape(data.shape), data)

@@ -108,7 +108,9 @@ def test_autotune_reports_and_picks_the_fastest(orc, n, L, batch):
     N = 1 << n
     primes = I.prime_chain(L, 2 * N)
     best, entries = G.ntt_autotune(N, primes, batch, reps=3)
-    assert len(entries) == (3 if n <= 12 else 20)
+    # one-pass sizes: one-pass, radix-2, high radix (and the cluster kernel
+    # for 2^10 .. 2^12); two-pass sizes: 3 geometries x 6 + radix-2 + high radix
+    assert len(entries) == ((4 if n >= 10 else 3) if n <= 12 else 20)
     assert all(e.status == G.NTT_OK and e.forward_us > 0 and e.inverse_us > 0 for e in entries)
     tot = [e.forward_us + e.inverse_us for e in entries]
     k = int(np.argmin(tot))

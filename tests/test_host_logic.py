@@ -190,7 +190,10 @@ def test_tune_candidates_cover_the_space(run):
         cands = [tuple(int(x) for x in c.split()) for c in line.split(";") if c.strip()]
         assert len(set(cands)) == len(cands)                         # no duplicates
         if n <= 12:
-            assert cands == [(0, 1, 0, 0), (3, 1, 0, 0), (4, 1, 0, 0)]   # one-pass kernel, radix-2, high radix
+            want = [(0, 1, 0, 0), (3, 1, 0, 0), (4, 1, 0, 0)]             # one-pass kernel, radix-2, high radix
+            if n >= 10:
+                want.append((5, 1, 0, 0))                               # and the cluster kernel
+            assert cands == want
             continue
         want = {(k, t, o, g) for g in range(3) for k in (1, 2) for t, o in ((1, 0), (2, 1), (2, 2))}
         want.add((3, 1, 0, 0))                                       # radix-2: table, default geometry
