@@ -80,6 +80,9 @@ def parse():
                     help="the command line that produced the CSV files (recorded in the JSON)")
     ap.add_argument("--int8-probe", action="store_true",
                     help="time the library int8 GEMM (torch._int_mm) against bf16 and print it (tensor-core check)")
+    ap.add_argument("--only", default=None, choices=["c1", "c4"],
+                    help="run one secondary leg alone and print its JSON (for profiling its kernels): "
+                         "c1 = the N=2^12 single-limb latency leg, c4 = the uneven 96-job batch, default plans")
     ap.add_argument("--split-calls", action="store_true",
                     help="each step as two calls (ntt_forward, ntt_inverse) instead of one ntt_execute")
     return ap.parse_args()
@@ -600,7 +603,8 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                     "batch_device_us": {"p50": float(np.percentile(dev_us, 50)),
                                         "p99": float(np.percentile(dev_us, 99))},
                     "max_gap_between_completions_us": float(np.max(np.diff(np.sort(done)))) / 1e3,
-                    "scheduler": {k: (v / 1e3 if k.endswith("_ns") else v) for k, v in sched.items()}}
+                    "scheduler": {(k[:-3] + "_us" if k.endswith("_ns") else k): (v / 1e3 if k.endswith("_ns") else v)
+                                  for k, v in sched.items()}}
 
         cap = run(None)
         out = {"requests": count, "budget_gb": budget_gb, "data": "device-resident, in place",
@@ -619,7 +623,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                 runs[frac][int(np.argsort(p99)[len(p99) // 2])], offered_requests_per_s=frac * cap["requests_per_s"],
                 p99_us_runs=p99, p50_us_runs=[r["latency_us"]["p50"] for r in runs[frac]],
                 p99_max_over_median=max(p99) / med if med > 0 else None)
-        out["scheduler_units"] = "us (counts for batches and requests)"
+        out["scheduler_units"] = "_us keys in microseconds; batches and requests are counts"
         return out
     finally:
         for p in plans.values():
@@ -948,6 +952,13 @@ def main():
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
     G.lib()
+    if args.only:
+        leg = single_limb_c1(G, torch) if args.only == "c1" else batched_c4(G, torch, 10)
+        if rank == 0:
+            print(json.dumps({args.only: leg}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.int8_probe:
         if rank == 0:
             print(json.dumps({"int8_probe": int8_probe(torch)}), flush=True)
