@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--twiddle", default="auto", choices=["auto", "table", "ot1", "ot2"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "per_pass"])
+    ap.add_argument("--geometry", type=int, default=0, choices=[0, 1, 2],
+                    help="pass geometry of the C2 plans when not autotuned (NTT_GEOMETRY_*)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--streams", type=int, default=3,
@@ -64,6 +66,9 @@ def parse():
     ap.add_argument("--ablation-reps", type=int, default=40)
     ap.add_argument("--word-size-only", action="store_true",
                     help="run only the word-size comparison and print it (for profiling its launches)")
+    ap.add_argument("--no-select", action="store_true",
+                    help="build the C2 plans from the autotuner's choice instead of timing the candidate "
+                         "configurations (organisation, twiddles, geometry, streams) in the timed setting")
     ap.add_argument("--no-tune", action="store_true",
                     help="plans with the fixed default options instead of the autotuner's choice")
     ap.add_argument("--serve-requests", type=int, default=20000)
@@ -96,7 +101,7 @@ def dist_env():
 
 
 KERNEL_SOURCES = ("arith.cuh", "device_types.cuh", "ntt_pass.cuh", "tma.cuh", "ntt_fused.cuh",
-                  "launch.cuh", "k_n16.cu")
+                  "launch.cuh", "k_n16.cu", "k_n16_g1.cu", "k_n16_g2.cu")
 
 
 def max_over_ranks(value: float, dist, device) -> float:
@@ -131,11 +136,12 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic(geometry: int, twiddle: str, direction: str):
-    """DRAM traffic of one steady-state launch of the C2 transform kernel
-    (ncu counters, committed under profiles/), for the plan's geometry,
-    twiddle supply and direction, if it was taken on the current kernel
-    sources (else None)."""
+def profile_traffic(kind: str, geometry: int, twiddle: str, direction: str):
+    """DRAM traffic of one steady-state call of the C2 transform (the fused
+    launch, or the per-pass call's column and row launches together; ncu
+    counters, committed under profiles/), for the plan's organisation,
+    geometry, twiddle supply and direction, if it was taken on the current
+    kernel sources (else None)."""
     try:
         with open(TRAFFIC_JSON) as f:
             entries = json.load(f)["entries"]
@@ -143,8 +149,8 @@ def profile_traffic(geometry: int, twiddle: str, direction: str):
         return None
     h = kernel_source_hash()
     for e in entries:
-        if (e.get("geometry"), e.get("twiddle"), e.get("direction"), e.get("source_hash")) == \
-                (geometry, twiddle, direction, h):
+        if (e.get("kind", "fused"), e.get("geometry"), e.get("twiddle"), e.get("direction"),
+                e.get("source_hash")) == (kind, geometry, twiddle, direction, h):
             return e
     return None
 
@@ -186,6 +192,7 @@ def write_traffic_json(out, csvs, command):
     N, L = 1 << 16, 45
     geoms = {(8, 4): 0, (8, 3): 1, (7, 3): 2}
     per = {}
+    passes = {}
     for path in csvs:
         hdr = None
         for r in _csv.reader(open(path)):
@@ -196,6 +203,21 @@ def write_traffic_json(out, csvs, command):
                 continue
             d = dict(zip(hdr, r))
             name = d["Kernel Name"]
+            v = float(d["Metric Value"].replace(",", ""))
+            metric = {"dram__bytes_read.sum": "read", "dram__bytes_write.sum": "write",
+                      "gpu__time_duration.sum": "t"}[d["Metric Name"]]
+            if "ntt_pass_kernel" in name:
+                # P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, W
+                pa = [x.strip() for x in re.search(r"ntt_pass_kernel<([^>]*)>", name).group(1).split(",")]
+                P, logc, rows, fwd, ots = int(pa[0]), int(pa[1]), int(pa[3]) == 1, int(pa[4]), int(pa[8])
+                direction = "forward" if fwd else "inverse"
+                e = passes.setdefault(direction, {"col": {"read": [], "write": [], "t": []},
+                                                  "row": {"read": [], "write": [], "t": []}})
+                part = e["row" if rows else "col"]
+                part[metric].append(v)
+                if rows:
+                    e["p1"], e["logc"], e["ots"] = 16 - P, logc, ots
+                continue
             if "ntt_fused_kernel" not in name:
                 continue
             args = [x.strip() for x in re.search(r"ntt_fused_kernel<([^>]*)>", name).group(1).split(",")]
@@ -205,17 +227,15 @@ def write_traffic_json(out, csvs, command):
                 continue
             key = (geoms.get((p1, lc), -1), "table" if ots == 0 else f"ot{ots}",
                    "forward+inverse" if chain else ("forward" if fwd else "inverse"))
-            v = float(d["Metric Value"].replace(",", ""))
             e = per.setdefault(key, {"kernel": name.split("(")[0].replace("void ", ""), "read": [], "write": [], "t": []})
-            e[{"dram__bytes_read.sum": "read", "dram__bytes_write.sum": "write",
-               "gpu__time_duration.sum": "t"}[d["Metric Name"]]].append(v)
+            e[metric].append(v)
     entries = []
     h = kernel_source_hash()
     for (g, tw, direction), e in sorted(per.items()):
         rd, wr = float(np.mean(e["read"])), float(np.mean(e["write"]))
         transforms = 2 if direction == "forward+inverse" else 1
         data = 8 * N * L                    # one read of the array
-        entries.append({"kernel": e["kernel"], "geometry": g, "twiddle": tw, "direction": direction,
+        entries.append({"kind": "fused", "kernel": e["kernel"], "geometry": g, "twiddle": tw, "direction": direction,
                         "source_hash": h, "launches": len(e["read"]),
                         "dram_read_bytes": rd, "dram_write_bytes": wr, "dram_bytes": rd + wr,
                         "alg_bytes": 16 * N * L * transforms,
@@ -225,6 +245,22 @@ def write_traffic_json(out, csvs, command):
                                "--cache-control none on steady-state launches of the bench's timed loop; writes "
                                "include write-back of lines evicted during the launch; data_read_bytes = one read "
                                "of the array (8 N L), the rest of the reads counted as twiddle reads"})
+    for direction, e in sorted(passes.items()):
+        if "p1" not in e or not e["col"]["read"]:
+            continue
+        rd = float(np.mean(e["col"]["read"])) + float(np.mean(e["row"]["read"]))
+        wr = float(np.mean(e["col"]["write"])) + float(np.mean(e["row"]["write"]))
+        entries.append({"kind": "per_pass", "kernel": "ntt_pass_kernel (column pass) + ntt_pass_kernel (row pass)",
+                        "geometry": geoms.get((e["p1"], e["logc"]), -1),
+                        "twiddle": "table" if e["ots"] == 0 else f"ot{e['ots']}", "direction": direction,
+                        "source_hash": h, "launches": len(e["col"]["read"]) + len(e["row"]["read"]),
+                        "dram_read_bytes": rd, "dram_write_bytes": wr, "dram_bytes": rd + wr,
+                        "alg_bytes": 16 * N * L, "data_read_bytes": min(rd, 8 * N * L),
+                        "twiddle_read_bytes": max(0.0, rd - 8 * N * L),
+                        "duration_us_mean_under_ncu": (float(np.mean(e["col"]["t"])) + float(np.mean(e["row"]["t"]))) / 1e3,
+                        "how": "per call: the mean column-pass launch plus the mean row-pass launch, same counters "
+                               "and cache control as the fused entries; the second pass re-reads the first pass's "
+                               "output, mostly from L2"})
     with open(out, "w") as f:
         json.dump({"workload": "c2_n65536_l45", "command": command, "entries": entries}, f, indent=1)
         f.write("\n")
@@ -912,6 +948,66 @@ def single_limb_c1(G, torch, reps=500):
             "timing": f"CUDA events around {reps} back-to-back steps on one stream"}
 
 
+# Configurations the C2 leg times in its own setting (steps on several streams,
+# plan clones) before the timed region: (organisation, twiddle supply, geometry,
+# persistent CTAs per SM, streams).  The autotuner ranks configurations by one
+# call at a time on one stream; with several streams the ranking changes (the
+# per-pass launches of different streams interleave on the SMs).
+C2_CANDIDATES = (
+    ("fused", "ot1", 0, 1, 3), ("fused", "table", 0, 1, 3), ("fused", "ot1", 0, 0, 2),
+    ("per_pass", "ot1", 1, 0, 2), ("per_pass", "ot2", 1, 0, 2), ("per_pass", "ot2", 1, 0, 3),
+    ("per_pass", "ot1", 0, 0, 2), ("per_pass", "ot2", 0, 0, 2),
+)
+TWIDDLES = {"auto": (0, 0), "table": (1, 0), "ot1": (2, 1), "ot2": (2, 2)}
+
+
+def select_c2(G, torch, N, primes, bufs, steps=400, warmup=20):
+    """Time each C2 candidate configuration as the timed region runs it (the
+    forward + inverse of one polynomial per step, steps spread over the
+    candidate's streams, CUDA events around all steps) and return the fastest
+    with the table of all."""
+    kernels = {"fused": G.NTT_KERNEL_FUSED, "per_pass": G.NTT_KERNEL_PER_PASS}
+    both = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+    lib = G.lib()
+    L = len(primes)
+    rows = []
+    for kname, tw, geom, ctas, S in C2_CANDIDATES:
+        base = G.Plan(N, primes, *TWIDDLES[tw], kernels[kname], geom, ctas_per_sm=ctas)
+        plans = [base] + [base.clone() for _ in range(S - 1)]
+        ss = [torch.cuda.Stream() for _ in range(S)]
+        hs = [p.handle for p in plans]
+
+        def step(i):
+            j = i % S
+            _ok(G, lib.ntt_execute(hs[j], bufs[i % len(bufs)].data_ptr(), 1, both, ss[j].cuda_stream),
+                "candidate step")
+        for i in range(warmup):
+            step(i)
+        torch.cuda.synchronize()
+        cur = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for st in ss:
+            st.wait_event(e0)
+        for i in range(steps):
+            step(i)
+        for st in ss:
+            e = torch.cuda.Event()
+            e.record(st)
+            cur.wait_event(e)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / (2 * steps)
+        ok = all(p.device_status() == 0 for p in plans)
+        for p in reversed(plans):
+            p.close()
+        rows.append({"kernel": kname, "twiddle": tw, "geometry": geom, "ctas_per_sm": ctas, "streams": S,
+                     "us_per_transform": round(us, 2), "value": L / us * 1e6, "ok": ok})
+    best = max((r for r in rows if r["ok"]), key=lambda r: r["value"])
+    return best, {"how": f"{steps} steps of each candidate in the timed region's setting, CUDA events",
+                  "candidates": rows}
+
+
 def config_dict(w, args, ws):
     return {"workload": "c2_n65536_l45_fwd_inv", "N": w.N, "L": len(w.primes), "polys_per_step": 1,
             "primes": "45 largest primes < 2^60 with q = 1 mod 2^17", "seed": w.seed,
@@ -984,22 +1080,34 @@ def main():
     S = max(1, args.streams)
     # one plan (tables + work area) per stream: steps on different streams are
     # independent polynomials and may overlap on the device
-    c2_tune = None
+    c2_tune = c2_select = None
     l2f = G.NTT_PLAN_L2_TWIDDLES if args.l2_twiddles else 0
-    if not args.no_tune and args.twiddle == "auto" and args.kernel == "auto":
+    poly_bytes = N * L * 8
+    nbuf = max(2 * max(S, 3), -(-2 * L2_BYTES // poly_bytes) + 1)
+    host = I.batch_uniform(w.seed, 1, primes, N)
+    src = torch.from_numpy(host.view(np.int64).copy()).cuda()
+    bufs = [src.clone() for _ in range(nbuf)]
+    tuned_run = not args.no_tune and args.twiddle == "auto" and args.kernel == "auto" and args.geometry == 0
+    if tuned_run:
         best, c2_tune = autotune(G, N, primes, 1, reps=20)
+    if tuned_run and not args.no_select and ws == 1:
+        chosen, c2_select = select_c2(G, torch, N, primes, bufs)
+        args.streams = S = chosen["streams"]
+        args.ctas_per_sm = chosen["ctas_per_sm"]
+        kern = {"fused": G.NTT_KERNEL_FUSED, "per_pass": G.NTT_KERNEL_PER_PASS}[chosen["kernel"]]
+        plans = [G.Plan(N, primes, *TWIDDLES[chosen["twiddle"]], kern, chosen["geometry"], flags=l2f,
+                        ctas_per_sm=args.ctas_per_sm)]
+        for b in bufs:
+            if not torch.equal(b, src):
+                raise RuntimeError("round trip mismatch in the configuration selection")
+    elif tuned_run:
         plans = [G.Plan.from_opts(N, primes, best, flags=l2f or None, ctas_per_sm=args.ctas_per_sm)]
     else:
-        plans = [G.Plan(N, primes, *mode, kern, flags=l2f, ctas_per_sm=args.ctas_per_sm)]
+        plans = [G.Plan(N, primes, *mode, kern, args.geometry, flags=l2f, ctas_per_sm=args.ctas_per_sm)]
     # the other streams' plans share the first plan's tables (ntt_plan_clone)
     plans += [plans[0].clone() for _ in range(S - 1)]
     plan = plans[0]
     info = plan.info()
-    poly_bytes = N * L * 8
-    nbuf = max(2 * S, -(-2 * L2_BYTES // poly_bytes) + 1)
-    host = I.batch_uniform(w.seed, 1, primes, N)
-    src = torch.from_numpy(host.view(np.int64).copy()).cuda()
-    bufs = [src.clone() for _ in range(nbuf)]
     streams = [torch.cuda.Stream() for _ in range(S)]
     lib = G.lib()
     handles = [p.handle for p in plans]
@@ -1198,7 +1306,8 @@ def main():
     kname = dom_name if per_launch == 2 else \
         f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})"
     direction = "forward+inverse" if per_launch == 2 else ("forward" if dom_name == "ntt_forward" else "inverse")
-    prof = profile_traffic(int(info.geometry), twname, direction) if info.kernel == G.NTT_KERNEL_FUSED else None
+    kind = {G.NTT_KERNEL_FUSED: "fused", G.NTT_KERNEL_PER_PASS: "per_pass"}.get(int(info.kernel))
+    prof = profile_traffic(kind, int(info.geometry), twname, direction) if kind else None
     traffic = prof["dram_bytes"] if prof else None
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": K,
@@ -1213,8 +1322,11 @@ def main():
                                               "twiddle_read_bytes", "how") if k in prof},
                      "kernel": kname,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
-                     "units_per_launch": f"{per_launch * L} limb-NTTs of N={N} (16 N bytes each: one read, one write)",
-                     "launch_timing": f"CUDA events around each of {Kp} launches on one stream (a clone of the timed plan with as many CTAs per SM as fit)",
+                     "units_per_launch": f"{per_launch * L} limb-NTTs of N={N} (16 N bytes each: one read, one write)"
+                                         + ("" if info.kernel == G.NTT_KERNEL_FUSED else
+                                            f"; per call of {int(info.passes)} pass launches"),
+                     "launch_timing": f"CUDA events around each of {Kp} calls on one stream (a clone of the timed plan"
+                                      " with as many CTAs per SM as fit)",
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src},
         "roofline_alu": {"bound": "alu", "achieved": bfly_achieved, "peak": alu_peak_gbfly(),
                          "unit": "G butterfly/s", "frac": bfly_achieved / alu_peak_gbfly(),
@@ -1236,8 +1348,10 @@ def main():
                  "passes": int(info.passes), "pass1_log2": int(info.pass1_log2),
                  "row_tile_log2": int(info.row_tile_log2), "geometry": int(info.geometry),
                  "kernel": KERNEL_NAMES[int(info.kernel)],
-                 "chosen_by": "ntt_autotune" if c2_tune else "fixed options"},
+                 "chosen_by": ("timed candidates in the timed setting (select_c2)" if c2_select else
+                               "ntt_autotune" if c2_tune else "fixed options")},
         "autotune_c2": c2_tune,
+        "select_c2": c2_select,
         "e2e": e2e,
         "per_limb_path": per_limb,
         "batched_uneven_c4": batched,

@@ -62,3 +62,11 @@ def test_gpu_arm_line():
     else:
         assert d["gpu_launches"] == 2 * d["plan"]["passes"] * d["steps"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+    # the timed configuration is the fastest of the candidates timed in the same setting
+    sel = d["select_c2"]
+    assert d["plan"]["chosen_by"].startswith("timed candidates")
+    rows = sel["candidates"]
+    assert len(rows) >= 2 and all(r["ok"] for r in rows)
+    best = max(rows, key=lambda r: r["value"])
+    assert d["config"]["streams"] == best["streams"] and d["config"]["ctas_per_sm"] == best["ctas_per_sm"]
+    assert d["plan"]["kernel"] == best["kernel"] and d["plan"]["geometry"] == best["geometry"]
