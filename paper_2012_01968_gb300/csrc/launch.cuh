@@ -59,7 +59,7 @@ cudaError_t launch_pass_w(const PassLaunch<W>& c, u32 s0, const typename WordTyp
                           const typename WordTypes<W>::Tw* otb)
 {
     auto kern = ntt_pass_kernel<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, W>;
-    constexpr size_t smem = pass_smem_bytes<P, LOGC, KMAX, TW_SMEM, OTS, W>();
+    constexpr size_t smem = pass_smem_bytes<P, LOGC, KMAX, ROWS, HAS_S0, TW_SMEM, OTS, W>();
     constexpr int T = pass_threads(P, LOGC, KMAX);
     if (smem > 48 * 1024) {
         static std::once_flag once;

@@ -323,7 +323,7 @@ ntt_fused_kernel(const __grid_constant__ FusedParams<MAXJ, W> a)
         };
         // row tiles loaded whose staged twiddles are still to be copied into
         // htw (unit numbers, in load order), and the copies issued so far
-        u32 hq[NBUF > 1 ? NBUF : 1];
+        u32 hq[NBUF > 1 ? NBUF : 1] = {};
         u32 hq_head = 0, hq_tail = 0, fills = 0;
         (void)hq;
         auto fill_htw = [&]() -> bool {

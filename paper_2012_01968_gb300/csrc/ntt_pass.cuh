@@ -529,6 +529,31 @@ __device__ __forceinline__ uint4 vec_from_smem(const W* sm, u32 w)
     }
 }
 
+// 16-byte global -> shared copy that does not pass through registers
+// (cp.async, cached in L2 only), and the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((u32)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Whether a second-pass row tile of the per-pass kernel stages its twiddles
+// in shared memory (all table runs of its rows and the OT factors, the
+// layout of RowStaging with STAGE 2), so that its rounds read no twiddle
+// from global memory: 64-bit words, two rounds or more, and at most 80 KB
+// of shared memory with the tile (two or more CTAs per SM).
+template <int P, int LOGC, int KMAX, bool ROWS, bool HAS_S0, int OTS, class W>
+__host__ __device__ constexpr bool pass_stages_rows()
+{
+    return ROWS && !HAS_S0 && sizeof(W) == 8 && nrounds(P, KMAX) >= 2 &&
+           (size_t)(1 << (P + LOGC)) * 8 + (size_t)RowStaging<P, 1 << LOGC, KMAX, OTS, 2>::NH * 16 <= 80 * 1024;
+}
+
+// Resident CTAs per SM the pass kernel's registers are sized for: 768
+// threads (24 warps; at most 85 registers per thread).
+__host__ __device__ constexpr int pass_min_blocks(int threads) { return threads <= 384 ? 768 / threads : 1; }
+
 // COUNT elements copied by T threads (element i by thread i % T): each thread
 // issues up to 8 loads before the stores that consume them, so a thread's
 // copies cost one memory latency per 8 elements rather than one each.
@@ -555,7 +580,7 @@ __device__ __forceinline__ void batched_copy(const u32 tid, LD ld, ST st)
 
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0,
           int OTS, bool TW_SMEM, class W = u64>
-__global__ void __launch_bounds__(pass_threads(P, LOGC, KMAX))
+__global__ void __launch_bounds__(pass_threads(P, LOGC, KMAX), pass_min_blocks(pass_threads(P, LOGC, KMAX)))
 ntt_pass_kernel(const PassArgsT<W> a)
 {
     using TwT = typename WordTypes<W>::Tw;
@@ -576,6 +601,11 @@ ntt_pass_kernel(const PassArgsT<W> a)
     // the tile is a multiple of 16 bytes or is at most 8 bytes; round up for the tables
     TwT* sm_tw = reinterpret_cast<TwT*>(smem_pass + (TILE * sizeof(W) + 15) / 16 * 2);   // 2^P entries
     TwT* sm_ota = sm_tw + (TW_SMEM ? R : 0);                                            // 2^P entries
+    // second-pass row tiles: the tile's table runs and OT factors (RowStaging
+    // layout, STAGE 2) in place of sm_ota
+    constexpr bool SR = pass_stages_rows<P, LOGC, KMAX, ROWS, HAS_S0, OTS, W>();
+    using RS = RowStaging<P, C, KMAX, OTS, 2>;
+    TwT* const htw = sm_ota;
 
     const u32 tid = threadIdx.x;
     const u32 tile = blockIdx.x;
@@ -596,6 +626,56 @@ ntt_pass_kernel(const PassArgsT<W> a)
         l0 = (tile % per_u) * C;
     }
 
+    if constexpr (sizeof(W) == 8 && VW == 2) {
+        // global -> shared: every 16-byte piece by cp.async, all in flight
+        // at once, then one wait (a tile's swizzle keeps word pairs together)
+        if constexpr (TW_SMEM) {
+            const TwT* g = a.tw + (size_t)pi * a.tw_len;
+#pragma unroll 1
+            for (u32 i = tid; i < (u32)R; i += T) cp_async16(&sm_tw[i], &g[i]);
+        }
+        if constexpr (SR) {
+            // stage sl's run for rows [u_base, u_base + C): C << sl entries at
+            // offset C (2^sl - 1), ascending (forward) or the mirrored run
+            // the inverse reads; then the A factors of the OT stages and one
+            // B factor per row and OT stage
+            const TwT* tb = a.tw + (size_t)pi * a.tw_len;
+#pragma unroll 1
+            for (u32 e = tid; e < (u32)RS::NT_H; e += T) {
+                const u32 sl = 31u - (u32)__clz((int)(e / (u32)C + 1u));
+                const u32 i = e - (u32)C * ((1u << sl) - 1u);
+                const u32 st = FWD ? (1u << (a.s0 + sl)) + (u_base << sl)
+                                   : (2u << (a.s0 + sl)) - ((u_base + (u32)C) << sl);
+                cp_async16(&htw[e], &tb[st + i]);
+            }
+            if constexpr (OTS > 0) {
+                const TwT* ga = a.ota + (size_t)pi * R + (1u << (P - OTS));
+                for (u32 i = tid; i < (u32)RS::NA; i += T) cp_async16(&htw[RS::A_OFF + i], &ga[i]);
+                const TwT* gb = a.otb + (size_t)pi * ((size_t)P << a.s0);
+                for (u32 e = tid; e < (u32)RS::NB; e += T) {
+                    const u32 k = e / (u32)C, r = e % (u32)C;
+                    cp_async16(&htw[RS::B_OFF + e], &gb[((size_t)(P - OTS + k) << a.s0) + u_base + r]);
+                }
+            }
+        } else if constexpr (OTS > 0) {
+            const TwT* g = a.ota + (size_t)pi * R;
+            for (u32 i = tid; i < (u32)R; i += T) cp_async16(&sm_ota[i], &g[i]);
+        }
+        if constexpr (ROWS) {
+            const W* src = base + ((size_t)u_base << P);
+#pragma unroll 1
+            for (u32 i = tid; i < (u32)(TILE / 2); i += T) cp_async16(sm + swz(2u * i), src + 2u * i);
+        } else {
+            constexpr int VPR = C / 2;                    // vectors per row
+            const W* blk = base + ((size_t)u_base << nb) + l0;
+#pragma unroll 1
+            for (u32 i = tid; i < (u32)(TILE / 2); i += T) {
+                const u32 v = i / VPR, cv = i % VPR;
+                cp_async16(sm + swz(v * C + 2u * cv), blk + ((size_t)v << a.b) + 2u * cv);
+            }
+        }
+        cp_async_wait_all();
+    } else {
     // global -> shared, every copy batched (loads in flight before their stores)
     if constexpr (TW_SMEM) {
         const TwT* g = a.tw + (size_t)pi * a.tw_len;
@@ -623,11 +703,17 @@ ntt_pass_kernel(const PassArgsT<W> a)
             },
             [&](u32 i, const uint4& x) { vec_to_smem(sm, (i / VPR) * C + VW * (i % VPR), x); });
     }
+    }
     __syncthreads();
 
-    compute_tile<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, T>(
-        sm, pr, TW_SMEM ? sm_tw : a.tw + (size_t)pi * a.tw_len, sm_ota,
-        a.otb ? a.otb + (size_t)pi * ((size_t)P << a.s0) : nullptr, u_base, a.s0, tid);
+    if constexpr (SR)
+        compute_tile<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, false, T, NoHook, false, false, W, 2,
+                     rows_stay_in_warp<P, LOGC, KMAX, T>()>(sm, pr, htw, nullptr, nullptr, u_base, a.s0, tid,
+                                                            NoHook(), htw);
+    else
+        compute_tile<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, T>(
+            sm, pr, TW_SMEM ? sm_tw : a.tw + (size_t)pi * a.tw_len, sm_ota,
+            a.otb ? a.otb + (size_t)pi * ((size_t)P << a.s0) : nullptr, u_base, a.s0, tid);
     __syncthreads();
 
     // shared -> global
@@ -647,12 +733,15 @@ ntt_pass_kernel(const PassArgsT<W> a)
     }
 }
 
-template <int P, int LOGC, int KMAX, bool TW_SMEM, int OTS, class W = u64>
+template <int P, int LOGC, int KMAX, bool ROWS, bool HAS_S0, bool TW_SMEM, int OTS, class W = u64>
 __host__ __device__ constexpr size_t pass_smem_bytes()
 {
     constexpr size_t tw = sizeof(typename WordTypes<W>::Tw);
-    return ((size_t)(1 << (P + LOGC)) * sizeof(W) + 15) / 16 * 16 + (TW_SMEM ? (size_t)(1 << P) * tw : 0) +
-           (OTS > 0 ? (size_t)(1 << P) * tw : 0);
+    constexpr size_t base = ((size_t)(1 << (P + LOGC)) * sizeof(W) + 15) / 16 * 16 + (TW_SMEM ? (size_t)(1 << P) * tw : 0);
+    if constexpr (pass_stages_rows<P, LOGC, KMAX, ROWS, HAS_S0, OTS, W>())
+        return base + (size_t)RowStaging<P, 1 << LOGC, KMAX, OTS, 2>::NH * tw;
+    else
+        return base + (OTS > 0 ? (size_t)(1 << P) * tw : 0);
 }
 
 }  // namespace ntt
