@@ -501,14 +501,16 @@ def per_limb_c2(G, torch, w, host, steps):
             p.close()
 
 
-def batched_c4(G, torch, reps, tuned=None):
+def batched_c4(G, torch, reps, tuned=None, plan_kw=None):
     """The uneven 96-job workload (N in 2^14..2^17, L in [1, 60], mixed
     directions): one ntt_batch_submit, its CUDA-graph replay, and the same
     jobs as 96 single calls on one stream.  `tuned` maps log2 N to plan
-    options (the autotuner's); None: the default options."""
+    options (the autotuner's); `plan_kw`: the same plan options for every
+    size; neither: the default options (one mixed-size launch per
+    submission)."""
     w = I.workload_c4()
     chain = I.chain_2_18_60()
-    plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain))
+    plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain, **(plan_kw or {})))
              for n in range(14, 18)}
     lib = G.lib()
     try:
@@ -542,6 +544,7 @@ def batched_c4(G, torch, reps, tuned=None):
 
         with G.Batch() as b:
             out["batched"] = timed(lambda: b.submit(jobs, s))
+            out["launches_per_submission"] = batch_last_launches(G, b)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
                 b.submit(jobs, s)
@@ -558,6 +561,16 @@ def batched_c4(G, torch, reps, tuned=None):
     finally:
         for p in plans.values():
             p.close()
+
+
+def batch_last_launches(G, b):
+    """Kernel launches the batch's last submission made (library test hook)."""
+    import ctypes
+    f = G.lib().ntt_internal_batch_last_launches
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]
+    n = ctypes.c_uint32()
+    return int(n.value) if f(b.handle, ctypes.byref(n)) == 0 else None
 
 
 def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jobs=64, slots=3,
@@ -1202,9 +1215,15 @@ def main():
     chain_avg = float(np.mean(chain_ms))
     chained = info.kernel == G.NTT_KERNEL_FUSED and info.passes == 2
     bfly_per_transform = L * (N // 2) * (N.bit_length() - 1)      # (N/2) log2 N butterflies per limb
+    per_pass_step = info.kernel == G.NTT_KERNEL_PER_PASS and info.passes == 2 and not args.split_calls
     if chained and not args.split_calls:
         # the timed steps' launch: forward + inverse of the polynomial
         dom_name, dom_ms, per_launch = "ntt_execute (forward + inverse, 1 fused launch)", chain_avg, 2
+    elif per_pass_step:
+        # the timed steps' call: forward + inverse as four pass launches (the
+        # inverse's passes read the forward's output, mostly from L2, so the
+        # unit is the whole call)
+        dom_name, dom_ms, per_launch = "ntt_execute (forward + inverse, 4 pass launches)", chain_avg, 2
     else:
         dom_name, dom_ms = ("ntt_forward", fwd_avg) if fwd_avg >= inv_avg else ("ntt_inverse", inv_avg)
         per_launch = 1
@@ -1267,6 +1286,11 @@ def main():
         if tuned:
             batched["autotuned"] = batched_c4(G, torch, 10, {n: t[0] for n, t in tuned.items()})
             batched["autotune"] = {f"N=2^{n}": t[1] for n, t in tuned.items()}
+        # every size on the per-pass organisation (OT2, smaller row tiles): the
+        # jobs' pass launches interleave on the batch's internal streams
+        batched["per_pass_plans"] = batched_c4(G, torch, 10, plan_kw={
+            "twiddle_mode": G.NTT_TWIDDLE_OT, "ot_stages": 2, "kernel": G.NTT_KERNEL_PER_PASS,
+            "geometry": G.NTT_GEOMETRY_SMALL_ROW_TILE})
     large = modes = c1 = words = None
     if ws == 1 and not args.no_batch_compare:
         w3 = I.workload_c3()
@@ -1307,7 +1331,17 @@ def main():
         f"{dom_name} ({'1 fused launch' if info.kernel == G.NTT_KERNEL_FUSED else str(info.passes) + ' pass launches'})"
     direction = "forward+inverse" if per_launch == 2 else ("forward" if dom_name == "ntt_forward" else "inverse")
     kind = {G.NTT_KERNEL_FUSED: "fused", G.NTT_KERNEL_PER_PASS: "per_pass"}.get(int(info.kernel))
-    prof = profile_traffic(kind, int(info.geometry), twname, direction) if kind else None
+    if per_pass_step:
+        # the forward call's and the inverse call's entries together
+        pf = profile_traffic(kind, int(info.geometry), twname, "forward")
+        pv = profile_traffic(kind, int(info.geometry), twname, "inverse")
+        prof = None if not (pf and pv) else {
+            k: pf[k] + pv[k] for k in ("dram_read_bytes", "dram_write_bytes", "dram_bytes", "twiddle_read_bytes")}
+        if prof:
+            prof["data_read_bytes"] = prof["dram_read_bytes"] - prof["twiddle_read_bytes"]
+            prof["how"] = pf["how"] + "; the step's forward call and inverse call summed"
+    else:
+        prof = profile_traffic(kind, int(info.geometry), twname, direction) if kind else None
     traffic = prof["dram_bytes"] if prof else None
     line = {
         "metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": K,
@@ -1324,6 +1358,7 @@ def main():
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_us": dom_ms * 1e3,
                      "units_per_launch": f"{per_launch * L} limb-NTTs of N={N} (16 N bytes each: one read, one write)"
                                          + ("" if info.kernel == G.NTT_KERNEL_FUSED else
+                                            "; one ntt_execute call of 4 pass launches" if per_pass_step else
                                             f"; per call of {int(info.passes)} pass launches"),
                      "launch_timing": f"CUDA events around each of {Kp} calls on one stream (a clone of the timed plan"
                                       " with as many CTAs per SM as fit)",
