@@ -563,6 +563,14 @@ def batched_c4(G, torch, reps, tuned=None, plan_kw=None):
             p.close()
 
 
+def PER_PASS_KW(G):
+    """Plan options of the per-pass variants of the batch and serving legs:
+    the per-pass organisation, OT on the last two stages, row tiles of half
+    height (measured fastest for the C4 mix in that organisation)."""
+    return {"twiddle_mode": G.NTT_TWIDDLE_OT, "ot_stages": 2, "kernel": G.NTT_KERNEL_PER_PASS,
+            "geometry": G.NTT_GEOMETRY_SMALL_ROW_TILE}
+
+
 def batch_last_launches(G, b):
     """Kernel launches the batch's last submission made (library test hook)."""
     import ctypes
@@ -574,7 +582,7 @@ def batch_last_launches(G, b):
 
 
 def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jobs=64, slots=3,
-             loads=(0.5, 0.8, 0.95), repeats=5):
+             loads=(0.5, 0.8, 0.95), repeats=5, plan_kw=None):
     """The serving workload: `count` requests (N in 2^15..2^17, L in [4, 60],
     mixed directions) on device-resident data, admitted by an HBM budget.
     A capacity run (every request submitted at once), then Poisson arrivals at
@@ -584,7 +592,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
     load reports its median run with the p99 of every run."""
     import collections
     chain = I.chain_2_18_60()
-    plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain))
+    plans = {n: (G.Plan.from_opts(1 << n, chain, tuned[n]) if tuned else G.Plan(1 << n, chain, **(plan_kw or {})))
              for n in (15, 16, 17)}
     word = 8
     ring_words = (ring_gb << 30) // word
@@ -1288,9 +1296,7 @@ def main():
             batched["autotune"] = {f"N=2^{n}": t[1] for n, t in tuned.items()}
         # every size on the per-pass organisation (OT2, smaller row tiles): the
         # jobs' pass launches interleave on the batch's internal streams
-        batched["per_pass_plans"] = batched_c4(G, torch, 10, plan_kw={
-            "twiddle_mode": G.NTT_TWIDDLE_OT, "ot_stages": 2, "kernel": G.NTT_KERNEL_PER_PASS,
-            "geometry": G.NTT_GEOMETRY_SMALL_ROW_TILE})
+        batched["per_pass_plans"] = batched_c4(G, torch, 10, plan_kw=PER_PASS_KW(G))
     large = modes = c1 = words = None
     if ws == 1 and not args.no_batch_compare:
         w3 = I.workload_c3()
@@ -1311,6 +1317,11 @@ def main():
         if tuned:
             served["autotuned"] = serve_c5(G, torch, args.serve_requests,
                                            tuned={n: t[0] for n, t in tuned.items()})
+        # every size on per-pass plans: a served batch's jobs then run as pass
+        # launches interleaved on the batch's internal streams (capacity and
+        # one 50% run)
+        served["per_pass_plans"] = serve_c5(G, torch, args.serve_requests, loads=(0.5,), repeats=1,
+                                            plan_kw=PER_PASS_KW(G))
 
     if rank != 0:
         if dist is not None:
