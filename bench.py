@@ -679,6 +679,10 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
             out[f"poisson_{int(frac * 100)}pct"] = dict(
                 runs[frac][int(np.argsort(p99)[len(p99) // 2])], offered_requests_per_s=frac * cap["requests_per_s"],
                 p99_us_runs=p99, p50_us_runs=[r["latency_us"]["p50"] for r in runs[frac]],
+                requests_per_batch_runs=[r["scheduler"]["requests"] / max(1, r["scheduler"]["batches"])
+                                         for r in runs[frac]],
+                max_completion_gap_us_runs=[r["scheduler"]["max_completion_gap_us"] for r in runs[frac]],
+                max_launch_us_runs=[r["scheduler"]["max_launch_us"] for r in runs[frac]],
                 p99_max_over_median=max(p99) / med if med > 0 else None)
         out["scheduler_units"] = "_us keys in microseconds; batches and requests are counts"
         return out
@@ -1318,10 +1322,9 @@ def main():
             served["autotuned"] = serve_c5(G, torch, args.serve_requests,
                                            tuned={n: t[0] for n, t in tuned.items()})
         # every size on per-pass plans: a served batch's jobs then run as pass
-        # launches interleaved on the batch's internal streams (capacity and
-        # one 50% run)
-        served["per_pass_plans"] = serve_c5(G, torch, args.serve_requests, loads=(0.5,), repeats=1,
-                                            plan_kw=PER_PASS_KW(G))
+        # launches interleaved on the batch's internal streams (capacity, and
+        # the three loads three times)
+        served["per_pass_plans"] = serve_c5(G, torch, args.serve_requests, repeats=3, plan_kw=PER_PASS_KW(G))
 
     if rank != 0:
         if dist is not None:

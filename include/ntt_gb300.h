@@ -345,20 +345,25 @@ ntt_status ntt_transform_noalloc(const ntt_plan* plan, uint64_t* data, uint32_t 
  * forked from and joined back to `stream`; the whole submission is ordered
  * on `stream` like a single call.  Results equal those of
  * ntt_forward_levels / ntt_inverse_levels on each job.  The mixed launch's job
- * descriptors (tensor maps and tables) are uploaded when they differ from the
- * previous submission's; a submission repeated on the same arrays (or replayed
- * from a captured graph) reuses them.
+ * descriptors (tensor maps and tables) are uploaded on `stream` when they
+ * differ from the previous submission's, into the next of four descriptor
+ * generations; a submission repeated on the same arrays (or replayed from a
+ * captured graph) reuses the latest generation.  The host waits only when a
+ * generation is reused while the submission that last used it is still
+ * running (four submissions with different descriptors in flight): the call
+ * does not drain `stream`.
  *
  * Ownership and concurrency: the caller keeps its plans and arrays alive until
  * the work has finished; arrays of one submission must not overlap (rejected).
  * The batch object owns internal streams, a work area and the descriptor
  * arrays; calls on one batch object must not overlap in time.  The work area
  * grows when a submission needs more (a device synchronisation and an
- * allocation), and a submission whose descriptors changed uploads them (it
- * waits for the previous upload), so make one eager submission of the same
- * jobs before capturing a submission into a CUDA graph, and submit no other
- * jobs on that batch object while the graph is in use.  Must run with the
- * batch's device current.
+ * allocation), and a submission whose descriptors changed uploads them, which
+ * a capture refuses; so make one eager submission of the same jobs before
+ * capturing a submission into a CUDA graph.  The graph reads that
+ * generation's descriptors: while it is in use, submit at most three other
+ * sets of jobs on that batch object.  Must run with the batch's device
+ * current.
  */
 typedef struct ntt_batch ntt_batch;
 

@@ -150,6 +150,30 @@ __host__ __device__ constexpr int gs_range_after(int X, int stages)
     return stages == 0 ? X : gs_range_after(gs_next(X), stages - 1);
 }
 
+// Bound of one slot in a round of GS stages held in registers, smallest
+// stride first.  The round's stage b pairs the slots that differ in bit b of
+// the slot index, so after stages 0 .. b-1 a slot's bound depends only on its
+// bits below b: a 1 made it a product output (below 4q), a 0 a sum (twice the
+// bound, brought back below 8q when that would pass 8q).  The two slots of a
+// pair therefore share the bound gs_slot_bound(X, b, i) (i: the bits below b,
+// X: the round's input bound), and only a sum of two values that may exceed 4q
+// needs the subtraction: 20 of the 32 that the uniform bound gs_next spends
+// on a radix-16 round from 8q.  Never above gs_range_after(X, b).
+__host__ __device__ constexpr int gs_slot_bound(int X, int b, int i)
+{
+    for (int j = 0; j < b; ++j) X = ((i >> j) & 1) ? 4 : (gs_reduces(X) ? 8 : 2 * X);
+    return X;
+}
+__host__ __device__ constexpr bool gs_slot_bounds_hold()
+{
+    for (int X = 1; X <= 8; ++X)
+        for (int b = 0; b <= 6; ++b)
+            for (int i = 0; i < (1 << b); ++i)
+                if (gs_slot_bound(X, b, i) > 8 || gs_slot_bound(X, b, i) > gs_range_after(X, b)) return false;
+    return true;
+}
+static_assert(gs_slot_bounds_hold(), "per-slot GS bounds within the uniform ones");
+
 // NEG: twiddle stored as -w (the forward table read backwards), so the
 // difference is taken as y - x.
 template <int X, bool NEG>

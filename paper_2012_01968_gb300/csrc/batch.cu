@@ -22,6 +22,11 @@ extern "C" void ntt_internal_set_cuda_error(cudaError_t e);
 
 namespace {
 constexpr int kStreams = 4;
+// descriptor generations of the mixed launches: a submission whose
+// descriptors differ from the latest stages them in the next generation, so
+// that up to this many submissions with different descriptors can be in
+// flight before the host waits for the oldest
+constexpr int kMixGenerations = 4;
 }
 
 struct ntt_batch {
@@ -33,11 +38,18 @@ struct ntt_batch {
     size_t work_words = 0;
     uint32_t* d_status = nullptr;
     uint32_t test_stall_polls = 0;  // test hook: the next submission's fused launches stall (bounded)
-    // job descriptors of the mixed-size launches (device array and its
-    // page-locked host copy, equal at all times; both start zeroed)
+    // job descriptors of the mixed-size launches: kMixGenerations device
+    // arrays of mix_cap descriptors and their page-locked host copies (each
+    // host copy equals what its upload wrote)
     void* d_mix = nullptr;
     void* h_mix = nullptr;
-    size_t mix_cap = 0;             // jobs
+    size_t mix_cap = 0;             // jobs per generation
+    int mix_gen = 0;                // generation holding the latest descriptors
+    size_t mix_bytes = 0;           // their size (0: none yet)
+    // recorded on the caller's stream after the latest submission that used
+    // a generation (its upload and its launches are then done)
+    cudaEvent_t mix_done[kMixGenerations] = {};
+    bool mix_used[kMixGenerations] = {};
     uint32_t last_launches = 0;     // kernel launches of the latest submission
     std::mutex mu;
 };
@@ -65,6 +77,8 @@ void release(ntt_batch* b)
         if (b->s[k]) cudaStreamDestroy(b->s[k]);
         if (b->join[k]) cudaEventDestroy(b->join[k]);
     }
+    for (int g = 0; g < kMixGenerations; ++g)
+        if (b->mix_done[g]) cudaEventDestroy(b->mix_done[g]);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_work) {
         cudaFreeAsync(b->d_work, nullptr);
@@ -106,9 +120,9 @@ cudaError_t grow_work(ntt_batch* b, size_t words, cudaStream_t caller)
     return e;
 }
 
-// Room for `jobs` mixed-launch descriptors (device and host copies, zeroed).
-// Growing drains the batch's streams first (an earlier launch may still read
-// the old arrays); not during graph capture.
+// Room for `jobs` mixed-launch descriptors per generation (device and host
+// copies).  Growing drains the batch's streams first (an earlier launch may
+// still read the old arrays); not during graph capture.
 cudaError_t reserve_mix(ntt_batch* b, size_t jobs, cudaStream_t caller)
 {
     if (jobs <= b->mix_cap) return cudaSuccess;
@@ -122,7 +136,9 @@ cudaError_t reserve_mix(ntt_batch* b, size_t jobs, cudaStream_t caller)
     cudaFreeHost(b->h_mix);
     b->d_mix = b->h_mix = nullptr;
     b->mix_cap = 0;
-    const size_t cap = std::max<size_t>(jobs, 128), bytes = cap * ntt::mixed_job_bytes();
+    b->mix_bytes = 0;
+    for (bool& u : b->mix_used) u = false;
+    const size_t cap = std::max<size_t>(jobs, 128), bytes = kMixGenerations * cap * ntt::mixed_job_bytes();
     e = cudaMalloc(&b->d_mix, bytes);
     if (e == cudaSuccess) e = cudaMemset(b->d_mix, 0, bytes);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_mix, bytes, cudaHostAllocDefault);
@@ -152,6 +168,8 @@ ntt_status ntt_batch_create(ntt_batch** out)
         e = cudaStreamCreateWithFlags(&b->s[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
     }
+    for (int g = 0; g < kMixGenerations && e == cudaSuccess; ++g)
+        e = cudaEventCreateWithFlags(&b->mix_done[g], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(uint32_t));
@@ -272,6 +290,39 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
         }
     }
 
+    // the mixed launches' descriptors: unchanged since the latest submission
+    // (e.g. a submission replayed from a CUDA graph), or staged in the next
+    // generation and uploaded on the caller's stream before the fork
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    {
+        cudaError_t e = cudaStreamIsCapturing(caller, &capture);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    std::vector<ntt::MixBuilt> built(mixin.size());
+    std::vector<unsigned char> descs;
+    for (size_t mi = 0; mi < mixin.size(); ++mi) {
+        cudaError_t e = ntt::build_mixed(mixin[mi].data(), (uint32_t)mixin[mi].size(), mix_ots[mi], &built[mi]);
+        if (e != cudaSuccess) return cuda_status(e);
+        descs.insert(descs.end(), built[mi].desc.begin(), built[mi].desc.end());
+    }
+    const size_t gen_bytes = b->mix_cap * ntt::mixed_job_bytes();
+    auto gen_host = [&](int g) { return static_cast<unsigned char*>(b->h_mix) + (size_t)g * gen_bytes; };
+    auto gen_dev = [&](int g) { return static_cast<unsigned char*>(b->d_mix) + (size_t)g * gen_bytes; };
+    if (!mixin.empty() && !(descs.size() == b->mix_bytes &&
+                            std::memcmp(gen_host(b->mix_gen), descs.data(), descs.size()) == 0)) {
+        if (capture != cudaStreamCaptureStatusNone) return cuda_status(cudaErrorStreamCaptureUnsupported);
+        const int g = (b->mix_gen + 1) % kMixGenerations;
+        cudaError_t e = b->mix_used[g] ? cudaEventSynchronize(b->mix_done[g]) : cudaSuccess;
+        if (e == cudaSuccess) {
+            std::memcpy(gen_host(g), descs.data(), descs.size());
+            e = cudaMemcpyAsync(gen_dev(g), gen_host(g), descs.size(), cudaMemcpyHostToDevice, caller);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        b->mix_gen = g;
+        b->mix_bytes = descs.size();
+    }
+    const int gen = b->mix_gen;
+
     // fork onto the internal streams
     const size_t nmix = mixin.size();
     const int used = (int)std::min<size_t>(kStreams, nmix + chunks.size() + direct.size());
@@ -291,14 +342,11 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
     const std::vector<int> at = ntt::host::place_least_loaded(work, used);
     size_t off = 0, item = 0, desc = 0;
     for (size_t mi = 0; mi < mixin.size() && e == cudaSuccess; ++mi) {
-        const size_t n = mixin[mi].size();
-        const size_t w = ntt::mixed_work_words(mixin[mi].data(), (uint32_t)n);
-        auto* d_desc = reinterpret_cast<ntt::MixJob*>(static_cast<char*>(b->d_mix) + desc * ntt::mixed_job_bytes());
-        auto* h_desc = reinterpret_cast<ntt::MixJob*>(static_cast<char*>(b->h_mix) + desc * ntt::mixed_job_bytes());
-        e = ntt::launch_mixed(mixin[mi].data(), (uint32_t)n, mix_ots[mi], d_desc, h_desc, b->d_work + off, w,
-                              b->d_status, stall, b->s[at[item]]);
+        const size_t w = ntt::mixed_work_words(mixin[mi].data(), (uint32_t)mixin[mi].size());
+        const auto* d_desc = reinterpret_cast<const ntt::MixJob*>(gen_dev(gen) + desc);
+        e = ntt::launch_mixed(built[mi], d_desc, b->d_work + off, w, b->d_status, stall, b->s[at[item]]);
         off += w;
-        desc += n;
+        desc += built[mi].desc.size();
         ++item;
     }
     std::vector<ntt::JobCtx> jc;
@@ -331,6 +379,14 @@ ntt_status ntt_batch_submit(ntt_batch* b, const ntt_job* jobs, uint32_t njobs, v
     for (int k = 0; k < used; ++k) {
         cudaEventRecord(b->join[k], b->s[k]);
         cudaStreamWaitEvent(caller, b->join[k], 0);
+    }
+    // the generation's host and device copies are free again once this
+    // event has passed (a captured submission leaves it to the eager one
+    // whose descriptors it reuses)
+    if (nmix && capture == cudaStreamCaptureStatusNone) {
+        const cudaError_t r = cudaEventRecord(b->mix_done[gen], caller);
+        if (e == cudaSuccess) e = r;
+        b->mix_used[gen] = true;
     }
     return cuda_status(e);
 }

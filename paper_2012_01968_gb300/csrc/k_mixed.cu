@@ -65,10 +65,9 @@ size_t mixed_work_words(const MixJobIn* jobs, u32 njobs)
     return w;
 }
 
-cudaError_t launch_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixJob* d_jobs, MixJob* h_jobs, u32* work,
-                         size_t work_words, u32* status, u32 stall_polls, cudaStream_t s)
+cudaError_t build_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixBuilt* out)
 {
-    if (njobs == 0 || njobs > (u32)MIX_MAX_JOBS || ots > 2) return cudaErrorInvalidValue;
+    if (!out || njobs == 0 || njobs > (u32)MIX_MAX_JOBS || ots > 2) return cudaErrorInvalidValue;
     // groups: one per (size class, direction), in that order
     std::vector<std::vector<u32>> members(MIX_MAX_GROUPS);
     for (u32 i = 0; i < njobs; ++i) {
@@ -113,23 +112,23 @@ cudaError_t launch_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixJob* d_job
         units_total += limbs * (((1ull << n) >> p1 >> 4) + ((1ull << p1) / cr));
         ++a.ngroups;
     }
-    const size_t words = (size_t)ctl + 1;
-    if (!work || work_words < words) return cudaErrorInvalidValue;
-    // the descriptors go to the device only when they changed (a repeated
-    // submission, e.g. one replayed from a CUDA graph, reuses them)
-    const size_t bytes = sizeof(MixJob) * njobs;
-    if (std::memcmp(h_jobs, hj.data(), bytes) != 0) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        cudaError_t e = cudaStreamIsCapturing(s, &cs);
-        if (e != cudaSuccess) return e;
-        if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
-        // the host copy may still be the source of an earlier upload: wait for it
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return e;
-        std::memcpy(h_jobs, hj.data(), bytes);
-        e = cudaMemcpyAsync(d_jobs, h_jobs, bytes, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return e;
-    }
+    out->desc.resize(sizeof(MixJob) * njobs);
+    std::memcpy(out->desc.data(), hj.data(), out->desc.size());
+    out->params.resize(sizeof(MixParams));
+    std::memcpy(out->params.data(), &a, sizeof(a));
+    out->units_total = units_total;
+    out->ots = ots;
+    out->work_words = (size_t)ctl + 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_mixed(const MixBuilt& m, const MixJob* d_jobs, u32* work, size_t work_words, u32* status,
+                         u32 stall_polls, cudaStream_t s)
+{
+    if (m.params.size() != sizeof(MixParams) || !d_jobs || m.ots > 2) return cudaErrorInvalidValue;
+    if (!work || work_words < m.work_words) return cudaErrorInvalidValue;
+    MixParams a;
+    std::memcpy(&a, m.params.data(), sizeof(a));
     if (stall_polls) {
         static const u32 taken = 0x40000000u;
         for (u32 g = 0; g < a.ngroups; ++g) {
@@ -140,13 +139,14 @@ cudaError_t launch_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixJob* d_job
     a.jobs = d_jobs;
     a.ctl = work;
     a.status = status;
-    a.ctl_words = (u32)words;
+    a.ctl_words = (u32)m.work_words;
     a.max_polls = stall_polls ? stall_polls : 1u << 22;
     u32 grid = 0;
-    switch (ots) {
-    case 0: return launch_mixed_ots<0>(a, s, (u32)std::min<u64>(units_total, 0xFFFFFFFFull), &grid);
-    case 1: return launch_mixed_ots<1>(a, s, (u32)std::min<u64>(units_total, 0xFFFFFFFFull), &grid);
-    default: return launch_mixed_ots<2>(a, s, (u32)std::min<u64>(units_total, 0xFFFFFFFFull), &grid);
+    const u32 units = (u32)std::min<u64>(m.units_total, 0xFFFFFFFFull);
+    switch (m.ots) {
+    case 0: return launch_mixed_ots<0>(a, s, units, &grid);
+    case 1: return launch_mixed_ots<1>(a, s, units, &grid);
+    default: return launch_mixed_ots<2>(a, s, units, &grid);
     }
 }
 

@@ -197,6 +197,20 @@ __device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
     }
 }
 
+// Compile-time loop: f(SlotIdx<I>{}) for I = I0 .. N-1.
+template <int I>
+struct SlotIdx {
+    static constexpr int value = I;
+};
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f)
+{
+    if constexpr (I < N) {
+        f(SlotIdx<I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
 // ---------------------------------------------------------------- inverse --
 // Whether the first stage an inverse round runs (its largest, 2^{KR-1}
 // twiddles per item) reads table twiddles from global memory; those are then
@@ -217,34 +231,40 @@ __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c,
 {
     if constexpr (k >= 0) {
         constexpr int half = E >> (k + 1);
+        constexpr int b = KR - 1 - k;               // this stage pairs slots differing in bit b
         constexpr int sl = K0 + k;
         constexpr bool ot = sl >= P - OTS;
         static_assert(X <= 8, "GS inputs must stay below 8q");
         if constexpr (HAS_S0 && K0 == 0 && k == 0) {
             // global stage 0: a single twiddle Psi^{-1}[1] = -Psi[1]
-#pragma unroll
-            for (int i = 0; i < half; ++i)
-                gs_bfly_scaled<X, true>(x[i], x[i + half], c.w1ninv, c.ninv, c.q);
+            static_for<0, half>([&](auto I) {
+                constexpr int XS = gs_slot_bound(X, b, decltype(I)::value);
+                gs_bfly_scaled<XS, true>(x[I.value], x[I.value + half], c.w1ninv, c.ninv, c.q);
+            });
         } else {
 #pragma unroll
             for (int pre = 0; pre < (1 << k); ++pre) {
                 const u32 jlo = ((u32)pre << K0) | c.hi;  // twiddle slot, see tw_slot
+                const int base = pre * 2 * half;
                 if constexpr (ot) {
                     typename WordTypes<W>::Tw f1, f2;
                     ot_factors<P, OTS, SOT, SCR, sl>(c, jlo, f1, f2);
-#pragma unroll
-                    for (int i = 0; i < half; ++i)
-                        gs_bfly_ot<X, false>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], f1, f2, c.q);
+                    static_for<0, half>([&](auto I) {
+                        constexpr int XS = gs_slot_bound(X, b, decltype(I)::value);
+                        gs_bfly_ot<XS, false>(x[base + I.value], x[base + I.value + half], f1, f2, c.q);
+                    });
                 } else {
                     constexpr bool pre_loaded = PRE && k == KR - 1 && inv_preloads<P, KR, K0, OTS, HAS_S0, TWM>();
                     const auto t = pre_loaded ? t0[pre] : c.tw[tw_index<TWM, SCR, SSB, sl, false>(c, jlo)];
-#pragma unroll
-                    for (int i = 0; i < half; ++i)
-                        gs_bfly<X, true>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q);
+                    static_for<0, half>([&](auto I) {
+                        constexpr int XS = gs_slot_bound(X, b, decltype(I)::value);
+                        gs_bfly<XS, true>(x[base + I.value], x[base + I.value + half], t.w, t.wp, c.q);
+                    });
                 }
             }
         }
-        inv_stages<P, KR, K0, k - 1, gs_next(X), OTS, HAS_S0, TWM, SCR, SSB, SOT, PRE, E>(x, c, t0);
+        // X stays the round's input bound: each slot's bound follows from it
+        inv_stages<P, KR, K0, k - 1, X, OTS, HAS_S0, TWM, SCR, SSB, SOT, PRE, E>(x, c, t0);
     }
 }
 

@@ -165,12 +165,13 @@ struct JobsCtx {
 cudaError_t launch_fused_jobs(const JobsCtx& c, bool fwd);
 
 // Jobs of different sizes (2^13 .. 2^17, plans of geometry 0) and directions
-// in one launch (ntt_mixed.cuh, k_mixed.cu), at most MIXED_MAX_JOBS jobs.  d_jobs / h_jobs: a device array
-// and its page-locked host copy of mixed_job_bytes() per job; the host copy
-// must equal what the device array holds (both start zeroed); descriptors are
-// uploaded only when they change, which a graph capture refuses.  The work
-// area holds mixed_work_words() zeroed words.  stall_polls > 0 (test hook):
-// every group's first-phase queue starts taken, waits bounded by it.
+// in one launch (ntt_mixed.cuh, k_mixed.cu), at most MIXED_MAX_JOBS jobs.
+// build_mixed makes the launch on the host: its job descriptors (tensor maps,
+// mixed_job_bytes() per job, which the kernel reads from device memory) and
+// its parameter block.  launch_mixed launches it with the descriptors at
+// d_jobs (uploaded by the caller, in stream order before the launch).  The
+// work area holds mixed_work_words() zeroed words.  stall_polls > 0 (test
+// hook): every group's first-phase queue starts taken, waits bounded by it.
 struct MixJobIn {
     JobCtx job;
     u32 n;                   // log2 N
@@ -180,8 +181,16 @@ struct MixJob;
 constexpr u32 MIXED_MAX_JOBS = 128;
 size_t mixed_job_bytes();
 size_t mixed_work_words(const MixJobIn* jobs, u32 njobs);
-cudaError_t launch_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixJob* d_jobs, MixJob* h_jobs, u32* work,
-                         size_t work_words, u32* status, u32 stall_polls, cudaStream_t s);
+struct MixBuilt {
+    std::vector<unsigned char> desc;      // the jobs' descriptors, mixed_job_bytes() each
+    std::vector<unsigned char> params;    // the launch's parameter block
+    u64 units_total = 0;
+    u32 ots = 0;
+    size_t work_words = 0;
+};
+cudaError_t build_mixed(const MixJobIn* jobs, u32 njobs, u32 ots, MixBuilt* out);
+cudaError_t launch_mixed(const MixBuilt& m, const MixJob* d_jobs, u32* work, size_t work_words, u32* status,
+                         u32 stall_polls, cudaStream_t s);
 cudaError_t launch_pointwise(const PrimeDev* primes, u32 L, u32 n, const u64* a, const u64* b,
                              u64* out, u32 limbs, cudaStream_t s);
 

@@ -297,7 +297,6 @@ ntt_status ntt_server_create(ntt_server** out, const ntt_server_opts* opts)
             if (s.stream) cudaStreamDestroy(s.stream);
             if (s.status) cudaFreeHost(s.status);
             if (s.done) cudaEventDestroy(s.done);
-        if (s.begin) cudaEventDestroy(s.begin);
             if (s.begin) cudaEventDestroy(s.begin);
         }
         cudaFree(srv->arena_mem);
@@ -326,6 +325,7 @@ void ntt_server_destroy(ntt_server* srv)
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.status) cudaFreeHost(s.status);
         if (s.done) cudaEventDestroy(s.done);
+        if (s.begin) cudaEventDestroy(s.begin);
     }
     cudaFree(srv->arena_mem);
     delete srv;

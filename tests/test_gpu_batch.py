@@ -155,6 +155,70 @@ def test_batch_graph_capture_and_replay(orc, chain):
             p.close()
 
 
+def _sets_of_jobs(chain, sets, seed):
+    """Device arrays with fresh inputs for each set of (n, levels, op) jobs."""
+    datas = [[I.batch_uniform(seed + 10 * k + i, 1, chain[:lv], 1 << n) for i, (n, lv, _) in enumerate(js)]
+             for k, js in enumerate(sets)]
+    return datas, [[dev(d) for d in ds] for ds in datas]
+
+
+def _check_sets(orc, chain, sets, datas, bufs):
+    for js, ds, ts in zip(sets, datas, bufs):
+        for (n, lv, op), d, t in zip(js, ds, ts):
+            want = (oracle_fwd if op == FWD else oracle_inv)(orc, d, chain[:lv])
+            assert np.array_equal(host(t), want), f"n={n} levels={lv} op={op}"
+
+
+def test_changed_descriptors_do_not_drain_the_stream(orc, chain):
+    """Three submissions with different mixed-launch descriptors, queued on a
+    stream behind a long kernel, return while that kernel still runs (the
+    host does not wait for the stream), and their results match the oracle."""
+    plans = {n: G.Plan(1 << n, chain) for n in (14, 15)}
+    sets = [[(14, 5, FWD), (15, 3, INV)], [(15, 4, FWD), (14, 2, FWD)], [(14, 6, INV)]]
+    try:
+        with G.Batch() as b:
+            s = torch.cuda.Stream()
+            _, bufs = _sets_of_jobs(chain, sets, 700)
+            for js, ts in zip(sets, bufs):             # sizes the work area and descriptor arrays
+                b.submit([(plans[n].handle, t, 1, lv, op) for (n, lv, op), t in zip(js, ts)], s)
+            torch.cuda.synchronize()
+            datas, bufs = _sets_of_jobs(chain, sets, 800)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(s):
+                torch.cuda._sleep(400_000_000)          # about 0.2 s of device time
+            for js, ts in zip(sets, bufs):
+                b.submit([(plans[n].handle, t, 1, lv, op) for (n, lv, op), t in zip(js, ts)], s)
+            assert not s.query(), "a submission waited for the stream"
+            torch.cuda.synchronize()
+            assert b.device_status() == 0
+        _check_sets(orc, chain, sets, datas, bufs)
+    finally:
+        for p in plans.values():
+            p.close()
+
+
+def test_many_changed_submissions_in_flight(orc, chain):
+    """Seven submissions with different descriptors back to back on one
+    stream (more than the four descriptor generations, so the later ones
+    reuse generations of earlier ones still queued): all match the oracle."""
+    plans = {n: G.Plan(1 << n, chain) for n in (13, 14, 16)}
+    sets = [[(13, 2 + k, FWD if k % 2 else INV), (16, 1 + k % 3, FWD), (14, 3, INV if k % 3 else FWD)]
+            for k in range(7)]
+    try:
+        with G.Batch() as b:
+            s = torch.cuda.Stream()
+            datas, bufs = _sets_of_jobs(chain, sets, 900)
+            torch.cuda.synchronize()
+            for js, ts in zip(sets, bufs):
+                b.submit([(plans[n].handle, t, 1, lv, op) for (n, lv, op), t in zip(js, ts)], s)
+            torch.cuda.synchronize()
+            assert b.device_status() == 0
+        _check_sets(orc, chain, sets, datas, bufs)
+    finally:
+        for p in plans.values():
+            p.close()
+
+
 def test_batch_argument_errors(chain):
     p = G.Plan(1 << 13, chain[:4])
     buf = torch.zeros(4 << 14, dtype=torch.int64, device="cuda")
