@@ -651,6 +651,9 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
             done = np.array([x[2] for x in times[first:]], dtype=np.float64)
             lat = (done - sub) / 1e3
             dev_us = np.array([x[3] for x in times[first:]], dtype=np.float64) / 1e3
+            admit = np.array([x[1] for x in times[first:]], dtype=np.float64)
+            queue_us = (admit - sub) / 1e3                  # submission to the batch's start
+            turn_us = (done - admit) / 1e3                  # batch start to completion seen
             span = (done.max() - sub.min()) / 1e9
             limbs = sum(r.L for r in base[first:])
             return {"limb_ntt_per_s": limbs / span, "requests_per_s": (count - first) / span,
@@ -660,6 +663,10 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                     "batch_device_us": {"p50": float(np.percentile(dev_us, 50)),
                                         "p99": float(np.percentile(dev_us, 99))},
                     "max_gap_between_completions_us": float(np.max(np.diff(np.sort(done)))) / 1e3,
+                    "timeline_us": {"queue_p50": float(np.percentile(queue_us, 50)),
+                                    "queue_p99": float(np.percentile(queue_us, 99)),
+                                    "batch_p50": float(np.percentile(turn_us, 50)),
+                                    "batch_p99": float(np.percentile(turn_us, 99))},
                     "scheduler": {(k[:-3] + "_us" if k.endswith("_ns") else k): (v / 1e3 if k.endswith("_ns") else v)
                                   for k, v in sched.items()}}
 
@@ -683,6 +690,7 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                                          for r in runs[frac]],
                 max_completion_gap_us_runs=[r["scheduler"]["max_completion_gap_us"] for r in runs[frac]],
                 max_launch_us_runs=[r["scheduler"]["max_launch_us"] for r in runs[frac]],
+                queue_p99_us_runs=[r["timeline_us"]["queue_p99"] for r in runs[frac]],
                 p99_max_over_median=max(p99) / med if med > 0 else None)
         out["scheduler_units"] = "_us keys in microseconds; batches and requests are counts"
         return out
