@@ -671,8 +671,16 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                                   for k, v in sched.items()}}
 
         cap = run(None)
+        if tuned:
+            plans_used = ("the autotuner's choice per N for 60 limbs x 6 polynomials per launch; the loads "
+                          "are fractions of the capacity these plans reach with full 64-request batches, "
+                          "which the smaller batches formed at 80% load run less efficiently")
+        elif plan_kw:
+            plans_used = "plans with the options " + json.dumps(plan_kw) + " (per-pass organisation)"
+        else:
+            plans_used = "library default plans (fused, default split: one mixed-size launch per batch)"
         out = {"requests": count, "budget_gb": budget_gb, "data": "device-resident, in place",
-               "capacity": cap}
+               "plans": plans_used, "capacity": cap}
         out["max_batch_jobs"], out["slots"] = max_batch_jobs, slots
         # the three loads, `repeats` times in a row: the p99 of every run, to show
         # whether a run's tail is an outlier
