@@ -436,11 +436,14 @@ def _ok(G, st, what):
 def host_link_rates(torch, hin, hout, reps=20):
     """Pinned host <-> device copy rates of this machine's link (GB/s): one
     direction at a time, and both at once on two streams, for the buffers
-    the end-to-end call moves."""
+    the end-to-end call moves; and each direction split into 2, 4 and 8
+    chunks copied concurrently on as many streams (whether more copy engines
+    raise the rate)."""
     d = torch.empty_like(hin, device="cuda")
     d2 = torch.empty_like(hin, device="cuda")
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     nbytes = hin.numel() * hin.element_size()
+    many = [torch.cuda.Stream() for _ in range(8)]
 
     def timed(fn):
         fn()
@@ -462,8 +465,23 @@ def host_link_rates(torch, hin, hout, reps=20):
     def both():
         h2d()
         d2h()
+
+    def split(k, to_device):
+        n = hin.numel() // k
+
+        def fn():
+            for i in range(k):
+                lo, hi = i * n, (hin.numel() if i == k - 1 else (i + 1) * n)
+                with torch.cuda.stream(many[i]):
+                    if to_device:
+                        d[lo:hi].copy_(hin[lo:hi], non_blocking=True)
+                    else:
+                        hout[lo:hi].copy_(d2[lo:hi], non_blocking=True)
+        return fn
     return {"h2d_gbs": nbytes / timed(h2d) / 1e9, "d2h_gbs": nbytes / timed(d2h) / 1e9,
-            "both_gbs": 2 * nbytes / timed(both) / 1e9}
+            "both_gbs": 2 * nbytes / timed(both) / 1e9,
+            "h2d_gbs_by_streams": {k: nbytes / timed(split(k, True)) / 1e9 for k in (2, 4, 8)},
+            "d2h_gbs_by_streams": {k: nbytes / timed(split(k, False)) / 1e9 for k in (2, 4, 8)}}
 
 
 def per_limb_c2(G, torch, w, host, steps):
