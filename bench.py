@@ -22,6 +22,7 @@ import argparse
 import gc
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -1031,6 +1032,8 @@ def select_c2(G, torch, N, primes, bufs, steps=400, warmup=20):
     L = len(primes)
     rows = []
     for kname, tw, geom, ctas, S in C2_CANDIDATES:
+        if len(bufs) % S:
+            raise ValueError("buffers must be a multiple of the streams (each buffer on one stream)")
         base = G.Plan(N, primes, *TWIDDLES[tw], kernels[kname], geom, ctas_per_sm=ctas)
         plans = [base] + [base.clone() for _ in range(S - 1)]
         ss = [torch.cuda.Stream() for _ in range(S)]
@@ -1143,6 +1146,12 @@ def main():
     l2f = G.NTT_PLAN_L2_TWIDDLES if args.l2_twiddles else 0
     poly_bytes = N * L * 8
     nbuf = max(2 * max(S, 3), -(-2 * L2_BYTES // poly_bytes) + 1)
+    # step i uses buffer i mod nbuf on stream i mod S: with nbuf a multiple of
+    # every stream count in use (S, and the 2 and 3 of the selection's
+    # candidates), each buffer stays on one stream, so no two steps in flight
+    # on different streams share an array
+    m = math.lcm(6, S)
+    nbuf = -(-nbuf // m) * m
     host = I.batch_uniform(w.seed, 1, primes, N)
     src = torch.from_numpy(host.view(np.int64).copy()).cuda()
     bufs = [src.clone() for _ in range(nbuf)]
