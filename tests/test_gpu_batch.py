@@ -185,7 +185,7 @@ def test_changed_descriptors_do_not_drain_the_stream(orc, chain):
             datas, bufs = _sets_of_jobs(chain, sets, 800)
             torch.cuda.synchronize()
             with torch.cuda.stream(s):
-                torch.cuda._sleep(400_000_000)          # about 0.2 s of device time
+                torch.cuda._sleep(1_000_000_000)        # about 0.5 s of device time
             for js, ts in zip(sets, bufs):
                 b.submit([(plans[n].handle, t, 1, lv, op) for (n, lv, op), t in zip(js, ts)], s)
             assert not s.query(), "a submission waited for the stream"
