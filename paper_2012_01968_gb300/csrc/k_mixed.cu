@@ -1,5 +1,5 @@
 // Host side of the mixed-size launch (ntt_mixed.cuh): groups, job
-// descriptors, CTA shares, and the three instantiations (table, OT of one or
+// descriptors, and the three instantiations (table, OT of one or
 // two stages).
 #include <algorithm>
 #include <cstring>
@@ -30,24 +30,8 @@ cudaError_t launch_mixed_ots(const MixParams& prm, cudaStream_t s, u32 units_tot
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const u64 slots = (u64)device_sm_count() * (u64)occ;
     const u32 grid = (u32)std::min<u64>(units_total, slots);
-    // SM shares of the groups (in 1/1024ths of the SMs), in proportion to
-    // their work (limbs x N log N)
-    MixParams a = prm;
-    double total = 0;
-    std::vector<double> w(a.ngroups);
-    for (u32 g = 0; g < a.ngroups; ++g) {
-        const u32 n = MIX_FIRST_N + a.group[g].cls;
-        w[g] = (double)a.group[g].limbs * (double)(1u << n) * n;
-        total += w[g];
-    }
-    double acc = 0;
-    for (u32 g = 0; g < a.ngroups; ++g) {
-        a.sm_start[g] = (u32)std::min<double>(1024.0, acc / total * 1024.0 + 0.5);
-        acc += w[g];
-    }
-    a.sm_start[a.ngroups] = 1024;
     *grid_out = grid;
-    kern<<<grid, LY::THREADS, LY::SMEM, s>>>(a);
+    kern<<<grid, LY::THREADS, LY::SMEM, s>>>(prm);
     return cudaGetLastError();
 }
 

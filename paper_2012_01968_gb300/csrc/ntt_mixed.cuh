@@ -6,12 +6,12 @@
 // each with the default geometry of its size) and one direction.  Each group
 // runs the two-phase protocol of the fused kernel (ntt_fused.cuh) on its own
 // work area: phase-0 tiles never wait, a phase-1 tile waits for every phase-0
-// tile of its limb, limbs are published in completion order.  The grid is
-// shared: a CTA starts in the group of the SM it runs on (the host gives the
-// groups shares of the SMs in proportion to their work, so that the CTAs on
-// one SM run the same tile routines) and, once that group has no ticket left
-// to claim, moves on to the next group that has, so the groups' tails overlap
-// and every CTA stays busy until all groups are done.  A unit descriptor
+// tile of its limb, limbs are published in completion order.  The grid
+// works through the groups in order: every CTA starts in group 0 and, once
+// that group has no ticket left to claim, moves on to the next group that
+// has, so at any time the SMs run the tile routines of one group (two at its
+// end), which keeps them in the instruction caches, and the groups' tails
+// overlap so that every CTA stays busy until all groups are done.  A unit descriptor
 // carries the group, and the compute threads run the tile routine of its
 // size class and direction.
 //
@@ -103,7 +103,6 @@ struct MixGroup {
 struct MixParams {
     MixJobInfo info[MIX_MAX_JOBS];
     MixGroup group[MIX_MAX_GROUPS];
-    u32 sm_start[MIX_MAX_GROUPS + 1];    // CTAs on SMs [sm_start[g], sm_start[g+1]) of nsmid start in group g
     const MixJob* jobs;
     u32* ctl;                    // work areas of the groups, then one word: CTAs finished
     u32* status;                 // persistent error word
@@ -163,15 +162,10 @@ ntt_mixed_kernel(const __grid_constant__ MixParams a)
         u32 q0 = 0, q1 = 0, q2 = 0, qn = 0;      // committed stores not yet published: group << 28 | limb, +1
         u32 left = 0;                             // 2 bits per group: phases that may still have tickets
         for (u32 g = 0; g < a.ngroups; ++g) left |= 3u << (2 * g);
-        // the group this CTA takes work from first: by the SM it runs on, so
-        // that the CTAs sharing an SM run the same tile routines (the
+        // every CTA takes work from group 0 first and then from the groups in
+        // order, so that the SMs run one group's tile routines at a time (the
         // groups' routines together exceed the instruction caches)
-        u32 smid, nsmid;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
         u32 g = 0;
-        const u32 pos = (u32)(((u64)smid * 1024u) / (nsmid ? nsmid : 1u));   // SM position in 1/1024ths
-        while (g + 1 < a.ngroups && pos >= a.sm_start[g + 1]) ++g;
         bool stopped = false, failed = false;
         u32 held = NONE, held_g = 0;
         u32 idle = 0;
