@@ -196,8 +196,10 @@ def write_traffic_json(out, csvs, command):
     N, L = 1 << 16, 45
     geoms = {(8, 4): 0, (8, 3): 1, (7, 3): 2}
     per = {}
-    passes = {}
+    pass_sets = []           # per CSV file (one per-pass configuration each): direction -> launches
     for path in csvs:
+        passes = {}
+        pass_sets.append(passes)
         hdr = None
         for r in _csv.reader(open(path)):
             if r and r[0] == "ID":
@@ -211,9 +213,11 @@ def write_traffic_json(out, csvs, command):
             metric = {"dram__bytes_read.sum": "read", "dram__bytes_write.sum": "write",
                       "gpu__time_duration.sum": "t"}[d["Metric Name"]]
             if "ntt_pass_kernel" in name:
-                # P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, W
+                # P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, W, TBL_LAST
                 pa = [x.strip() for x in re.search(r"ntt_pass_kernel<([^>]*)>", name).group(1).split(",")]
                 P, logc, rows, fwd, ots = int(pa[0]), int(pa[1]), int(pa[3]) == 1, int(pa[4]), int(pa[8])
+                if len(pa) >= 12 and pa[11] in ("1", "true"):
+                    ots = 0          # table plan: the last stage reads the table, not OT factors
                 direction = "forward" if fwd else "inverse"
                 e = passes.setdefault(direction, {"col": {"read": [], "write": [], "t": []},
                                                   "row": {"read": [], "write": [], "t": []}})
@@ -249,7 +253,7 @@ def write_traffic_json(out, csvs, command):
                                "--cache-control none on steady-state launches of the bench's timed loop; writes "
                                "include write-back of lines evicted during the launch; data_read_bytes = one read "
                                "of the array (8 N L), the rest of the reads counted as twiddle reads"})
-    for direction, e in sorted(passes.items()):
+    for direction, e in [(d, ps[d]) for ps in pass_sets for d in sorted(ps)]:
         if "p1" not in e or not e["col"]["read"]:
             continue
         rd = float(np.mean(e["col"]["read"])) + float(np.mean(e["row"]["read"]))
@@ -814,6 +818,38 @@ def large_ring_c3(G, torch, reps=50, opts=None):
         ms = timed(step, reps)
         if not all(torch.equal(b, src) for b in bufs):
             raise RuntimeError("C3 round trip mismatch")
+        # independent ciphertexts on two streams (a clone of the plan each),
+        # as the C2 timed steps run: buffer i on stream i mod 2
+        streams2 = [s, torch.cuda.Stream()]
+        nb2 = nbuf + (nbuf % 2)
+        while len(bufs) < nb2:
+            bufs.append(src.clone())
+        with p.clone() as p2:
+            hs = [p.handle, p2.handle]
+
+            def step2(i):
+                b, j = bufs[i % nb2].data_ptr(), i % 2
+                _ok(G, lib.ntt_forward(hs[j], b, 2, streams2[j].cuda_stream), "C3 forward")
+                _ok(G, lib.ntt_inverse(hs[j], b, 2, streams2[j].cuda_stream), "C3 inverse")
+            for i in range(4):
+                step2(i)
+            torch.cuda.synchronize()
+            cur = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            for st in streams2:
+                st.wait_event(e0)
+            for i in range(2 * reps):
+                step2(i)
+            for st in streams2:
+                e = torch.cuda.Event()
+                e.record(st)
+                cur.wait_event(e)
+            e1.record(cur)
+            torch.cuda.synchronize()
+            ms2 = e0.elapsed_time(e1) / (2 * reps)
+            if not all(torch.equal(b, src) for b in bufs) or p2.device_status() != 0:
+                raise RuntimeError("C3 two-stream round trip mismatch")
         c = torch.empty(L * N, dtype=torch.int64, device="cuda")
 
         def product(i):
@@ -834,6 +870,9 @@ def large_ring_c3(G, torch, reps=50, opts=None):
     return {"workload": "N=2^17, L=60, batch 2 (one ciphertext), forward + inverse, one stream",
             "value": 2 * 2 * L / (ms / 1e3), "unit": "limb-NTT/s", "ms_per_step": ms,
             "alg_bytes_per_step": 2 * 2 * 16 * L * N,
+            "two_streams": {"value": 2 * 2 * L / (ms2 / 1e3), "unit": "limb-NTT/s", "ms_per_step": ms2,
+                            "how": "independent ciphertexts, step i on stream i mod 2 (a plan clone each), "
+                                   "CUDA events around all steps"},
             "negacyclic_product_us": ms_mul * 1e3,
             "negacyclic_product": "c = a * b mod (X^N + 1), 60 limbs: 2 forwards in one launch, product, inverse",
             "negacyclic_product_in_place_us": ms_mul_ip * 1e3,
@@ -1020,6 +1059,7 @@ C2_CANDIDATES = (
     ("fused", "ot1", 0, 1, 3), ("fused", "table", 0, 1, 3), ("fused", "ot1", 0, 0, 2),
     ("per_pass", "ot1", 1, 0, 2), ("per_pass", "ot2", 1, 0, 2), ("per_pass", "ot2", 1, 0, 3),
     ("per_pass", "ot1", 0, 0, 2), ("per_pass", "ot2", 0, 0, 2),
+    ("per_pass", "table", 1, 0, 2), ("per_pass", "table", 1, 0, 3),
 )
 TWIDDLES = {"auto": (0, 0), "table": (1, 0), "ot1": (2, 1), "ot2": (2, 2)}
 

@@ -54,11 +54,11 @@ struct PassLaunch {
 };
 
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
-          bool TW_SMEM, class W>
+          bool TW_SMEM, class W, bool TBL_LAST = false>
 cudaError_t launch_pass_w(const PassLaunch<W>& c, u32 s0, const typename WordTypes<W>::Tw* ota,
                           const typename WordTypes<W>::Tw* otb)
 {
-    auto kern = ntt_pass_kernel<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, W>;
+    auto kern = ntt_pass_kernel<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, W, TBL_LAST>;
     constexpr size_t smem = pass_smem_bytes<P, LOGC, KMAX, ROWS, HAS_S0, TW_SMEM, OTS, W>();
     constexpr int T = pass_threads(P, LOGC, KMAX);
     if (smem > 48 * 1024) {
@@ -93,12 +93,12 @@ cudaError_t launch_pass_w(const PassLaunch<W>& c, u32 s0, const typename WordTyp
 }
 
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
-          bool TW_SMEM>
+          bool TW_SMEM, bool TBL_LAST = false>
 cudaError_t launch_pass(const LaunchCtx& c, u32 s0, const Tw* ota, const Tw* otb)
 {
     const PassLaunch<u64> pl{c.data,   c.limbs,    c.L,        c.n,        c.primes,
                              c.tw,     c.tw_len,   c.stream,   c.l2_base,  c.l2_bytes, c.l2_hit};
-    return launch_pass_w<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, u64>(pl, s0, ota, otb);
+    return launch_pass_w<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, u64, TBL_LAST>(pl, s0, ota, otb);
 }
 
 // Single pass over all n stages (n <= 12): one CTA per limb, with the limb's
@@ -112,20 +112,28 @@ cudaError_t launch_single_n(const LaunchCtx& c, bool fwd)
     return launch_pass<N_LOG, 0, KMAX_ALL, true, false, 1, true, true, 0, true>(c, 0, nullptr, nullptr);
 }
 
-// Two passes: P1 column-like stages [0, P1), then P2 row-like stages.
+// Two passes: P1 column-like stages [0, P1), then P2 row-like stages.  The
+// row passes take OTS on-the-fly stages with their factor tables; in table
+// mode (OTS 0) they read the last stage's twiddles from the table in global
+// memory instead (TBL_LAST), with the other stages' runs staged in shared
+// memory as with one OT stage, so that they keep the shared-memory footprint
+// of OT1 without its second product.
 template <int P1, int P2, int LOGC_R, int KMAX_R, int OTS>
 cudaError_t launch_two_pass_ots(const LaunchCtx& c, bool fwd)
 {
     constexpr int LOGC_C = 4;
     constexpr int KMAX_C = KMAX_R;
+    constexpr bool TBL_LAST = OTS == 0;
+    constexpr int OTS_R = TBL_LAST ? 1 : OTS;
     cudaError_t e;
     if (fwd) {
         e = launch_pass<P1, LOGC_C, KMAX_C, false, true, 1, false, true, 0, true>(c, 0, nullptr, nullptr);
         if (e != cudaSuccess) return e;
         constexpr int X2 = ct_range_after(1, P1);
-        return launch_pass<P2, LOGC_R, KMAX_R, true, true, X2, true, false, OTS, false>(c, P1, c.ota_f, c.otb_f);
+        return launch_pass<P2, LOGC_R, KMAX_R, true, true, X2, true, false, OTS_R, false, TBL_LAST>(c, P1, c.ota_f,
+                                                                                                   c.otb_f);
     }
-    e = launch_pass<P2, LOGC_R, KMAX_R, true, false, 1, false, false, OTS, false>(c, P1, c.ota_i, c.otb_i);
+    e = launch_pass<P2, LOGC_R, KMAX_R, true, false, 1, false, false, OTS_R, false, TBL_LAST>(c, P1, c.ota_i, c.otb_i);
     if (e != cudaSuccess) return e;
     constexpr int X1 = gs_range_after(1, P2);
     return launch_pass<P1, LOGC_C, KMAX_C, false, false, X1, true, true, 0, true>(c, 0, nullptr, nullptr);

@@ -91,6 +91,7 @@ struct ItemCtxT {
     u32 hi;              // bits of v above the round digit
     u32 s0;              // first stage of the pass
     TwT ninv, w1ninv;
+    const TwT* twg;      // the prime's full table in global memory (SOT 2: the last stage's twiddles)
 };
 using ItemCtx = ItemCtxT<u64>;
 
@@ -155,7 +156,10 @@ __device__ __forceinline__ u32 tw_index(const ItemCtxT<W>& c, const u32 jlo)
 // OT factors of stage sl (one of the last OTS stages): the per-row factor
 // B[sl][u] and the per-position factor A[2^sl + j].  SOT: both are staged in
 // shared memory with the tile (A from entry 2^(P-OTS), B as OTS runs of SCR
-// rows), else read from the prime's global tables.
+// rows), else read from the prime's global tables.  SOT 2 (a table-mode row
+// pass with the OT staging layout and OTS 1): the last stage is not
+// factored; its plain table twiddles come from the table in global memory
+// (`twg`), loaded into registers at the start of the round that holds it.
 template <int P, int OTS, int SOT, int SCR, int sl, class W>
 __device__ __forceinline__ void ot_factors(const ItemCtxT<W>& c, const u32 jlo, typename WordTypes<W>::Tw& f1,
                                            typename WordTypes<W>::Tw& f2)
@@ -171,7 +175,8 @@ __device__ __forceinline__ void ot_factors(const ItemCtxT<W>& c, const u32 jlo, 
 
 // ---------------------------------------------------------------- forward --
 template <int P, int KR, int K0, int k, int X, int OTS, int TWM, int SCR, int SSB, int SOT, int E, class W>
-__device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
+__device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c,
+                                           const typename WordTypes<W>::Tw (&t0)[(E >> 1) > 0 ? (E >> 1) : 1])
 {
     if constexpr (k < KR) {
         constexpr int half = E >> (k + 1);
@@ -180,7 +185,12 @@ __device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
 #pragma unroll
         for (int pre = 0; pre < (1 << k); ++pre) {
             const u32 jlo = ((u32)pre << K0) | c.hi;      // twiddle slot, see tw_slot
-            if constexpr (ot) {
+            if constexpr (ot && SOT == 2) {
+                const auto t = k == KR - 1 ? t0[pre] : c.twg[tw_index<TW_GLOBAL, SCR, SSB, sl, true>(c, jlo)];
+#pragma unroll
+                for (int i = 0; i < half; ++i)
+                    ct_bfly<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.q4);
+            } else if constexpr (ot) {
                 typename WordTypes<W>::Tw f1, f2;
                 ot_factors<P, OTS, SOT, SCR, sl>(c, jlo, f1, f2);
 #pragma unroll
@@ -193,7 +203,7 @@ __device__ __forceinline__ void fwd_stages(W (&x)[E], const ItemCtxT<W>& c)
                     ct_bfly<X>(x[pre * 2 * half + i], x[pre * 2 * half + i + half], t.w, t.wp, c.q, c.q4);
             }
         }
-        fwd_stages<P, KR, K0, k + 1, ct_next(X), OTS, TWM, SCR, SSB, SOT, E>(x, c);
+        fwd_stages<P, KR, K0, k + 1, ct_next(X), OTS, TWM, SCR, SSB, SOT, E>(x, c, t0);
     }
 }
 
@@ -246,7 +256,13 @@ __device__ __forceinline__ void inv_stages(W (&x)[E], const ItemCtxT<W>& c,
             for (int pre = 0; pre < (1 << k); ++pre) {
                 const u32 jlo = ((u32)pre << K0) | c.hi;  // twiddle slot, see tw_slot
                 const int base = pre * 2 * half;
-                if constexpr (ot) {
+                if constexpr (ot && SOT == 2) {
+                    const auto t = k == KR - 1 ? t0[pre] : c.twg[tw_index<TW_GLOBAL, SCR, SSB, sl, false>(c, jlo)];
+                    static_for<0, half>([&](auto I) {
+                        constexpr int XS = gs_slot_bound(X, b, decltype(I)::value);
+                        gs_bfly<XS, true>(x[base + I.value], x[base + I.value + half], t.w, t.wp, c.q);
+                    });
+                } else if constexpr (ot) {
                     typename WordTypes<W>::Tw f1, f2;
                     ot_factors<P, OTS, SOT, SCR, sl>(c, jlo, f1, f2);
                     static_for<0, half>([&](auto I) {
@@ -305,6 +321,14 @@ __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base
             for (int pre = 0; pre < (E >> 1); ++pre)
                 t0[pre] = c.tw[tw_index<TWM, SCR, SSB, K0 + KR - 1, false>(c, ((u32)pre << K0) | hi)];
         }
+        if constexpr (SOT == 2 && K0 + KR - 1 >= P - OTS) {
+            // the last stage's table twiddles come from global memory: load
+            // them before the round's shared-memory reads (t0 serves the
+            // round's last forward stage or its first inverse stage)
+#pragma unroll
+            for (int pre = 0; pre < (E >> 1); ++pre)
+                t0[pre] = c.twg[tw_index<TW_GLOBAL, SCR, SSB, K0 + KR - 1, FWD>(c, ((u32)pre << K0) | hi)];
+        }
         W x[E];
         if constexpr (PAIRS) {
 #pragma unroll
@@ -321,7 +345,7 @@ __device__ __forceinline__ void run_round(W* sm, ItemCtxT<W> c, const u32 u_base
             }
         }
         if constexpr (FWD)
-            fwd_stages<P, KR, K0, 0, XR, OTS, TWM, SCR, SSB, SOT, E>(x, c);
+            fwd_stages<P, KR, K0, 0, XR, OTS, TWM, SCR, SSB, SOT, E>(x, c, t0);
         else
             inv_stages<P, KR, K0, KR - 1, XR, OTS, HAS_S0, TWM, SCR, SSB, SOT, PRE, E>(x, c, t0);
         if constexpr (CANON > 0) {
@@ -412,14 +436,14 @@ struct RowStaging {
 // filled, report it read).
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0, int OTS,
           bool TW_SMEM, int NT, class Hook = NoHook, bool NAMED = false, bool PRELOAD_TW = false, class W = u64,
-          int STAGE = 0, bool WARPX = false, class HW = NoHook, class HA = NoHook>
+          int STAGE = 0, bool WARPX = false, class HW = NoHook, class HA = NoHook, bool TBL_LAST = false>
 __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>::Prime& pr,
                                              const typename WordTypes<W>::Tw* tw,
                                              const typename WordTypes<W>::Tw* ota,
                                              const typename WordTypes<W>::Tw* otb, const u32 u_base, const u32 s0,
                                              const u32 tid, Hook mid = Hook(),
                                              const typename WordTypes<W>::Tw* htw = nullptr, HW hw = HW(),
-                                             HA ha = HA())
+                                             HA ha = HA(), const typename WordTypes<W>::Tw* twg = nullptr)
 {
     constexpr int NR = nrounds(P, KMAX);
     static_assert(NR <= 4, "at most four rounds per pass");
@@ -439,6 +463,7 @@ __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>:
     c.ninv = pr.ninv;
     c.w1ninv = pr.w1ninv;
     c.tw = tw;
+    c.twg = twg;
     c.ota = STAGE ? htw + RS::A_OFF : ota;
     c.otb = STAGE ? htw + RS::B_OFF : otb;
     (void)CRS;
@@ -448,7 +473,8 @@ __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>:
     constexpr int TWM0 = STAGE ? TW_STAGED : TWM_PLAIN;
     constexpr int TWM1 = STAGE ? TW_STAGED : TWM_PLAIN;
     constexpr int SB0 = 0, SB1 = RS::SSB;
-    constexpr int SOT = STAGE ? 1 : 0;
+    constexpr int SOT = TBL_LAST ? 2 : (STAGE ? 1 : 0);
+    static_assert(!TBL_LAST || (STAGE && OTS == 1), "TBL_LAST takes the staging layout of one OT stage");
     constexpr bool PRE = PRELOAD_TW && !STAGE;
     ItemCtxT<W> c1 = c;
     if constexpr (STAGE) {
@@ -523,6 +549,9 @@ __device__ __forceinline__ void compute_tile(W* sm, const typename WordTypes<W>:
 //   OTS                 : the last OTS stages of the pass use on-the-fly twiddles
 //   TW_SMEM             : stage the pass's twiddles Psi[1 .. 2^P) in shared
 //                         memory (only when s0 == 0, where they are all it needs)
+//   TBL_LAST            : (table plans, OTS 1, staged row twiddles) the last
+//                         stage is not factored: its twiddles come from the
+//                         table in global memory, the others' runs are staged
 // 16-byte global <-> shared moves of a tile: one vector holds 16 / sizeof(W)
 // words and lands in shared memory as word pairs (the swizzle keeps pairs).
 template <class W>
@@ -599,7 +628,7 @@ __device__ __forceinline__ void batched_copy(const u32 tid, LD ld, ST st)
 }
 
 template <int P, int LOGC, int KMAX, bool ROWS, bool FWD, int XIN, bool FINAL, bool HAS_S0,
-          int OTS, bool TW_SMEM, class W = u64>
+          int OTS, bool TW_SMEM, class W = u64, bool TBL_LAST = false>
 __global__ void __launch_bounds__(pass_threads(P, LOGC, KMAX), pass_min_blocks(pass_threads(P, LOGC, KMAX)))
 ntt_pass_kernel(const PassArgsT<W> a)
 {
@@ -626,6 +655,7 @@ ntt_pass_kernel(const PassArgsT<W> a)
     constexpr bool SR = pass_stages_rows<P, LOGC, KMAX, ROWS, HAS_S0, OTS, W>();
     using RS = RowStaging<P, C, KMAX, OTS, 2>;
     TwT* const htw = sm_ota;
+    static_assert(!TBL_LAST || SR, "the last stage reads the global table only with staged row twiddles");
 
     const u32 tid = threadIdx.x;
     const u32 tile = blockIdx.x;
@@ -668,7 +698,7 @@ ntt_pass_kernel(const PassArgsT<W> a)
                                    : (2u << (a.s0 + sl)) - ((u_base + (u32)C) << sl);
                 cp_async16(&htw[e], &tb[st + i]);
             }
-            if constexpr (OTS > 0) {
+            if constexpr (OTS > 0 && !TBL_LAST) {
                 const TwT* ga = a.ota + (size_t)pi * R + (1u << (P - OTS));
                 for (u32 i = tid; i < (u32)RS::NA; i += T) cp_async16(&htw[RS::A_OFF + i], &ga[i]);
                 const TwT* gb = a.otb + (size_t)pi * ((size_t)P << a.s0);
@@ -728,8 +758,9 @@ ntt_pass_kernel(const PassArgsT<W> a)
 
     if constexpr (SR)
         compute_tile<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, false, T, NoHook, false, false, W, 2,
-                     rows_stay_in_warp<P, LOGC, KMAX, T>()>(sm, pr, htw, nullptr, nullptr, u_base, a.s0, tid,
-                                                            NoHook(), htw);
+                     rows_stay_in_warp<P, LOGC, KMAX, T>(), NoHook, NoHook, TBL_LAST>(
+            sm, pr, htw, nullptr, nullptr, u_base, a.s0, tid, NoHook(), htw, NoHook(), NoHook(),
+            a.tw + (size_t)pi * a.tw_len);
     else
         compute_tile<P, LOGC, KMAX, ROWS, FWD, XIN, FINAL, HAS_S0, OTS, TW_SMEM, T>(
             sm, pr, TW_SMEM ? sm_tw : a.tw + (size_t)pi * a.tw_len, sm_ota,
