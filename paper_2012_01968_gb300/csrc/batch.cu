@@ -425,13 +425,16 @@ ntt_status ntt_internal_batch_status_async(ntt_batch* b, uint32_t* host_word, vo
     return cuda_status(e);
 }
 
-// Library-internal: size the work area up front (the serving loop reserves
-// its batches' areas at creation, so that no submission grows one).
+// Library-internal: size the work area and the mixed launches' descriptor
+// arrays up front (the serving loop reserves its batches at creation, so that
+// no submission grows an area or drains the device to allocate the arrays).
 ntt_status ntt_internal_batch_reserve(ntt_batch* b, uint64_t words, void* stream)
 {
     if (!b) return NTT_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> guard(b->mu);
-    return cuda_status(grow_work(b, (size_t)words, (cudaStream_t)stream));
+    cudaError_t e = grow_work(b, (size_t)words, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = reserve_mix(b, 1, (cudaStream_t)stream);
+    return cuda_status(e);
 }
 
 ntt_status ntt_batch_device_status(ntt_batch* b, uint32_t* status)
