@@ -118,6 +118,15 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
+def agree_on_rank0(obj, dist):
+    """Rank 0's value of a picklable object on every rank (itself alone)."""
+    if dist is None:
+        return obj
+    box = [obj]
+    dist.broadcast_object_list(box, src=0)
+    return box[0]
+
+
 def whole_job_value(limbs_per_step: int, steps: int, ranks: int, total_ms: float) -> float:
     """limb-NTT/s of the whole job: every rank transforms its own polynomials
     (replicas), each step one forward and one inverse of limbs_per_step limbs."""
@@ -1213,8 +1222,11 @@ def main():
     tuned_run = not args.no_tune and args.twiddle == "auto" and args.kernel == "auto" and args.geometry == 0
     if tuned_run:
         best, c2_tune = autotune(G, N, primes, 1, reps=20)
-    if tuned_run and not args.no_select and ws == 1:
+    if tuned_run and not args.no_select:
         chosen, c2_select = select_c2(G, torch, N, primes, bufs, prequeue_ms=args.prequeue_ms)
+        # replicas: every rank times the candidates on its own GPU, and all
+        # run rank 0's choice, so that the ranks' steps are the same work
+        chosen = agree_on_rank0(chosen, dist)
         args.streams = S = chosen["streams"]
         args.ctas_per_sm = chosen["ctas_per_sm"]
         kern = {"fused": G.NTT_KERNEL_FUSED, "per_pass": G.NTT_KERNEL_PER_PASS}[chosen["kernel"]]

@@ -27,7 +27,8 @@ def _rank(rank, world, port, times, out):
         ws, r, local = bench.dist_env()
         t = bench.max_over_ranks(times[rank], dist, "cpu")
         dist.barrier()
-        out[rank] = (ws, r, local, t, bench.whole_job_value(45, 100, ws, t))
+        pick = bench.agree_on_rank0({"config": f"chosen by rank {rank}"}, dist)
+        out[rank] = (ws, r, local, t, bench.whole_job_value(45, 100, ws, t), pick)
     finally:
         dist.destroy_process_group()
 
@@ -40,7 +41,8 @@ def test_two_ranks_max_time_and_whole_job_value():
         mp.spawn(_rank, args=(world, port, times, out), nprocs=world, join=True)
         res = dict(out)
     for rank in range(world):
-        ws, r, local, t, value = res[rank]
+        ws, r, local, t, value, pick = res[rank]
+        assert pick == {"config": "chosen by rank 0"}   # every replica runs rank 0's selection
         assert (ws, r, local) == (world, rank, rank)
         assert t == 20.0                      # every rank reports the slowest rank's time
         assert value == pytest.approx(2 * 45 * 100 * world / 0.020)
