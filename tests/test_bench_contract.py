@@ -70,3 +70,36 @@ def test_gpu_arm_line():
     best = max(rows, key=lambda r: r["value"])
     assert d["config"]["streams"] == best["streams"] and d["config"]["ctas_per_sm"] == best["ctas_per_sm"]
     assert d["plan"]["kernel"] == best["kernel"] and d["plan"]["geometry"] == best["geometry"]
+
+
+def _traffic_csv(path, kernels, read, write):
+    """An ncu --csv log of one call: each kernel with its DRAM bytes and duration."""
+    import csv
+    with open(path, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"])
+        i = 0
+        for k in kernels:
+            for m, v in (("dram__bytes_read.sum", read), ("dram__bytes_write.sum", write),
+                         ("gpu__time_duration.sum", "20,000")):
+                w.writerow([i, k, m, "byte", v])
+                i += 1
+
+
+def test_traffic_json_keys_each_per_pass_configuration(tmp_path):
+    """The traffic JSON writer keeps per-pass configurations from different
+    CSV logs apart: a table plan's row pass (TBL_LAST set) is keyed "table",
+    an OT1 plan's "ot1", each with its own column and row launches summed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    col = "void ntt_pass_kernel<8, 4, 4, 0, 1, 1, 0, 1, 0, 1, unsigned long long, 0>(PassArgsT<T11>)"
+    row_tbl = "void ntt_pass_kernel<8, 3, 4, 1, 1, 12, 1, 0, 1, 0, unsigned long long, 1>(PassArgsT<T11>)"
+    row_ot1 = "void ntt_pass_kernel<8, 3, 4, 1, 1, 12, 1, 0, 1, 0, unsigned long long, 0>(PassArgsT<T11>)"
+    a, b, out = tmp_path / "a.csv", tmp_path / "b.csv", tmp_path / "t.json"
+    _traffic_csv(a, [col, row_tbl], "2,000,000", "1,000")
+    _traffic_csv(b, [col, row_ot1], "3,000", "500")
+    bench.write_traffic_json(str(out), [str(a), str(b)], "test")
+    entries = json.load(open(out))["entries"]
+    got = {(e["kind"], e["geometry"], e["twiddle"], e["direction"]): e["dram_bytes"] for e in entries}
+    assert got == {("per_pass", 1, "table", "forward"): 4002000.0, ("per_pass", 1, "ot1", "forward"): 7000.0}
+    assert all(e["source_hash"] == bench.kernel_source_hash() for e in entries)
