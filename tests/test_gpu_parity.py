@@ -711,3 +711,41 @@ def test_cluster_many_limbs_and_edges(orc):
         p.inverse(d, 200)
         torch.cuda.synchronize()
         assert np.array_equal(host(d).reshape(data.shape), data)
+
+
+def test_every_c2_candidate_full_size(orc):
+    """Every configuration the bench's C2 selection can run, at full C2 size:
+    a plan and its clones on the candidate's streams, each step one
+    ntt_execute(FORWARD | INVERSE) of its own polynomial, as the timed region
+    issues them; the forward of each plan, alone, against the oracle."""
+    import bench
+    w = I.workload_c2()
+    both = G.NTT_OP_FORWARD | G.NTT_OP_INVERSE
+    datas = [I.batch_uniform(w.seed + 20 * k, 1, w.primes, w.N) for k in range(3)]
+    want = oracle_fwd(orc, datas[0], w.primes)
+    kernels = {"fused": G.NTT_KERNEL_FUSED, "per_pass": G.NTT_KERNEL_PER_PASS}
+    lib = G.lib()
+    for kname, tw, geom, ctas, S in bench.C2_CANDIDATES:
+        plans = [G.Plan(w.N, w.primes, *bench.TWIDDLES[tw], kernels[kname], geom, ctas_per_sm=ctas)]
+        try:
+            plans += [plans[0].clone() for _ in range(S - 1)]
+            streams = [torch.cuda.Stream() for _ in range(S)]
+            bufs = [dev(d) for d in datas]
+            torch.cuda.synchronize()
+            for i in range(2 * len(bufs)):
+                j = i % S
+                st = lib.ntt_execute(plans[j].handle, bufs[i % len(bufs)].data_ptr(), 1, both,
+                                     streams[j].cuda_stream)
+                assert st == 0, (kname, tw, geom, S)
+            torch.cuda.synchronize()
+            for b, d in zip(bufs, datas):
+                assert np.array_equal(host(b), d), f"round trip {kname} {tw} g{geom} s{S}"
+            for p in plans:
+                x = dev(datas[0])
+                p.forward(x, 1)
+                torch.cuda.synchronize()
+                assert np.array_equal(host(x), want), f"forward {kname} {tw} g{geom} s{S}"
+                assert p.device_status() == 0
+        finally:
+            for p in reversed(plans):
+                p.close()
