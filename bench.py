@@ -733,6 +733,8 @@ def serve_c5(G, torch, count, budget_gb=64, ring_gb=80, tuned=None, max_batch_jo
                                          for r in runs[frac]],
                 max_completion_gap_us_runs=[r["scheduler"]["max_completion_gap_us"] for r in runs[frac]],
                 max_launch_us_runs=[r["scheduler"]["max_launch_us"] for r in runs[frac]],
+                max_loop_gap_us_runs=[r["scheduler"]["max_loop_gap_us"] for r in runs[frac]],
+                max_device_us_runs=[r["scheduler"]["max_device_us"] for r in runs[frac]],
                 queue_p99_us_runs=[r["timeline_us"]["queue_p99"] for r in runs[frac]],
                 p99_max_over_median=max(p99) / med if med > 0 else None)
         out["scheduler_units"] = "_us keys in microseconds; batches and requests are counts"
