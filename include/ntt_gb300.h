@@ -65,7 +65,12 @@ typedef struct ntt_plan ntt_plan;
 
 /* Twiddle supply (Sec. VII): precomputed table Psi with Shoup companions, or
  * on-the-fly twiddling (OT), which rebuilds the twiddles of the last stages
- * from two small per-prime factor tables with one extra Shoup product each. */
+ * from two small per-prime factor tables with one extra Shoup product each.
+ * A table plan holds N entries (16 B each) per prime; with PER_PASS its row
+ * pass stages the twiddles of all but its last stage in shared memory and
+ * reads the last stage's from the table in device memory (half of the table
+ * per forward or inverse call), where OT keeps N/2 entries and computes
+ * them. */
 enum {
     NTT_TWIDDLE_AUTO = 0,
     NTT_TWIDDLE_TABLE = 1,
