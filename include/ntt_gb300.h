@@ -69,8 +69,8 @@ typedef struct ntt_plan ntt_plan;
  * A table plan holds N entries (16 B each) per prime; with PER_PASS its row
  * pass stages the twiddles of all but its last stage in shared memory and
  * reads the last stage's from the table in device memory (half of the table
- * per forward or inverse call), where OT keeps N/2 entries and computes
- * them. */
+ * per forward or inverse call), where OT on one stage keeps N/2 entries
+ * and forms the last stage's twiddles from its factor tables. */
 enum {
     NTT_TWIDDLE_AUTO = 0,
     NTT_TWIDDLE_TABLE = 1,
